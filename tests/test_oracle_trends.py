@@ -1,0 +1,57 @@
+"""Trend pins against the paper's experiments (Sec. 7), in its massively parallel setting
+(subdomains = fine elements), C_sigma = 10, rtol 1e-8, zero initial guess.
+
+The paper's meshes are not published, so its digits are context only (parity unpinned); what is
+pinned is the behaviour that its tables show and Remark 6.6 predicts:
+* Example 2 (tables for p = q = 1): K(P_ad) about constant when H/h is fixed, growing about 4x
+  when h halves at fixed H (e.g. 72.31 -> 269.70 in the first row);
+* Example 1: coefficient jumps aligned with the coarse agglomerates leave K flat in rho_e
+  (2.31e2 -> 2.34e2), jumps not aligned make K grow linearly (2.92e2 -> 7.38e6);
+* Example 5: nested coarse spaces with q = p give K growing about linearly in p.
+"""
+import numpy as np
+import pytest
+
+from oracle import partition, pcg, schwarz, sipg
+from synth.voronoi import voronoi_mesh
+
+
+def paper_mode_K(n, n_coarse, p, q, seed=1, rho_fn=None):
+    mesh = voronoi_mesh(n, seed)
+    A, _, geom = sipg.assemble(mesh, np.ones(n), p, 10.0)
+    sub = np.arange(n, dtype=np.int32)
+    agg = partition.agglomerates(geom.centroid, sub, n, n_coarse)
+    if rho_fn is not None:
+        A, _, geom = sipg.assemble(mesh, rho_fn(agg, n), p, 10.0, geom=geom)
+    S = schwarz.build(A, mesh, geom, p, sub, agg, q)
+    b = np.random.default_rng(0).standard_normal(A.shape[0])
+    res = pcg.pcg(A, b, S.apply, rtol=1e-8)
+    assert res.converged
+    return pcg.condition_estimate(res), res.iters
+
+
+@pytest.mark.slow
+def test_example2_h_over_H():
+    k_256_16, _ = paper_mode_K(256, 16, 1, 1)
+    k_1024_64, _ = paper_mode_K(1024, 64, 1, 1)
+    k_1024_16, _ = paper_mode_K(1024, 16, 1, 1)
+    assert 1 / 1.5 <= k_1024_64 / k_256_16 <= 1.5          # diagonal of the table: H/h fixed
+    assert 2.5 <= k_1024_16 / k_256_16 <= 6.0              # along a row: h halves at fixed H
+
+
+def test_example1_alignment():
+    aligned = lambda rho_e: (lambda agg, n: np.where(agg % 2 == 0, rho_e, 1.0))  # noqa: E731
+    not_aligned = lambda rho_e: (lambda agg, n: np.where(np.arange(n) % 2 == 0, rho_e, 1.0))  # noqa: E731
+    ka_lo, _ = paper_mode_K(256, 16, 1, 1, rho_fn=aligned(10.0))
+    ka_hi, _ = paper_mode_K(256, 16, 1, 1, rho_fn=aligned(1e6))
+    kn_lo, _ = paper_mode_K(256, 16, 1, 1, rho_fn=not_aligned(10.0))
+    kn_hi, _ = paper_mode_K(256, 16, 1, 1, rho_fn=not_aligned(1e6))
+    assert ka_hi / ka_lo <= 1.2
+    assert kn_hi / kn_lo >= 1e4
+
+
+@pytest.mark.slow
+def test_example5_p_dependence():
+    k1, _ = paper_mode_K(256, 16, 1, 1)
+    k4, _ = paper_mode_K(256, 16, 4, 4)
+    assert 2.0 <= k4 / k1 <= 16.0
