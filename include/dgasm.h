@@ -1,0 +1,223 @@
+/*
+ * dgasm: SIPG discretisation of -div(rho grad u) = f on polygonal meshes of a 2D domain, solved by
+ * conjugate gradients preconditioned with the two-level non-overlapping additive Schwarz operator
+ *     B = R_0^T A_0^{-1} R_0 + sum_i R_i^T A_i^{-1} R_i
+ * of Antonietti, Houston, Pennesi and Suli (arXiv 1903.11357), on one GPU (sm_103a).
+ *
+ * Conventions
+ *  - Every function returns an int: DGASM_OK (0), DGASM_PENDING (> 0, serving only) or a negative
+ *    DGASM_E* code.  dgasm_last_error() returns the calling thread's last message.
+ *  - Handles are opaque, owned by the caller, and released by the matching *_destroy (NULL is a
+ *    no-op).  A system must outlive the preconditioners built from it; a mesh must outlive its
+ *    systems.
+ *  - Host arrays passed in are copied during the call; the caller keeps ownership.
+ *  - Device pointers are borrowed for the duration of the call (dgasm_solve) or until dgasm_poll /
+ *    dgasm_wait reports completion (dgasm_submit).
+ *  - "stream" arguments are cudaStream_t values passed as void*; NULL means the library's own
+ *    stream.  Calls are synchronous with respect to the host unless stated otherwise.
+ *  - Indices are 0-based int32.  Dof a of element e (in the caller's element order) has global index
+ *    e * n_p + a, with n_p = (p+1)(p+2)/2 and the basis order below.
+ *  - The library allocates device memory with cudaMalloc unless dgasm_set_allocator installs hooks.
+ *  - Distinct handles may be used from distinct threads concurrently; one handle is not thread-safe
+ *    except a server, whose submit/poll/wait are.
+ */
+#ifndef DGASM_H
+#define DGASM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DGASM_OK = 0,
+  DGASM_PENDING = 1,      /* request admitted or queued, not finished */
+  DGASM_EINVAL = -1,      /* invalid argument or mesh topology; message names the index */
+  DGASM_ENOMEM = -2,      /* device or host allocation failed */
+  DGASM_ENOTSPD = -3,     /* a non-positive pivot in a local or coarse Cholesky factorisation */
+  DGASM_ENOCONV = -4,     /* maxit reached before the stop test held; x holds the last iterate */
+  DGASM_ENAN = -5,        /* NaN or Inf in the right-hand side or in a Krylov scalar */
+  DGASM_ECUDA = -6,       /* a CUDA runtime call failed; message carries cudaGetErrorString */
+  DGASM_ETIMEOUT = -7,    /* dgasm_wait deadline passed, or a request exceeded its time limit */
+  DGASM_ETOOBIG = -8,     /* request footprint exceeds the server's whole memory budget */
+  DGASM_ECANCELLED = -9,  /* request cancelled before it ran */
+  DGASM_ENOTFOUND = -10   /* unknown ticket */
+};
+
+typedef enum {
+  DGASM_FP64 = 0, /* local factors and solves in FP64 */
+  DGASM_FP32 = 1, /* local factors and solves in FP32 (CUDA cores); outer loop FP64 */
+  DGASM_TF32 = 2, /* local factor trailing updates on tensor cores (TF32 in, FP32 accumulate) */
+  DGASM_BF16 = 3  /* local factor stored in BF16, FP32 accumulation; outer loop FP64 */
+} dgasm_precision;
+
+typedef struct dgasm_mesh_s* dgasm_mesh_t;
+typedef struct dgasm_system_s* dgasm_system_t;
+typedef struct dgasm_prec_s* dgasm_prec_t;
+typedef struct dgasm_server_s* dgasm_server_t;
+
+/* Right-hand side callback: f(xy[2i], xy[2i+1]) -> out[i] for i < n.  Called from the calling
+ * thread only, with n up to a few thousand points per call. */
+typedef void (*dgasm_rhs_fn)(int n, const double* xy, double* out, void* user);
+
+/* Optional device allocator hooks (e.g. a framework's caching allocator). alloc returns NULL on
+ * failure.  Passing NULL for both restores cudaMalloc/cudaFree.  Process-wide. */
+typedef void* (*dgasm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*dgasm_free_fn)(void* ptr, void* stream, void* user);
+int dgasm_set_allocator(dgasm_alloc_fn alloc, dgasm_free_fn free_, void* user);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to n) into buf.
+ * Returns the code of that error (DGASM_OK if none). */
+int dgasm_last_error(char* buf, size_t n);
+
+/* ---- Mesh (Sec. 2: tessellation T_h of polygons kappa, diameter h_kappa, faces F_h^I, F_h^B;
+ *      Remark 2.1: rho piecewise constant, rho_kappa > 0) ------------------------------------- */
+
+/* nv vertices xy[2*nv] (x, y interleaved); ne polygons, polygon e has vertex ids
+ * poly_vtx[poly_ptr[e] .. poly_ptr[e+1]) in counter-clockwise order; rho[ne] > 0.
+ * Faces are derived from shared vertex pairs: an edge (a, b) whose reverse (b, a) belongs to
+ * another polygon is an interior face, otherwise a boundary face (zero Dirichlet data).
+ * Computes areas, area centroids, diameters h_kappa (largest vertex distance) and bounding boxes.
+ * Errors: DGASM_EINVAL for fewer than 3 vertices, a vertex id out of range, non-positive signed
+ * area (clockwise or degenerate polygon), rho <= 0 or non-finite, an edge used twice in the same
+ * direction; the message names the element. */
+int dgasm_mesh_create(int nv, const double* xy, int ne, const int* poly_ptr, const int* poly_vtx,
+                      const double* rho, dgasm_mesh_t* out);
+/* Counts: elements, interior faces, boundary faces. */
+int dgasm_mesh_info(dgasm_mesh_t m, int* ne, int* nf_interior, int* nf_boundary);
+/* Area centroids (2*ne doubles, x/y interleaved) as used by the partitioner. */
+int dgasm_mesh_centroids(dgasm_mesh_t m, double* out_xy);
+int dgasm_mesh_destroy(dgasm_mesh_t m);
+
+/* ---- Partitions (Sec. 3: subdomains Omega_i, unions of elements; coarse agglomerates D_j) ------
+ * Recursive coordinate bisection of the element area centroids: a set is cut along the longer side
+ * of its centroid bounding box (x on ties) after sorting by (coordinate, element id); for k parts
+ * the first floor(k/2) parts take floor(n floor(k/2) / k) elements; parts numbered depth-first,
+ * lower side first.  Agglomerates: if ncoarse >= nsub, subdomain i is cut into
+ * floor((i+1) ncoarse / nsub) - floor(i ncoarse / nsub) agglomerates (nested in the subdomains);
+ * otherwise the whole mesh is cut into ncoarse agglomerates.  ncoarse = 0 leaves agg_of_elem
+ * untouched.  Outputs are host arrays of ne ints.  Errors: DGASM_EINVAL if nsub < 1 or > ne or
+ * ncoarse < 0 or > ne. */
+int dgasm_partition(dgasm_mesh_t m, int nsub, int ncoarse, int* sub_of_elem, int* agg_of_elem);
+
+/* ---- SIPG system (Sec. 2, Eq. Ah with the lifting of Eq. lifting, penalty of Eq. Sigma) ---------
+ * Basis on element kappa with bounding box [x0,x1]x[y0,y1]: phi_ij = c_ij L_i(xi) L_j(eta),
+ * xi = 2(x - xc)/wx, eta = 2(y - yc)/wy, i + j <= p, c_ij = sqrt((2i+1)(2j+1)/(wx wy)); ordered by
+ * total degree ascending, then i descending.  The matrix is
+ *   A[a,b] = rho_k int grad phi_a . grad phi_b
+ *          + sum_F int_F ( -<rho>/2 s_a phi_a d_n phi_b - <rho>/2 s_b phi_b d_n phi_a
+ *                          + sigma s_a s_b phi_a phi_b )
+ * with <.> the harmonic average (rho_kappa and h_kappa themselves on boundary faces), s = +-1 the
+ * side and sigma = c_sigma <rho> p^2 / <h>.  All integrals are exact up to rounding.  If f is not
+ * NULL the load vector b_a = int f phi_a is assembled (Gauss rule of p+5 points per direction on
+ * each triangle of the element's fan).  The block-sparse matrix is uploaded to the device and kept
+ * by the system.  Errors: DGASM_EINVAL (p < 1 or p > 8, c_sigma <= 0), DGASM_ENOMEM, DGASM_ECUDA. */
+int dgasm_assemble(dgasm_mesh_t m, int p, double c_sigma, dgasm_rhs_fn f, void* user,
+                   dgasm_system_t* out);
+/* Number of dofs (ne * n_p) and n_p. */
+int dgasm_system_dofs(dgasm_system_t s, int64_t* ndof, int* n_p);
+/* Host copy of the load vector (ndof doubles); DGASM_EINVAL if no f was given. */
+int dgasm_system_rhs(dgasm_system_t s, double* b);
+/* Host copy of the block-sparse matrix in the caller's element order: block rows = elements,
+ * rowptr[ne+1], col[nnzb], vals[nnzb * n_p * n_p] with block (e, col) stored row-major
+ * (vals[k*n_p*n_p + a*n_p + b] = A[e*n_p + a, col*n_p + b]).  Pass NULL to query nnzb only. */
+int dgasm_system_blocks(dgasm_system_t s, int64_t* nnzb, int* rowptr, int* col, double* vals);
+/* y = A x on the device, caller's dof order; x, y device arrays of ndof doubles. */
+int dgasm_system_spmv(dgasm_system_t s, const double* x, double* y, void* stream);
+int dgasm_system_destroy(dgasm_system_t s);
+
+/* ---- Two-level Schwarz preconditioner (Sec. 3: local solvers, coarse solver, Eq. R0T, Eq. A0) --- */
+typedef struct {
+  int nsub;                 /* number of subdomains (1..ne); ignored if sub_of_elem is given */
+  int ncoarse;              /* number of coarse agglomerates; 0 = one-level (no coarse space) */
+  int p_c;                  /* coarse degree q, 1 <= q <= p (Sec. 3 requires q <= p) */
+  const int* sub_of_elem;   /* optional host array [ne]: subdomain of each element */
+  const int* agg_of_elem;   /* optional host array [ne]: agglomerate of each element */
+  int precision;            /* dgasm_precision for the local factors and solves */
+  void* stream;             /* cudaStream_t or NULL */
+} dgasm_setup_opts;
+
+/* Builds the partition (RCB as dgasm_partition, unless arrays are given), renumbers the elements
+ * subdomain by subdomain (reverse Cuthill-McKee inside each), extracts each A_i (the principal
+ * submatrix of A on Omega_i's dofs, Sec. 3), scales it to unit diagonal and factors it by tile
+ * Cholesky (FP64/FP32/TF32/BF16 per precision); builds R_0^T|_kappa = M_kappa^{-1} N_kappa (Eq. R0T,
+ * exact injection in the nested case, Remark 3.1), A_0 = R_0 A R_0^T (Eq. A0) and its FP64 Cholesky
+ * factor and inverse.  All numerical work runs on the device.  Errors: DGASM_EINVAL (bad options or
+ * arrays), DGASM_ENOTSPD (the message names the subdomain, or "coarse", and the pivot row),
+ * DGASM_ENOMEM, DGASM_ECUDA. */
+int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_prec_t* out);
+/* z = B r for nrhs vectors (device, caller's dof order, column-major ndof x nrhs). */
+int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, double* z, void* stream);
+/* Partition actually used (host arrays [ne]); either pointer may be NULL. */
+int dgasm_prec_partition(dgasm_prec_t pc, int* sub_of_elem, int* agg_of_elem);
+/* Bytes held on the device by the preconditioner (factors, coarse operator, permuted matrix). */
+int dgasm_prec_footprint(dgasm_prec_t pc, int64_t* bytes);
+int dgasm_prec_destroy(dgasm_prec_t pc);
+
+/* ---- ASPCG solve (Sec. 7: PCG with P_ad from x0 = 0, stop when ||r||_2 / ||b||_2 < rtol) --------- */
+typedef struct {
+  double rtol;          /* relative residual tolerance (Sec. 7 uses 1e-8); <= 0 means 1e-8 */
+  int maxit;            /* iteration limit; <= 0 means 10000 */
+  int fixed_iters;      /* > 0: run exactly this many iterations, no stop test */
+  int x0_given;         /* 1: x holds the initial guess on entry; 0: start from zero (Sec. 7) */
+  int host_buffers;     /* 1: b and x are host pointers (copied in and out inside the call) */
+  void* stream;         /* cudaStream_t or NULL */
+} dgasm_solve_opts;
+
+typedef struct {
+  int iters;            /* PCG iterations (matrix-vector products after the initial residual) */
+  int converged;        /* 1 if ||r_k|| / ||b|| <= rtol held */
+  double relres;        /* recursive residual ||r_k|| / ||b|| */
+  double true_relres;   /* ||b - A x_k|| / ||b||, recomputed in FP64 */
+  double lambda_min;    /* Lanczos extreme-eigenvalue estimates of B A from the CG coefficients */
+  double lambda_max;
+  double kappa;         /* lambda_max / lambda_min: the estimate of K(P_ad) of Sec. 7 */
+  double solve_ms;      /* device time of the solve */
+} dgasm_stats;
+
+/* Solves A x = b for nrhs right-hand sides (column-major ndof x nrhs, caller's dof order), device
+ * pointers unless opts->host_buffers.  st (nrhs entries) may be NULL.  The Lanczos estimate uses all
+ * CG coefficients of the run.  Returns DGASM_ENOCONV if a right-hand side hit maxit (x holds the
+ * last iterate), DGASM_ENAN on a NaN/Inf in b or in a Krylov scalar, DGASM_EINVAL, DGASM_ECUDA. */
+int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x, const dgasm_solve_opts* o,
+                dgasm_stats* st);
+
+/* Solves nprob independent problems in one set of batched launches: problem i uses pcs[i] with
+ * nrhs[i] right-hand sides b[i] / x[i] (device pointers).  Results are bitwise identical to
+ * dgasm_solve of each problem alone.  st holds sum(nrhs) entries in problem order (may be NULL). */
+int dgasm_solve_batch(int nprob, const dgasm_prec_t* pcs, const int* nrhs, const double* const* b,
+                      double* const* x, const dgasm_solve_opts* o, dgasm_stats* st);
+
+/* Convenience: Lanczos extremes of the tridiagonal built from k CG coefficients alpha[k], beta[k-1]
+ * (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j), host only. */
+int dgasm_lanczos(int k, const double* alpha, const double* beta, double* lambda_min, double* lambda_max);
+
+/* ---- Serving: continuous batching of solve requests ---------------------------------------------
+ * A server owns a scheduler thread.  dgasm_submit enqueues a request (a system, setup options, nrhs
+ * right-hand sides); the request is admitted when its device footprint (factors + coarse operator +
+ * Krylov state for nrhs) fits in hbm_budget next to the admitted ones and one of max_slots slots is
+ * free.  Admitted requests are set up, then advance together, one PCG iteration each per batched
+ * round; finished requests retire between rounds and queued ones join.  b and x are device pointers
+ * (ndof x nrhs, column-major) borrowed until completion. */
+int dgasm_server_create(size_t hbm_budget, int max_slots, void* stream, dgasm_server_t* out);
+int dgasm_submit(dgasm_server_t sv, dgasm_system_t sys, const dgasm_setup_opts* so, int nrhs,
+                 const double* b, double* x, const dgasm_solve_opts* o, uint64_t* ticket);
+/* DGASM_PENDING while queued or running; DGASM_OK or the request's error when finished (st gets the
+ * statistics of each right-hand side, may be NULL); DGASM_ENOTFOUND for an unknown or already
+ * collected ticket.  A finished ticket is released by the first poll that reports it. */
+int dgasm_poll(dgasm_server_t sv, uint64_t ticket, dgasm_stats* st);
+/* Blocks until the ticket finishes or timeout_ms passes (DGASM_ETIMEOUT, ticket stays valid). */
+int dgasm_wait(dgasm_server_t sv, uint64_t ticket, int timeout_ms, dgasm_stats* st);
+/* Cancels a queued (not yet admitted) request: DGASM_OK, or DGASM_PENDING if it already runs. */
+int dgasm_cancel(dgasm_server_t sv, uint64_t ticket);
+/* Server counters: requests done, rounds run, admission stalls, bytes in use. */
+int dgasm_server_stats(dgasm_server_t sv, int64_t* done, int64_t* rounds, int64_t* stalls,
+                       int64_t* bytes_in_use);
+int dgasm_server_destroy(dgasm_server_t sv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGASM_H */

@@ -1,0 +1,112 @@
+// Device-side descriptors of the batched PCG engine and the launch wrappers of its kernels.
+// Shared by the CUDA translation units and the host orchestration; plain data only.
+#pragma once
+
+#include <cstdint>
+
+#include "dgasm.h"
+
+namespace dgasm {
+
+constexpr int NTHREADS = 256;  // threads per CTA of the vector kernels
+constexpr int KMAX = 8;        // right-hand sides per problem
+constexpr int KC = 4;          // right-hand sides per local-solve CTA
+
+enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
+enum Counter { C_SPMV = 0, C_GRP = 1, C_PUPD = 2, C_NCOUNTERS = 4 };
+
+// One problem (one preconditioner with k right-hand sides) of a batch.
+struct ProbDev {
+  int ne, np, np2s, nq, ndof, nsub, ngrp, n0, k, prec;
+  int epi;            // elements per element-chunk item
+  int n_chunk_items;  // element-chunk items (SpMV, p update)
+  int n_coarse_items; // coarse GEMV items (8 rows each)
+  int kc;             // right-hand sides per local-solve item
+  int n_rhs_chunks;   // ceil(k / kc)
+  int maxit, fixed_iters;
+  double rtol;
+  // matrix, internal order, blocks column-major with stride np2s
+  const int* rowptr;
+  const int* col;
+  const double* vals;
+  const int* perm;    // internal element -> caller element
+  // local factors
+  const int* sub_e0;
+  const int* sub_trow;
+  const int* trow_F;
+  const long long* trow_ptr;
+  const void* Lr;     // row-major tiles (backward sweep, diagonal tiles hold inv(L_II))
+  const void* Lc;     // column-major tiles (forward sweep)
+  const double* scale;
+  // groups and coarse space
+  const int* grp_ptr;
+  const int* grp_elems;
+  const int* agg_int; // agglomerate of each internal element
+  const double* r0t;  // [ne][np][nq] R_0^T blocks, internal element order
+  const double* A0inv;// [n0][n0]
+  // caller-order input/output, column-major ndof x k
+  const double* b_user;
+  double* x_user;
+  // Krylov state [k][ndof], internal order
+  double *b, *x, *r, *p, *q, *z;
+  double *r0, *z0;    // [k][n0]
+  // per right-hand side scalars
+  double *bnorm, *gamma, *alpha, *relres, *true_rr;
+  int *done, *iters, *status;
+  double *alpha_hist, *beta_hist;  // [k][maxit]
+  // deterministic partial sums
+  double *part_pq;    // [n_chunk_items][k]
+  double *part_rr;    // [ngrp][k]
+  double *part_rz;    // [nsub][k]
+  double *part_c;     // [n_coarse_items][k]
+  unsigned int* counters;  // [C_NCOUNTERS]
+  int* remaining;     // right-hand sides still iterating, shared by the batch
+};
+
+struct BatchDev {
+  const ProbDev* probs;
+  int nprob;
+  const int* prefix[K_NKINDS + 8];  // item prefix per kind; K_NKINDS + 2*prec + (kc > 1) for local solves
+};
+
+// ---- solve kernels (kernels_solve.cu) ----
+enum UpdateMode { MODE_INIT = 0, MODE_ITER = 1 };
+int launch_spmv(const BatchDev& B, int total, int operand /*0: q = A p, 1: q = A x, true residual*/, void* stream);
+int launch_update(const BatchDev& B, int total, int mode, int use_q, void* stream);
+int launch_local(const BatchDev& B, int slot, int total, int smem_bytes, void* stream);
+int launch_coarse(const BatchDev& B, int total, void* stream);
+int launch_pupdate(const BatchDev& B, int total, int mode, void* stream);
+int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);
+int local_smem_bytes(int prec, int ndof_max, int kc);
+int launch_system_spmv(const int* rowptr, const int* col, const double* vals, int ne, int np, int np2s,
+                       const double* x, double* y, void* stream);
+
+// ---- setup kernels (kernels_setup.cu) ----
+struct EnvDev {
+  int nsub;
+  const int* ndof;        // [nsub]
+  const int* sub_trow;
+  const int* trow_F;
+  const long long* trow_ptr;
+};
+int launch_permute_blocks(const double* src, const long long* src_blk, double* dst, long long nnzb, int np2s,
+                          void* stream);
+int launch_scale(const int* rowptr, const int* col, const double* vals, int ne, int np, int np2s, double* scale,
+                 void* stream);
+int launch_extract_rows(int prec, const EnvDev& E, const int* sub_e0, const int* rowptr, const int* col,
+                        const double* vals, int np, int np2s, const double* scale, void* Lr, int nsub, int ne,
+                        void* stream);
+int launch_chol_step(int prec, const EnvDev& E, void* Lr, int K, const int* diag_task, int n_diag,
+                     const int* panel_task, int n_panel, const int* upd_task, int n_upd, int* err, void* stream);
+int launch_to_colmajor(int prec, const void* Lr, void* Lc, long long ntiles, void* stream);
+int launch_to_bf16(const float* src, void* dst, long long n, void* stream);
+int launch_r0t(const int* perm, const double* xy, const int* pptr, const int* pvtx, const double* bbox,
+               const int* agg_int, const double* agg_bbox, int ne, int p, int q, const double* gl_t,
+               const double* gl_w, int mq, double* r0t, void* stream);
+int launch_galerkin(const int* grp_ptr, const int* grp_elems, const int* agg_int, const int* rowptr,
+                    const int* col, const double* vals, const double* r0t, int nagg, int np, int np2s, int nq,
+                    double* A0, void* stream);
+int launch_coarse_extract(const double* A0, int n0, double* scale0, const EnvDev& E0, double* Lr0, void* stream);
+int launch_identity(double* I, int n, void* stream);
+
+}  // namespace dgasm

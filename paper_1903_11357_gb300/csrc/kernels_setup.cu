@@ -1,0 +1,489 @@
+// Device setup kernels: matrix permutation, Jacobi scaling, extraction of the subdomain matrices A_i
+// (principal submatrices of A, Sec. 3) into tile envelopes, tile Cholesky factorisation with inverted
+// diagonal tiles, the L2 prolongation R_0^T (Eq. R0T) and the Galerkin coarse operator A_0 (Eq. A0).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "engine.h"
+
+namespace dgasm {
+
+namespace {
+
+constexpr int T = 32;      // tile edge
+constexpr int TT = T * T;
+
+template <typename S> struct Compute { using type = float; };
+template <> struct Compute<double> { using type = double; };
+
+template <typename C> __device__ __forceinline__ C csqrt(C x);
+template <> __device__ __forceinline__ double csqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float csqrt<float>(float x) { return sqrtf(x); }
+
+__device__ __forceinline__ long long tile_index(const EnvDev& E, int s, int I, int J) {
+  int tr = E.sub_trow[s] + I;
+  return E.trow_ptr[tr] + (J - E.trow_F[tr]);
+}
+
+__global__ void k_permute_blocks(const double* __restrict__ src, const long long* __restrict__ src_blk,
+                                 double* __restrict__ dst, long long nnzb, int np2s) {
+  long long total = nnzb * np2s;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    long long b = t / np2s;
+    int o = (int)(t - b * np2s);
+    dst[t] = src[src_blk[b] * np2s + o];
+  }
+}
+
+// scale[i*np + a] = 1 / sqrt(A_ii[a][a]) from the diagonal block of internal row i
+__global__ void k_scale(const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ vals,
+                        int ne, int np, int np2s, double* __restrict__ scale) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne * np; t += gridDim.x * blockDim.x) {
+    int i = t / np, a = t - i * np;
+    double d = -1.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+      if (col[k] == i) { d = vals[(long long)k * np2s + a * np + a]; break; }
+    scale[t] = d > 0.0 ? 1.0 / sqrt(d) : __longlong_as_double(0x7ff8000000000000ULL);
+  }
+}
+
+// one warp per internal element row: write the lower-triangle entries of the scaled A_i into the
+// row-major tile pool; padding rows of the last tile row get a unit diagonal
+template <typename S>
+__global__ void k_extract(EnvDev E, const int* __restrict__ sub_e0, const int* __restrict__ rowptr,
+                          const int* __restrict__ col, const double* __restrict__ vals, int np, int np2s,
+                          const double* __restrict__ scale, S* __restrict__ Lr, int nsub) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  int ne = sub_e0[nsub];
+  if (warp >= ne) return;
+  int i = warp;
+  // subdomain of row i (binary search)
+  int lo = 0, hi = nsub;
+  while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (sub_e0[mid] <= i) lo = mid; else hi = mid; }
+  int s = lo, e0 = sub_e0[s], e1 = sub_e0[s + 1];
+  int n = (e1 - e0) * np;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+    int c = col[k];
+    if (c < e0 || c >= e1) continue;
+    for (int t = lane; t < np * np; t += 32) {
+      int a = t % np, b = t / np;  // column-major entry (a, b) at b*np + a
+      int row = (i - e0) * np + a, cl = (c - e0) * np + b;
+      if (row < cl) continue;
+      double v = vals[(long long)k * np2s + t] * scale[(long long)i * np + a] * scale[(long long)c * np + b];
+      long long ti = tile_index(E, s, row / T, cl / T);
+      Lr[ti * TT + (row % T) * T + (cl % T)] = (S)v;
+    }
+  }
+  // padding: the last element of the subdomain writes the unit diagonal of the padded rows
+  if (i == e1 - 1) {
+    int nbt = (n + T - 1) / T;
+    for (int row = n + lane; row < nbt * T; row += 32) {
+      long long ti = tile_index(E, s, nbt - 1, nbt - 1);
+      Lr[ti * TT + (row % T) * T + (row % T)] = (S)1.0;
+    }
+  }
+}
+
+// Cholesky of the diagonal tile (K, K) and in-place replacement by inv(L_KK) (lower triangular)
+template <typename S>
+__global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, int K, const int* __restrict__ tasks,
+                                                   int* __restrict__ err) {
+  using C = typename Compute<S>::type;
+  __shared__ C a[T][T + 1];
+  __shared__ C inv[T][T + 1];
+  __shared__ int bad;
+  int s = tasks[blockIdx.x];
+  long long ti = tile_index(E, s, K, K);
+  S* tile = L + ti * TT;
+  int tid = threadIdx.x;
+  if (tid == 0) bad = -1;
+  for (int t = tid; t < TT; t += blockDim.x) {
+    int r = t / T, c = t % T;
+    a[r][c] = (r >= c) ? (C)tile[t] : (C)0;
+  }
+  __syncthreads();
+  for (int j = 0; j < T; ++j) {
+    if (tid == 0) {
+      C d = a[j][j];
+      if (!(d > (C)0)) { if (bad < 0) bad = j; d = (C)1; }
+      a[j][j] = csqrt<C>(d);
+    }
+    __syncthreads();
+    if (tid > j && tid < T) a[tid][j] /= a[j][j];
+    __syncthreads();
+    for (int t = tid; t < TT; t += blockDim.x) {
+      int r = t / T, c = t % T;
+      if (c > j && r >= c) a[r][c] -= a[r][j] * a[c][j];
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular factor, one column per thread
+  if (tid < T) {
+    int c = tid;
+    for (int r = 0; r < c; ++r) inv[r][c] = (C)0;
+    inv[c][c] = (C)1 / a[c][c];
+    for (int r = c + 1; r < T; ++r) {
+      C acc = (C)0;
+      for (int m = c; m < r; ++m) acc += a[r][m] * inv[m][c];
+      inv[r][c] = -acc / a[r][r];
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < TT; t += blockDim.x) tile[t] = (S)inv[t / T][t % T];
+  if (tid == 0 && bad >= 0) {
+    // record the first failure: subdomain and pivot row
+    atomicCAS(&err[0], 0, 1);
+    atomicCAS(&err[1], -1, s);
+    atomicCAS(&err[2], -1, K * T + bad);
+  }
+}
+
+// panel: L_IK = A_IK inv(L_KK)^T
+template <typename S>
+__global__ void __launch_bounds__(256) k_chol_panel(EnvDev E, S* __restrict__ L, int K, const int* __restrict__ tasks) {
+  using C = typename Compute<S>::type;
+  __shared__ C inv[T][T + 1];
+  __shared__ C A[T][T + 1];
+  int s = tasks[2 * blockIdx.x], I = tasks[2 * blockIdx.x + 1];
+  const S* D = L + tile_index(E, s, K, K) * TT;
+  S* P = L + tile_index(E, s, I, K) * TT;
+  for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+    inv[t / T][t % T] = (C)D[t];
+    A[t / T][t % T] = (C)P[t];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+    int r = t / T, c = t % T;
+    C acc = (C)0;
+    for (int m = 0; m <= c; ++m) acc += A[r][m] * inv[c][m];
+    P[t] = (S)acc;
+  }
+}
+
+// trailing update: A_IJ -= L_IK L_JK^T
+template <typename S>
+__global__ void __launch_bounds__(256) k_chol_update(EnvDev E, S* __restrict__ L, int K, const int* __restrict__ tasks) {
+  using C = typename Compute<S>::type;
+  __shared__ C X[T][T + 1];
+  __shared__ C Y[T][T + 1];
+  int s = tasks[3 * blockIdx.x], I = tasks[3 * blockIdx.x + 1], J = tasks[3 * blockIdx.x + 2];
+  const S* Li = L + tile_index(E, s, I, K) * TT;
+  const S* Lj = L + tile_index(E, s, J, K) * TT;
+  S* Cij = L + tile_index(E, s, I, J) * TT;
+  for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+    X[t / T][t % T] = (C)Li[t];
+    Y[t / T][t % T] = (C)Lj[t];
+  }
+  __syncthreads();
+  // each thread owns 4 entries of one column c: rows r0, r0+8, r0+16, r0+24
+  int c = threadIdx.x % T, r0 = threadIdx.x / T;
+  C acc[4] = {0, 0, 0, 0};
+  for (int m = 0; m < T; ++m) {
+    C y = Y[c][m];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += X[r0 + 8 * u][m] * y;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int r = r0 + 8 * u;
+    Cij[r * T + c] = (S)((C)Cij[r * T + c] - acc[u]);
+  }
+}
+
+template <typename S>
+__global__ void k_to_colmajor(const S* __restrict__ Lr, S* __restrict__ Lc, long long ntiles) {
+  __shared__ S buf[T][T + 1];
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const S* src = Lr + t * TT;
+    S* dst = Lc + t * TT;
+    for (int u = threadIdx.x; u < TT; u += blockDim.x) buf[u / T][u % T] = src[u];
+    __syncthreads();
+    for (int u = threadIdx.x; u < TT; u += blockDim.x) dst[u] = buf[u % T][u / T];
+    __syncthreads();
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    dst[t] = __float2bfloat16_rn(src[t]);
+}
+
+// ---- coarse transfer R_0^T|_kappa = M_kappa^{-1} N_kappa (Eq. R0T, nested agglomerates) ---------
+constexpr int R0T_WARPS = 4;
+
+__device__ void legendre_dev(int p, double t, double* L, double* dL) {
+  L[0] = 1.0; dL[0] = 0.0;
+  if (p >= 1) { L[1] = t; dL[1] = 1.0; }
+  for (int k = 1; k < p; ++k) {
+    L[k + 1] = ((2.0 * k + 1.0) * t * L[k] - k * L[k - 1]) / (k + 1.0);
+    dL[k + 1] = dL[k - 1] + (2.0 * k + 1.0) * L[k];
+  }
+}
+
+// values of the scaled Legendre basis of degree p on box at (x, y)
+__device__ void basis_dev(int p, const double* box, double x, double y, double* out, int stride) {
+  double wx = box[1] - box[0], wy = box[3] - box[2];
+  double xi = 2.0 * (x - 0.5 * (box[0] + box[1])) / wx;
+  double eta = 2.0 * (y - 0.5 * (box[2] + box[3])) / wy;
+  double Lx[10], dLx[10], Ly[10], dLy[10];
+  legendre_dev(p, xi, Lx, dLx);
+  legendre_dev(p, eta, Ly, dLy);
+  int a = 0;
+  for (int d = 0; d <= p; ++d)
+    for (int i = d; i >= 0; --i, ++a) {
+      int j = d - i;
+      out[a * stride] = sqrt((2.0 * i + 1.0) * (2.0 * j + 1.0) / (wx * wy)) * Lx[i] * Ly[j];
+    }
+}
+
+__global__ void k_r0t(const int* __restrict__ perm, const double* __restrict__ xy, const int* __restrict__ pptr,
+                      const int* __restrict__ pvtx, const double* __restrict__ bbox, const int* __restrict__ agg_int,
+                      const double* __restrict__ agg_bbox, int ne, int p, int q, const double* __restrict__ gl_t,
+                      const double* __restrict__ gl_w, int mq, double* __restrict__ r0t) {
+  extern __shared__ double sm[];
+  const int np = (p + 1) * (p + 2) / 2, nq = (q + 1) * (q + 2) / 2;
+  const int per_warp = 32 * np + 32 * nq + np * np + np * nq;
+  int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* phi = sm + wid * per_warp;   // [np][32]
+  double* psi = phi + 32 * np;         // [nq][32]
+  double* M = psi + 32 * nq;           // [np][np]
+  double* N = M + np * np;             // [np][nq]
+  int i = blockIdx.x * R0T_WARPS + wid;
+  if (i >= ne) return;
+  int e = perm[i];
+  const double* box = bbox + 4LL * e;
+  const double* cbox = agg_bbox + 4LL * agg_int[i];
+  int b = pptr[e], nv = pptr[e + 1] - b;
+  double cx = 0, cy = 0;
+  for (int k = 0; k < nv; ++k) { cx += xy[2LL * pvtx[b + k]]; cy += xy[2LL * pvtx[b + k] + 1]; }
+  cx /= nv; cy /= nv;
+  for (int t = lane; t < np * np; t += 32) M[t] = 0.0;
+  for (int t = lane; t < np * nq; t += 32) N[t] = 0.0;
+  __syncwarp();
+  int npts = nv * mq * mq;
+  for (int base = 0; base < npts; base += 32) {
+    int pt = base + lane;
+    double wq = 0.0;
+    if (pt < npts) {
+      int tri = pt / (mq * mq), rem = pt % (mq * mq), iu = rem / mq, iv = rem % mq;
+      const double* B = xy + 2LL * pvtx[b + tri];
+      const double* Cv = xy + 2LL * pvtx[b + (tri + 1) % nv];
+      double e1x = B[0] - cx, e1y = B[1] - cy, e2x = Cv[0] - B[0], e2y = Cv[1] - B[1];
+      double u = gl_t[iu], v = gl_t[iv];
+      double x = cx + u * e1x + u * v * e2x, y = cy + u * e1y + u * v * e2y;
+      wq = gl_w[iu] * gl_w[iv] * u * fabs(e1x * e2y - e1y * e2x);
+      basis_dev(p, box, x, y, phi + lane, 32);
+      basis_dev(q, cbox, x, y, psi + lane, 32);
+      for (int a = 0; a < np; ++a) phi[a * 32 + lane] *= sqrt(wq);
+      for (int c = 0; c < nq; ++c) psi[c * 32 + lane] *= sqrt(wq);
+    } else {
+      for (int a = 0; a < np; ++a) phi[a * 32 + lane] = 0.0;
+      for (int c = 0; c < nq; ++c) psi[c * 32 + lane] = 0.0;
+    }
+    __syncwarp();
+    for (int t = lane; t < np * np; t += 32) {
+      int a = t / np, c = t % np;
+      double acc = 0.0;
+      for (int u = 0; u < 32; ++u) acc += phi[a * 32 + u] * phi[c * 32 + u];
+      M[t] += acc;
+    }
+    for (int t = lane; t < np * nq; t += 32) {
+      int a = t / nq, c = t % nq;
+      double acc = 0.0;
+      for (int u = 0; u < 32; ++u) acc += phi[a * 32 + u] * psi[c * 32 + u];
+      N[t] += acc;
+    }
+    __syncwarp();
+  }
+  // Cholesky of M (lane 0), then forward/backward solves, one coarse column per lane
+  if (lane == 0) {
+    for (int j = 0; j < np; ++j) {
+      double d = M[j * np + j];
+      for (int m = 0; m < j; ++m) d -= M[j * np + m] * M[j * np + m];
+      d = sqrt(d);
+      M[j * np + j] = d;
+      for (int r = j + 1; r < np; ++r) {
+        double v = M[r * np + j];
+        for (int m = 0; m < j; ++m) v -= M[r * np + m] * M[j * np + m];
+        M[r * np + j] = v / d;
+      }
+    }
+  }
+  __syncwarp();
+  for (int c = lane; c < nq; c += 32) {
+    for (int r = 0; r < np; ++r) {
+      double v = N[r * nq + c];
+      for (int m = 0; m < r; ++m) v -= M[r * np + m] * N[m * nq + c];
+      N[r * nq + c] = v / M[r * np + r];
+    }
+    for (int r = np - 1; r >= 0; --r) {
+      double v = N[r * nq + c];
+      for (int m = r + 1; m < np; ++m) v -= M[m * np + r] * N[m * nq + c];
+      N[r * nq + c] = v / M[r * np + r];
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < np * nq; t += 32) r0t[(long long)i * np * nq + t] = N[t];
+}
+
+// A_0 = R_0 A R_0^T (Eq. A0): one warp per agglomerate J, blocks visited in a fixed order; only this
+// warp writes the rows of J, so no atomics are needed and the sum order is deterministic
+__global__ void k_galerkin(const int* __restrict__ grp_ptr, const int* __restrict__ grp_elems,
+                           const int* __restrict__ agg_int, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ vals, const double* __restrict__ r0t, int nagg, int np, int np2s,
+                           int nq, double* __restrict__ A0) {
+  extern __shared__ double sm[];
+  int J = blockIdx.x;
+  if (J >= nagg) return;
+  int lane = threadIdx.x;
+  double* Tm = sm;  // [np][nq]
+  const int n0 = nagg * nq;
+  for (int g = grp_ptr[J]; g < grp_ptr[J + 1]; ++g) {
+    int e = grp_elems[g];
+    const double* Re = r0t + (long long)e * np * nq;
+    for (int k = rowptr[e]; k < rowptr[e + 1]; ++k) {
+      int c = col[k];
+      int Jc = agg_int[c];
+      const double* Rc = r0t + (long long)c * np * nq;
+      const double* Bk = vals + (long long)k * np2s;
+      __syncwarp();
+      for (int t = lane; t < np * nq; t += 32) {
+        int r = t / nq, cc = t % nq;
+        double acc = 0.0;
+        for (int m = 0; m < np; ++m) acc += Bk[m * np + r] * Rc[m * nq + cc];
+        Tm[t] = acc;
+      }
+      __syncwarp();
+      for (int t = lane; t < nq * nq; t += 32) {
+        int a = t / nq, cc = t % nq;
+        double acc = 0.0;
+        for (int r = 0; r < np; ++r) acc += Re[r * nq + a] * Tm[r * nq + cc];
+        A0[(long long)(J * nq + a) * n0 + Jc * nq + cc] += acc;
+      }
+    }
+  }
+}
+
+// symmetrise, scale to unit diagonal and write the lower triangle of A_0 into its (dense) tile envelope
+__global__ void k_coarse_scale(const double* __restrict__ A0, int n0, double* __restrict__ scale0) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  double d = A0[(long long)i * n0 + i];
+  scale0[i] = d > 0.0 ? 1.0 / sqrt(d) : __longlong_as_double(0x7ff8000000000000ULL);
+}
+
+__global__ void k_coarse_extract(const double* __restrict__ A0, int n0, const double* __restrict__ scale0, EnvDev E,
+                                 double* __restrict__ Lr) {
+  int nbt = (n0 + T - 1) / T;
+  long long total = (long long)nbt * T * nbt * T;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int row = (int)(t / (nbt * T)), cl = (int)(t % (nbt * T));
+    if (row < cl) continue;
+    double v;
+    if (row < n0 && cl < n0)
+      v = 0.5 * (A0[(long long)row * n0 + cl] + A0[(long long)cl * n0 + row]) * scale0[row] * scale0[cl];
+    else
+      v = (row == cl) ? 1.0 : 0.0;
+    Lr[tile_index(E, 0, row / T, cl / T) * TT + (row % T) * T + (cl % T)] = v;
+  }
+}
+
+__global__ void k_identity(double* __restrict__ I, int n) {
+  long long total = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
+    I[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+inline int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 152LL * 32) g = 152LL * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int launch_permute_blocks(const double* src, const long long* src_blk, double* dst, long long nnzb, int np2s, void* st) {
+  k_permute_blocks<<<grid_for(nnzb * np2s, 256), 256, 0, (cudaStream_t)st>>>(src, src_blk, dst, nnzb, np2s);
+  return (int)cudaGetLastError();
+}
+
+int launch_scale(const int* rowptr, const int* col, const double* vals, int ne, int np, int np2s, double* scale, void* st) {
+  k_scale<<<grid_for((long long)ne * np, 256), 256, 0, (cudaStream_t)st>>>(rowptr, col, vals, ne, np, np2s, scale);
+  return (int)cudaGetLastError();
+}
+
+int launch_extract_rows(int prec, const EnvDev& E, const int* sub_e0, const int* rowptr, const int* col,
+                        const double* vals, int np, int np2s, const double* scale, void* Lr, int nsub, int ne, void* st) {
+  int blocks = (ne * 32 + 255) / 256;
+  if (prec == 0)
+    k_extract<double><<<blocks, 256, 0, (cudaStream_t)st>>>(E, sub_e0, rowptr, col, vals, np, np2s, scale, (double*)Lr, nsub);
+  else
+    k_extract<float><<<blocks, 256, 0, (cudaStream_t)st>>>(E, sub_e0, rowptr, col, vals, np, np2s, scale, (float*)Lr, nsub);
+  return (int)cudaGetLastError();
+}
+
+int launch_chol_step(int prec, const EnvDev& E, void* L, int K, const int* diag_task, int n_diag, const int* panel_task,
+                     int n_panel, const int* upd_task, int n_upd, int* err, void* st) {
+  cudaStream_t s = (cudaStream_t)st;
+  if (prec == 0) {
+    if (n_diag) k_chol_diag<double><<<n_diag, 256, 0, s>>>(E, (double*)L, K, diag_task, err);
+    if (n_panel) k_chol_panel<double><<<n_panel, 256, 0, s>>>(E, (double*)L, K, panel_task);
+    if (n_upd) k_chol_update<double><<<n_upd, 256, 0, s>>>(E, (double*)L, K, upd_task);
+  } else {
+    if (n_diag) k_chol_diag<float><<<n_diag, 256, 0, s>>>(E, (float*)L, K, diag_task, err);
+    if (n_panel) k_chol_panel<float><<<n_panel, 256, 0, s>>>(E, (float*)L, K, panel_task);
+    if (n_upd) k_chol_update<float><<<n_upd, 256, 0, s>>>(E, (float*)L, K, upd_task);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_to_colmajor(int prec, const void* Lr, void* Lc, long long ntiles, void* st) {
+  int g = (int)(ntiles < 152 * 16 ? ntiles : 152 * 16);
+  if (g < 1) g = 1;
+  if (prec == 0) k_to_colmajor<double><<<g, 256, 0, (cudaStream_t)st>>>((const double*)Lr, (double*)Lc, ntiles);
+  else k_to_colmajor<float><<<g, 256, 0, (cudaStream_t)st>>>((const float*)Lr, (float*)Lc, ntiles);
+  return (int)cudaGetLastError();
+}
+
+int launch_to_bf16(const float* src, void* dst, long long n, void* st) {
+  k_to_bf16<<<grid_for(n, 256), 256, 0, (cudaStream_t)st>>>(src, (__nv_bfloat16*)dst, n);
+  return (int)cudaGetLastError();
+}
+
+int launch_r0t(const int* perm, const double* xy, const int* pptr, const int* pvtx, const double* bbox, const int* agg_int,
+               const double* agg_bbox, int ne, int p, int q, const double* gl_t, const double* gl_w, int mq, double* r0t,
+               void* st) {
+  int np = (p + 1) * (p + 2) / 2, nq = (q + 1) * (q + 2) / 2;
+  size_t smem = sizeof(double) * (size_t)R0T_WARPS * (32 * np + 32 * nq + np * np + np * nq);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_r0t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  int blocks = (ne + R0T_WARPS - 1) / R0T_WARPS;
+  k_r0t<<<blocks, 32 * R0T_WARPS, smem, (cudaStream_t)st>>>(perm, xy, pptr, pvtx, bbox, agg_int, agg_bbox, ne, p, q, gl_t,
+                                                             gl_w, mq, r0t);
+  return (int)cudaGetLastError();
+}
+
+int launch_galerkin(const int* grp_ptr, const int* grp_elems, const int* agg_int, const int* rowptr, const int* col,
+                    const double* vals, const double* r0t, int nagg, int np, int np2s, int nq, double* A0, void* st) {
+  size_t smem = sizeof(double) * (size_t)np * nq;
+  k_galerkin<<<nagg, 32, smem, (cudaStream_t)st>>>(grp_ptr, grp_elems, agg_int, rowptr, col, vals, r0t, nagg, np, np2s,
+                                                    nq, A0);
+  return (int)cudaGetLastError();
+}
+
+int launch_coarse_extract(const double* A0, int n0, double* scale0, const EnvDev& E0, double* Lr0, void* st) {
+  k_coarse_scale<<<(n0 + 255) / 256, 256, 0, (cudaStream_t)st>>>(A0, n0, scale0);
+  int nbt = (n0 + T - 1) / T;
+  k_coarse_extract<<<grid_for((long long)nbt * T * nbt * T, 256), 256, 0, (cudaStream_t)st>>>(A0, n0, scale0, E0, Lr0);
+  return (int)cudaGetLastError();
+}
+
+int launch_identity(double* I, int n, void* st) {
+  k_identity<<<grid_for((long long)n * n, 256), 256, 0, (cudaStream_t)st>>>(I, n);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dgasm

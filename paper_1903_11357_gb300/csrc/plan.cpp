@@ -1,0 +1,271 @@
+// Plan construction: element renumbering (subdomain by subdomain, reverse Cuthill-McKee inside),
+// tile envelopes of the local Cholesky factors and their task lists.
+//
+// A Cholesky factor L of A_i has no entry left of the first nonzero of each row of A_i (fill stays
+// inside the row envelope), so storing the tiles (I, F(I)) .. (I, I), with F(I) the first tile
+// column touched by any row of tile row I, holds the exact dense factor.  Reverse Cuthill-McKee
+// keeps the envelope narrow for the planar element graphs of a subdomain.
+#include <algorithm>
+#include <numeric>
+#include <queue>
+
+#include "plan.h"
+
+namespace dgasm {
+
+void Envelope::build(const std::vector<std::vector<int>>& first_col) {
+  nsub = (int)first_col.size();
+  ndof.resize(nsub);
+  sub_trow.assign(nsub + 1, 0);
+  trow_F.clear();
+  trow_ptr.clear();
+  ntiles = 0;
+  max_nbt = 0;
+  std::vector<std::vector<int>> Fs(nsub);
+  for (int s = 0; s < nsub; ++s) {
+    int n = (int)first_col[s].size();
+    ndof[s] = n;
+    int nbt = (n + TILE - 1) / TILE;
+    max_nbt = std::max(max_nbt, nbt);
+    Fs[s].resize(nbt);
+    for (int I = 0; I < nbt; ++I) {
+      int F = I;
+      for (int r = I * TILE; r < std::min(n, (I + 1) * TILE); ++r) F = std::min(F, first_col[s][r] / TILE);
+      Fs[s][I] = F;
+      trow_F.push_back(F);
+      trow_ptr.push_back(ntiles);
+      ntiles += I - F + 1;
+    }
+    sub_trow[s + 1] = sub_trow[s] + nbt;
+  }
+  diag_off.assign(max_nbt + 1, 0);
+  panel_off.assign(max_nbt + 1, 0);
+  upd_off.assign(max_nbt + 1, 0);
+  diag_task.clear();
+  panel_task.clear();
+  upd_task.clear();
+  std::vector<int> S;
+  for (int K = 0; K < max_nbt; ++K) {
+    for (int s = 0; s < nsub; ++s) {
+      int nbt = (int)Fs[s].size();
+      if (K >= nbt) continue;
+      diag_task.push_back(s);
+      S.clear();
+      for (int I = K + 1; I < nbt; ++I)
+        if (Fs[s][I] <= K) S.push_back(I);
+      for (int I : S) { panel_task.push_back(s); panel_task.push_back(I); }
+      for (size_t a = 0; a < S.size(); ++a)
+        for (size_t b = 0; b <= a; ++b) {
+          upd_task.push_back(s);
+          upd_task.push_back(S[a]);
+          upd_task.push_back(S[b]);
+        }
+    }
+    diag_off[K + 1] = (int)diag_task.size();
+    panel_off[K + 1] = (int)(panel_task.size() / 2);
+    upd_off[K + 1] = (int)(upd_task.size() / 3);
+  }
+}
+
+namespace {
+
+// Reverse Cuthill-McKee of the element graph restricted to `elems` (caller ids); returns the order.
+std::vector<int> rcm_order(const std::vector<int>& elems, const std::vector<int>& rowptr, const std::vector<int>& col,
+                           const std::vector<int>& sub_of, int s) {
+  int n = (int)elems.size();
+  std::vector<int> local(n);
+  // map caller id -> local index via sorted lookup
+  std::vector<int> sorted(elems);
+  std::sort(sorted.begin(), sorted.end());
+  auto loc = [&](int e) { return (int)(std::lower_bound(sorted.begin(), sorted.end(), e) - sorted.begin()); };
+  std::vector<std::vector<int>> adj(n);
+  for (int i = 0; i < n; ++i) {
+    int e = sorted[i];
+    for (int k = rowptr[e]; k < rowptr[e + 1]; ++k) {
+      int c = col[k];
+      if (c != e && sub_of[c] == s) adj[i].push_back(loc(c));
+    }
+  }
+  std::vector<int> deg(n);
+  for (int i = 0; i < n; ++i) deg[i] = (int)adj[i].size();
+  auto bfs = [&](int root, std::vector<int>& order, std::vector<int>& level) {
+    order.clear();
+    level.assign(n, -1);
+    std::vector<int> q{root};
+    level[root] = 0;
+    size_t h = 0;
+    while (h < q.size()) {
+      int u = q[h++];
+      order.push_back(u);
+      std::vector<int> nb;
+      for (int v : adj[u]) if (level[v] < 0) { level[v] = level[u] + 1; nb.push_back(v); }
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+      for (int v : nb) q.push_back(v);
+    }
+  };
+  std::vector<int> order, level, visited(n, 0), result;
+  result.reserve(n);
+  for (int start = 0; start < n; ++start) {
+    if (visited[start]) continue;
+    // pseudo-peripheral root of this component (George-Liu iteration)
+    int root = start;
+    int best_depth = -1;
+    for (int it = 0; it < 8; ++it) {
+      bfs(root, order, level);
+      int depth = level[order.back()];
+      if (depth <= best_depth) break;
+      best_depth = depth;
+      int cand = order.back();
+      for (int u : order) if (level[u] == depth && deg[u] < deg[cand]) cand = u;
+      root = cand;
+    }
+    bfs(root, order, level);
+    for (int u : order) { visited[u] = 1; result.push_back(u); }
+  }
+  std::reverse(result.begin(), result.end());
+  std::vector<int> out(n);
+  for (int i = 0; i < n; ++i) out[i] = sorted[result[i]];
+  return out;
+}
+
+}  // namespace
+
+int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const int* sub_in, const int* agg_in, Plan& P) {
+  const MeshData& m = sys.mesh->m;
+  const int ne = m.ne, np = sys.np;
+  P.ne = ne;
+  P.np = np;
+  // partition
+  if (sub_in) {
+    P.sub_of.assign(sub_in, sub_in + ne);
+    int mx = 0;
+    for (int e = 0; e < ne; ++e) {
+      if (P.sub_of[e] < 0) return set_error(DGASM_EINVAL, "sub_of_elem[%d] is negative", e);
+      mx = std::max(mx, P.sub_of[e]);
+    }
+    nsub = mx + 1;
+    std::vector<int> cnt(nsub, 0);
+    for (int e = 0; e < ne; ++e) cnt[P.sub_of[e]]++;
+    for (int s = 0; s < nsub; ++s) if (!cnt[s]) return set_error(DGASM_EINVAL, "subdomain %d is empty", s);
+  } else {
+    DG_TRY(compute_partition(m, nsub, 0, P.sub_of, nullptr));
+  }
+  P.nsub = nsub;
+  P.q = q;
+  P.nq = ncoarse > 0 || agg_in ? n_basis(q) : 0;
+  if (agg_in) {
+    P.agg_of.assign(agg_in, agg_in + ne);
+    int mx = 0;
+    for (int e = 0; e < ne; ++e) {
+      if (P.agg_of[e] < 0) return set_error(DGASM_EINVAL, "agg_of_elem[%d] is negative", e);
+      mx = std::max(mx, P.agg_of[e]);
+    }
+    P.nagg = mx + 1;
+  } else if (ncoarse > 0) {
+    if (ncoarse > ne) return set_error(DGASM_EINVAL, "ncoarse=%d exceeds the element count", ncoarse);
+    P.agg_of.assign(ne, 0);
+    if (ncoarse >= nsub) {
+      std::vector<std::vector<int>> members(nsub);
+      for (int e = 0; e < ne; ++e) members[P.sub_of[e]].push_back(e);
+      int next = 0;
+      for (int i = 0; i < nsub; ++i) {
+        int ci = (int)(((long long)(i + 1) * ncoarse) / nsub - ((long long)i * ncoarse) / nsub);
+        if (ci < 1 || (size_t)ci > members[i].size())
+          return set_error(DGASM_EINVAL, "subdomain %d cannot hold %d agglomerates", i, ci);
+        rcb_parts(m, members[i], ci, P.agg_of, next);
+        next += ci;
+      }
+    } else {
+      std::vector<int> all(ne);
+      std::iota(all.begin(), all.end(), 0);
+      rcb_parts(m, all, ncoarse, P.agg_of, 0);
+    }
+    P.nagg = ncoarse;
+  } else {
+    P.nagg = 0;
+  }
+  if (P.nagg > 0) {
+    std::vector<int> cnt(P.nagg, 0);
+    for (int e = 0; e < ne; ++e) cnt[P.agg_of[e]]++;
+    for (int j = 0; j < P.nagg; ++j) if (!cnt[j]) return set_error(DGASM_EINVAL, "agglomerate %d is empty", j);
+  }
+  // internal order: subdomain by subdomain, RCM inside
+  std::vector<std::vector<int>> members(nsub);
+  for (int e = 0; e < ne; ++e) members[P.sub_of[e]].push_back(e);
+  P.perm.clear();
+  P.sub_e0.assign(nsub + 1, 0);
+  for (int s = 0; s < nsub; ++s) {
+    std::vector<int> ord = rcm_order(members[s], sys.rowptr, sys.col, P.sub_of, s);
+    P.perm.insert(P.perm.end(), ord.begin(), ord.end());
+    P.sub_e0[s + 1] = (int)P.perm.size();
+  }
+  P.iperm.assign(ne, 0);
+  for (int i = 0; i < ne; ++i) P.iperm[P.perm[i]] = i;
+  // permuted CSR (columns ascending in internal ids)
+  P.rowptr.assign(ne + 1, 0);
+  P.col.clear();
+  P.src_blk.clear();
+  std::vector<std::pair<int, int>> row;
+  for (int i = 0; i < ne; ++i) {
+    int e = P.perm[i];
+    row.clear();
+    for (int k = sys.rowptr[e]; k < sys.rowptr[e + 1]; ++k) row.push_back({P.iperm[sys.col[k]], k});
+    std::sort(row.begin(), row.end());
+    for (auto& c : row) { P.col.push_back(c.first); P.src_blk.push_back(c.second); }
+    P.rowptr[i + 1] = (int)P.col.size();
+  }
+  // envelopes: first column of each local dof row
+  std::vector<std::vector<int>> fc(nsub);
+  for (int s = 0; s < nsub; ++s) {
+    int e0 = P.sub_e0[s], e1 = P.sub_e0[s + 1];
+    fc[s].resize((size_t)(e1 - e0) * np);
+    for (int i = e0; i < e1; ++i) {
+      int first = i - e0;
+      for (int k = P.rowptr[i]; k < P.rowptr[i + 1]; ++k) {
+        int c = P.col[k];
+        if (c >= e0 && c < e1) first = std::min(first, c - e0);
+      }
+      for (int a = 0; a < np; ++a) fc[s][(size_t)(i - e0) * np + a] = first * np;
+    }
+  }
+  P.env.build(fc);
+  // groups and coarse data
+  P.agg_int.assign(ne, -1);
+  P.grp_ptr.assign(1, 0);
+  P.grp_elems.clear();
+  if (P.nagg > 0) {
+    std::vector<std::vector<int>> mem(P.nagg);
+    for (int i = 0; i < ne; ++i) { P.agg_int[i] = P.agg_of[P.perm[i]]; mem[P.agg_int[i]].push_back(i); }
+    for (int j = 0; j < P.nagg; ++j) {
+      P.grp_elems.insert(P.grp_elems.end(), mem[j].begin(), mem[j].end());
+      P.grp_ptr.push_back((int)P.grp_elems.size());
+    }
+    P.ngrp = P.nagg;
+    P.agg_bbox.assign(4 * (size_t)P.nagg, 0.0);
+    for (int j = 0; j < P.nagg; ++j) {
+      P.agg_bbox[4 * j] = 1e300; P.agg_bbox[4 * j + 1] = -1e300;
+      P.agg_bbox[4 * j + 2] = 1e300; P.agg_bbox[4 * j + 3] = -1e300;
+    }
+    for (int e = 0; e < ne; ++e) {
+      int j = P.agg_of[e];
+      const double* b = &m.bbox[4 * (size_t)e];
+      P.agg_bbox[4 * j] = std::min(P.agg_bbox[4 * j], b[0]);
+      P.agg_bbox[4 * j + 1] = std::max(P.agg_bbox[4 * j + 1], b[1]);
+      P.agg_bbox[4 * j + 2] = std::min(P.agg_bbox[4 * j + 2], b[2]);
+      P.agg_bbox[4 * j + 3] = std::max(P.agg_bbox[4 * j + 3], b[3]);
+    }
+    int n0 = P.nagg * P.nq;
+    std::vector<std::vector<int>> fc0(1, std::vector<int>(n0, 0));
+    P.env0.build(fc0);
+  } else {
+    const int G = 64;
+    for (int i = 0; i < ne; i += G) {
+      for (int k = i; k < std::min(ne, i + G); ++k) P.grp_elems.push_back(k);
+      P.grp_ptr.push_back((int)P.grp_elems.size());
+    }
+    P.ngrp = (int)P.grp_ptr.size() - 1;
+  }
+  return DGASM_OK;
+}
+
+}  // namespace dgasm

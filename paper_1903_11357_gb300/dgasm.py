@@ -1,0 +1,296 @@
+"""ctypes binding of the dgasm C-ABI (include/dgasm.h): argument marshalling only.
+
+Every numerical step runs inside libdgasm.so.  Device arrays are passed as torch CUDA tensors
+(their data pointers); host arrays as numpy arrays.  If the shared library has not been built,
+``lib()`` raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdgasm.so")
+
+OK, PENDING = 0, 1
+EINVAL, ENOMEM, ENOTSPD, ENOCONV, ENAN, ECUDA, ETIMEOUT, ETOOBIG, ECANCELLED, ENOTFOUND = range(-1, -11, -1)
+FP64, FP32, TF32, BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+
+RHS_FN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+
+
+class SetupOpts(C.Structure):
+    _fields_ = [("nsub", C.c_int), ("ncoarse", C.c_int), ("p_c", C.c_int),
+                ("sub_of_elem", C.POINTER(C.c_int)), ("agg_of_elem", C.POINTER(C.c_int)),
+                ("precision", C.c_int), ("stream", C.c_void_p)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("maxit", C.c_int), ("fixed_iters", C.c_int), ("x0_given", C.c_int),
+                ("host_buffers", C.c_int), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres", C.c_double), ("true_relres", C.c_double),
+                ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("kappa", C.c_double),
+                ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class DgasmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dgasm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libdgasm.so; raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdgasm.so is missing ({LIB_PATH}); build it with "
+                               "`python -m paper_1903_11357_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, ip, dp, i64p = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int64)
+        sig = {
+            "dgasm_last_error": [C.c_char_p, C.c_size_t],
+            "dgasm_mesh_create": [C.c_int, dp, C.c_int, ip, ip, dp, C.POINTER(vp)],
+            "dgasm_mesh_info": [vp, ip, ip, ip],
+            "dgasm_mesh_centroids": [vp, dp],
+            "dgasm_mesh_destroy": [vp],
+            "dgasm_partition": [vp, C.c_int, C.c_int, ip, ip],
+            "dgasm_assemble": [vp, C.c_int, C.c_double, RHS_FN, vp, C.POINTER(vp)],
+            "dgasm_system_dofs": [vp, i64p, ip],
+            "dgasm_system_rhs": [vp, dp],
+            "dgasm_system_blocks": [vp, i64p, ip, ip, dp],
+            "dgasm_system_spmv": [vp, vp, vp, vp],
+            "dgasm_system_destroy": [vp],
+            "dgasm_setup": [vp, C.POINTER(SetupOpts), C.POINTER(vp)],
+            "dgasm_prec_apply": [vp, C.c_int, vp, vp, vp],
+            "dgasm_prec_partition": [vp, ip, ip],
+            "dgasm_prec_footprint": [vp, i64p],
+            "dgasm_prec_destroy": [vp],
+            "dgasm_solve": [vp, C.c_int, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats)],
+            "dgasm_solve_batch": [C.c_int, C.POINTER(vp), ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
+                                  C.POINTER(Stats)],
+            "dgasm_lanczos": [C.c_int, dp, dp, dp, dp],
+            "dgasm_set_allocator": [vp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the entry points declared in include/dgasm.h."""
+    import re
+    with open(os.path.join(os.path.dirname(_HERE), "include", "dgasm.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\bint\s+(dgasm_\w+)\s*\(", text)))
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(512)
+    lib().dgasm_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def check(code):
+    if code < 0:
+        raise DgasmError(code, last_error())
+    return code
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _dev_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    def __init__(self, xy, poly_ptr, poly_vtx, rho):
+        self._xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+        ptr = np.ascontiguousarray(poly_ptr, dtype=np.int32)
+        vtx = np.ascontiguousarray(poly_vtx, dtype=np.int32)
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        self.ne = len(ptr) - 1
+        h = C.c_void_p()
+        check(lib().dgasm_mesh_create(len(self._xy) // 2, _dp(self._xy), self.ne, _ip(ptr), _ip(vtx), _dp(rho),
+                                      C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_polymesh(cls, m, rho):
+        return cls(m.xy, m.poly_ptr, m.poly_vtx, rho)
+
+    def info(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        check(lib().dgasm_mesh_info(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def centroids(self):
+        out = np.empty(2 * self.ne)
+        check(lib().dgasm_mesh_centroids(self.h, _dp(out)))
+        return out.reshape(-1, 2)
+
+    def partition(self, nsub, ncoarse=0):
+        sub = np.empty(self.ne, np.int32)
+        agg = np.empty(self.ne, np.int32)
+        check(lib().dgasm_partition(self.h, nsub, ncoarse, _ip(sub), _ip(agg)))
+        return sub, (agg if ncoarse > 0 else None)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dgasm_mesh_destroy(self.h)
+            self.h = None
+
+
+class System:
+    def __init__(self, mesh: Mesh, p: int, c_sigma: float = 10.0, f=None):
+        self.mesh = mesh  # keeps the mesh alive
+        self.p = p
+        h = C.c_void_p()
+        cb = RHS_FN()
+        if f is not None:
+            def _cb(n, xy, out, user):
+                pts = np.ctypeslib.as_array(xy, shape=(n, 2))
+                o = np.ctypeslib.as_array(out, shape=(n,))
+                o[:] = f(pts)
+            cb = RHS_FN(_cb)
+        self._cb = cb
+        check(lib().dgasm_assemble(mesh.h, p, c_sigma, cb, None, C.byref(h)))
+        self.h = h
+        n = C.c_int64()
+        npb = C.c_int()
+        check(lib().dgasm_system_dofs(h, C.byref(n), C.byref(npb)))
+        self.ndof, self.np = n.value, npb.value
+
+    def rhs(self):
+        b = np.empty(self.ndof)
+        check(lib().dgasm_system_rhs(self.h, _dp(b)))
+        return b
+
+    def blocks(self):
+        nnzb = C.c_int64()
+        check(lib().dgasm_system_blocks(self.h, C.byref(nnzb), None, None, None))
+        rowptr = np.empty(self.mesh.ne + 1, np.int32)
+        col = np.empty(nnzb.value, np.int32)
+        vals = np.empty(nnzb.value * self.np * self.np)
+        check(lib().dgasm_system_blocks(self.h, C.byref(nnzb), _ip(rowptr), _ip(col), _dp(vals)))
+        return rowptr, col, vals.reshape(-1, self.np, self.np)
+
+    def spmv(self, x, y, stream=None):
+        check(lib().dgasm_system_spmv(self.h, _dev_ptr(x), _dev_ptr(y), _stream_ptr(stream)))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dgasm_system_destroy(self.h)
+            self.h = None
+
+
+class Prec:
+    def __init__(self, system: System, nsub: int, ncoarse: int, p_c: int = 1, precision="fp64", sub_of_elem=None,
+                 agg_of_elem=None, stream=None):
+        self.system = system
+        o = SetupOpts()
+        o.nsub, o.ncoarse, o.p_c = nsub, ncoarse, p_c
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._sub = self._agg = None
+        if sub_of_elem is not None:
+            self._sub = np.ascontiguousarray(sub_of_elem, np.int32)
+            o.sub_of_elem = _ip(self._sub)
+        if agg_of_elem is not None:
+            self._agg = np.ascontiguousarray(agg_of_elem, np.int32)
+            o.agg_of_elem = _ip(self._agg)
+        o.stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        check(lib().dgasm_setup(system.h, C.byref(o), C.byref(h)))
+        self.h = h
+        self.ndof = system.ndof
+
+    def apply(self, r, z, stream=None):
+        k = 1 if r.dim() == 1 else r.shape[0]
+        check(lib().dgasm_prec_apply(self.h, k, _dev_ptr(r), _dev_ptr(z), _stream_ptr(stream)))
+
+    def partition(self):
+        ne = self.system.mesh.ne
+        sub = np.empty(ne, np.int32)
+        agg = np.full(ne, -1, np.int32)
+        check(lib().dgasm_prec_partition(self.h, _ip(sub), _ip(agg)))
+        return sub, agg
+
+    def footprint(self):
+        b = C.c_int64()
+        check(lib().dgasm_prec_footprint(self.h, C.byref(b)))
+        return b.value
+
+    def solve(self, b, x, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None, host_buffers=False):
+        """b, x: (k, ndof) or (ndof,) float64 CUDA tensors (numpy arrays if host_buffers).  Returns
+        (return code, [stats dict per right-hand side])."""
+        o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=0,
+                      host_buffers=1 if host_buffers else 0, stream=_stream_ptr(stream))
+        if host_buffers:
+            k = 1 if b.ndim == 1 else b.shape[0]
+            bp, xp = C.c_void_p(b.ctypes.data), C.c_void_p(x.ctypes.data)
+        else:
+            k = 1 if b.dim() == 1 else b.shape[0]
+            bp, xp = _dev_ptr(b), _dev_ptr(x)
+        st = (Stats * k)()
+        rc = lib().dgasm_solve(self.h, k, bp, xp, C.byref(o), st)
+        if rc < 0 and rc != ENOCONV:
+            check(rc)
+        return rc, [s.as_dict() for s in st]
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dgasm_prec_destroy(self.h)
+            self.h = None
+
+
+def solve_batch(precs, bs, xs, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None):
+    n = len(precs)
+    hs = (C.c_void_p * n)(*[p.h.value for p in precs])
+    ks = np.array([1 if b.dim() == 1 else b.shape[0] for b in bs], np.int32)
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=0, host_buffers=0,
+                  stream=_stream_ptr(stream))
+    st = (Stats * int(ks.sum()))()
+    rc = lib().dgasm_solve_batch(n, hs, _ip(ks), bp, xp, C.byref(o), st)
+    if rc < 0 and rc != ENOCONV:
+        check(rc)
+    return rc, [s.as_dict() for s in st]
+
+
+def lanczos(alphas, betas):
+    a = np.ascontiguousarray(alphas, np.float64)
+    b = np.ascontiguousarray(betas if len(betas) else [0.0], np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    check(lib().dgasm_lanczos(len(a), _dp(a), _dp(b), C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value

@@ -1,0 +1,137 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerances: FP64 mode solutions agree with the oracle to a relative L2 difference of 1e-10 when both
+run the same number of iterations, and iteration counts under the 1e-8 stop test agree within +-1.
+Operator-level checks (SpMV, preconditioner application) agree to 1e-12 relative: both sides compute
+the same sums of products of the same FP64 numbers in different orders.
+"""
+import numpy as np
+import pytest
+
+from oracle import partition, pcg, schwarz, sipg
+from oracle.geometry import build_geometry
+from synth.coeff import checker_per_subdomain
+from tests.helpers import f_sin, have_gpu, mesh
+
+pytestmark = pytest.mark.gpu
+
+if have_gpu():
+    import torch
+    from paper_1903_11357_gb300 import dgasm as dg
+
+
+def build_case(n, seed, p, nsub, ncoarse, q=1, contrast=1.0, precision="fp64"):
+    m = mesh(n, seed)
+    M0 = dg.Mesh.from_polymesh(m, np.ones(n))
+    sub, _ = M0.partition(nsub, 0)
+    rho = checker_per_subdomain(m, sub, contrast) if contrast != 1.0 else np.ones(n)
+    M = dg.Mesh.from_polymesh(m, rho)
+    S = dg.System(M, p, 10.0, f=f_sin)
+    P = dg.Prec(S, nsub, ncoarse, q, precision=precision)
+    A, b, g = sipg.assemble(m, rho, p, 10.0, f_sin)
+    osub = partition.subdomains(g.centroid, nsub)
+    oagg = partition.agglomerates(g.centroid, osub, nsub, ncoarse) if ncoarse else None
+    O = schwarz.build(A, m, g, p, osub, oagg, q)
+    return dict(m=m, M=M, S=S, P=P, A=A, b=b, O=O, rho=rho)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("n,p", [(256, 2), (600, 3)])
+def test_spmv_matches_oracle(n, p):
+    c = build_case(n, 3, p, 4, 0)
+    x = np.random.default_rng(0).standard_normal(c["A"].shape[0])
+    y = torch.zeros_like(dev(x))
+    c["S"].spmv(dev(x), y)
+    torch.cuda.synchronize()
+    ref = c["A"] @ x
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,p,nsub,ncoarse,q", [(256, 2, 4, 16, 1), (600, 3, 8, 32, 1), (300, 2, 5, 0, 1),
+                                                 (400, 3, 4, 16, 2), (150, 1, 1, 0, 1)])
+def test_preconditioner_apply_matches_oracle(n, p, nsub, ncoarse, q):
+    c = build_case(n, 7, p, nsub, ncoarse, q)
+    r = np.random.default_rng(1).standard_normal(c["A"].shape[0])
+    z = torch.zeros_like(dev(r))
+    c["P"].apply(dev(r), z)
+    torch.cuda.synchronize()
+    ref = c["O"].apply(r)
+    assert np.linalg.norm(z.cpu().numpy() - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_partition_used_matches_oracle():
+    c = build_case(256, 1, 2, 4, 16)
+    sub, agg = c["P"].partition()
+    g = build_geometry(c["m"])
+    osub = partition.subdomains(g.centroid, 4)
+    assert np.array_equal(sub, osub)
+    assert np.array_equal(agg, partition.agglomerates(g.centroid, osub, 4, 16))
+
+
+@pytest.mark.parametrize("contrast", [1.0, 1e4])
+def test_cfg1_solve_parity_fp64(contrast):
+    """256 Voronoi cells, p = 2, 4 RCB subdomains, 16 agglomerates at q = 1 (the small configuration)."""
+    c = build_case(256, 1, 2, 4, 16, 1, contrast)
+    ref = pcg.pcg(c["A"], c["b"], c["O"].apply, rtol=1e-8)
+    x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
+    rc, st = c["P"].solve(dev(c["b"]), x, rtol=1e-8)
+    assert rc == 0 and st[0]["converged"]
+    assert abs(st[0]["iters"] - ref.iters) <= 1
+    assert st[0]["true_relres"] <= 1.1e-8
+    # equal iteration counts: solutions agree to 1e-10
+    rc, st2 = c["P"].solve(dev(c["b"]), x, fixed_iters=ref.iters)
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(xr - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    assert st2[0]["iters"] == ref.iters
+    K = pcg.condition_estimate(ref)
+    assert st[0]["kappa"] == pytest.approx(K, rel=0.05)
+
+
+def test_multi_rhs_equals_single():
+    c = build_case(300, 4, 2, 4, 16)
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((3, len(c["b"])))
+    X = torch.zeros(3, len(c["b"]), dtype=torch.float64, device="cuda")
+    rc, st = c["P"].solve(dev(B), X, rtol=1e-8)
+    assert rc == 0 and len(st) == 3
+    for j in range(3):
+        x1 = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
+        c["P"].solve(dev(B[j]), x1, rtol=1e-8)
+        assert torch.equal(x1, X[j])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_mixed_precision_reaches_tolerance(precision):
+    c = build_case(256, 1, 2, 4, 16, 1, 1e4, precision=precision)
+    x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
+    rc, st = c["P"].solve(dev(c["b"]), x, rtol=1e-8)
+    assert rc == 0 and st[0]["converged"] and st[0]["true_relres"] <= 2e-8
+    xs = np.linalg.solve(c["A"].toarray(), c["b"])
+    assert np.linalg.norm(x.cpu().numpy() - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+def test_zero_rhs_and_one_subdomain():
+    c = build_case(200, 2, 2, 1, 0)
+    x = torch.ones(len(c["b"]), dtype=torch.float64, device="cuda")
+    rc, st = c["P"].solve(torch.zeros_like(x), x)
+    assert rc == 0 and st[0]["iters"] == 0 and float(x.abs().max()) == 0.0
+    rc, st = c["P"].solve(dev(c["b"]), x)
+    assert st[0]["iters"] == 1 and st[0]["true_relres"] < 1e-10
+
+
+def test_batch_equals_alone():
+    cases = [build_case(256, 1, 2, 4, 16), build_case(300, 2, 3, 4, 8), build_case(200, 3, 1, 2, 8)]
+    xs_alone = []
+    for c in cases:
+        x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
+        c["P"].solve(dev(c["b"]), x)
+        xs_alone.append(x)
+    bs = [dev(c["b"]) for c in cases]
+    xs = [torch.zeros_like(b) for b in bs]
+    rc, st = dg.solve_batch([c["P"] for c in cases], bs, xs)
+    assert rc == 0
+    for a, b in zip(xs_alone, xs):
+        assert torch.equal(a, b)

@@ -1,0 +1,102 @@
+"""Host-side checks of libdgasm.so (no GPU): it loads, exports every entry point of include/dgasm.h,
+validates meshes, and its partition and SIPG assembly agree with the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import partition, pcg, sipg
+from paper_1903_11357_gb300 import dgasm as dg
+from synth.coeff import checker_per_subdomain
+from synth.voronoi import PolyMesh, quad_mesh
+from tests.helpers import f_sin, mesh
+
+
+def test_library_loads_and_exports_header_symbols():
+    L = dg.lib()
+    names = dg.exported_symbols()
+    assert "dgasm_solve" in names and "dgasm_setup" in names and "dgasm_submit" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_mesh_validation_errors():
+    sq = quad_mesh(1)
+    with pytest.raises(dg.DgasmError) as e:
+        dg.Mesh(sq.xy, sq.poly_ptr, sq.poly_vtx[::-1].copy(), [1.0])
+    assert e.value.code == dg.EINVAL and "area" in str(e.value)
+    with pytest.raises(dg.DgasmError):
+        dg.Mesh(sq.xy, sq.poly_ptr, sq.poly_vtx, [0.0])
+    with pytest.raises(dg.DgasmError):
+        dg.Mesh(sq.xy, sq.poly_ptr, np.array([0, 1, 3, 7], np.int32), [1.0])
+    bad = PolyMesh(xy=np.array([[0, 0], [1, 0], [0, 1.0]]), poly_ptr=np.array([0, 2], np.int32),
+                   poly_vtx=np.array([0, 1], np.int32))
+    with pytest.raises(dg.DgasmError):
+        dg.Mesh(bad.xy, bad.poly_ptr, bad.poly_vtx, [1.0])
+
+
+def test_faces_counted():
+    m = mesh(200, 3)
+    M = dg.Mesh.from_polymesh(m, np.ones(200))
+    ne, nfi, nfb = M.info()
+    from oracle.geometry import build_geometry
+    g = build_geometry(m)
+    assert ne == 200 and nfi == sum(1 for f in g.faces if f[1] >= 0) and nfb == sum(1 for f in g.faces if f[1] < 0)
+
+
+@pytest.mark.parametrize("n,nsub,ncoarse", [(256, 4, 16), (300, 7, 20), (500, 16, 5), (1024, 4, 64), (64, 64, 8)])
+def test_partition_matches_oracle(n, nsub, ncoarse):
+    m = mesh(n, n)
+    M = dg.Mesh.from_polymesh(m, np.ones(n))
+    sub, agg = M.partition(nsub, ncoarse)
+    from oracle.geometry import build_geometry
+    g = build_geometry(m)
+    assert np.array_equal(M.centroids(), g.centroid)
+    osub = partition.subdomains(g.centroid, nsub)
+    assert np.array_equal(sub, osub)
+    assert np.array_equal(agg, partition.agglomerates(g.centroid, osub, nsub, ncoarse))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_assembly_matches_oracle(p):
+    m = mesh(96, 5)
+    sub, _ = dg.Mesh.from_polymesh(m, np.ones(96)).partition(6, 0)
+    rho = checker_per_subdomain(m, sub, 1e4)
+    M = dg.Mesh.from_polymesh(m, rho)
+    S = dg.System(M, p, 10.0, f=f_sin)
+    A, b, _ = sipg.assemble(m, rho, p, 10.0, f_sin)
+    rowptr, col, vals = S.blocks()
+    npb = S.np
+    Ad = A.toarray()
+    L = np.zeros_like(Ad)
+    for e in range(96):
+        for k in range(rowptr[e], rowptr[e + 1]):
+            L[e * npb:(e + 1) * npb, col[k] * npb:(col[k] + 1) * npb] = vals[k]
+    assert np.abs(L - Ad).max() <= 1e-13 * np.abs(Ad).max()
+    assert np.abs(S.rhs() - b).max() <= 1e-13 * np.abs(b).max()
+
+
+def test_assemble_rejects_bad_degree():
+    m = mesh(16, 1)
+    M = dg.Mesh.from_polymesh(m, np.ones(16))
+    with pytest.raises(dg.DgasmError):
+        dg.System(M, 0)
+    with pytest.raises(dg.DgasmError):
+        dg.System(M, 9)
+
+
+def test_lanczos_matches_oracle():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((30, 30))
+    A = A @ A.T + 30 * np.eye(30)
+    res = pcg.pcg(A, rng.standard_normal(30), lambda r: r.copy(), rtol=1e-12)
+    lo_o, hi_o = pcg.lanczos_extremes(res.alphas, res.betas[:len(res.alphas) - 1])
+    lo, hi = dg.lanczos(res.alphas, res.betas[:len(res.alphas) - 1])
+    assert lo == pytest.approx(lo_o, rel=1e-10) and hi == pytest.approx(hi_o, rel=1e-10)
+
+
+def test_last_error_roundtrip():
+    buf = ctypes.create_string_buffer(64)
+    dg.lib().dgasm_partition(None, 1, 0, None, None)
+    assert dg.lib().dgasm_last_error(buf, 64) == dg.EINVAL
+    assert b"NULL" in buf.value
