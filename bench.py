@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: ASPCG (SIPG + two-level additive Schwarz PCG) time to a 1e-8 relative residual and solves
+per second on one GB300, on the 16384-cell Lloyd-Voronoi workload at p = 3 (163840 dofs, 64 RCB
+subdomains, 256 agglomerates at p_c = 1, checkerboard coefficient 1e4 aligned to the subdomains).
+
+One step = one complete solve through the C-ABI: dgasm_setup (extraction and tile Cholesky of the 64
+local matrices, coarse transfer, Galerkin A_0, its factor and inverse) followed by dgasm_solve to 1e-8
+(SpMV, local solves, coarse correction, fused vector updates, stop test, true residual, Lanczos
+estimate).  The assembled SIPG system is resident in HBM before timing starts.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgasm|reference]
+Under torchrun each rank runs an independent replica on its own GPU (the method has no exchange step
+on one GPU): weak scaling, value = solves of all ranks / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 rel. residual & solves/s vs FP64 plain PCG; p50/p99 latency"
+N_ELEM, SEED, P_DEG, NSUB, NCOARSE, P_C, CONTRAST = 16384, 2, 3, 64, 256, 1, 1e4
+WORKLOAD = ("16384 Lloyd-relaxed Voronoi cells of (0,1)^2 (seed 2, 20 Lloyd steps), SIPG p=3 (163840 dofs), "
+            "C_sigma=10, 64 RCB subdomains (~2560 dofs), 256 RCB agglomerates at p_c=1, rho=1e4 on a 4x4 "
+            "checkerboard of subdomains; f = 2 pi^2 sin(pi x) sin(pi y); rtol 1e-8 from x0=0")
+FP64_PEAK_FLOPS_PER_CLK = 152 * 2 * 2   # 152 SMs x 2 DFMA/clk (measured issue rate) x 2 flop
+
+
+def f_sin(X):
+    return 2 * np.pi ** 2 * np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])
+
+
+def build_problem():
+    from synth.coeff import checker_per_subdomain
+    from synth.voronoi import voronoi_mesh
+    from paper_1903_11357_gb300 import dgasm as dg
+    m = voronoi_mesh(N_ELEM, SEED)
+    sub, _ = dg.Mesh.from_polymesh(m, np.ones(m.n_elem)).partition(NSUB, 0)
+    rho = checker_per_subdomain(m, sub, CONTRAST)
+    M = dg.Mesh.from_polymesh(m, rho)
+    S = dg.System(M, P_DEG, 10.0, f=f_sin)
+    return m, rho, M, S
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_prep(m, rho):
+    """Untimed preparation for the CPU baseline: the oracle's SIPG assembly and partitions, and the full
+    coarse transfer (needed by the sampled PCG iterations)."""
+    import scipy.sparse as sp
+
+    from oracle import partition, schwarz, sipg
+    A, b, g = sipg.assemble(m, rho, P_DEG, 10.0, f_sin)
+    sub = partition.subdomains(g.centroid, NSUB)
+    agg = partition.agglomerates(g.centroid, sub, NSUB, NCOARSE)
+    nb = (P_DEG + 1) * (P_DEG + 2) // 2
+    R0T = schwarz.prolongation(m, g, agg, P_DEG, P_C)
+    return {"m": m, "A": sp.csr_matrix(A), "b": b, "g": g, "agg": agg, "dofs": schwarz.local_dof_sets(sub, nb),
+            "R0T": R0T}
+
+
+def oracle_sample(prep, gpu_iters, sample_subdomains=4, sample_elems=1024, sample_iters=3):
+    """The CPU oracle timed on a bounded sample of the workload, scaled to one solve:
+    local Cholesky of `sample_subdomains` of the 64 subdomain matrices (x 64 / sample), the L2
+    prolongation on the first `sample_elems` elements (x ne / sample), the Galerkin product A_0 and its
+    Cholesky (full), and `sample_iters` PCG iterations (x the GPU's iteration count)."""
+    from oracle import pcg, schwarz
+    from synth.voronoi import PolyMesh
+    A, b, m, g, agg, dofs, R0T = (prep[k] for k in ("A", "b", "m", "g", "agg", "dofs", "R0T"))
+    t0 = time.perf_counter()
+    chol = [np.linalg.cholesky(A[idx][:, idx].toarray()) for idx in dofs[:sample_subdomains]]
+    t_local = (time.perf_counter() - t0) * NSUB / sample_subdomains
+    ne = m.n_elem
+    sub_mesh = PolyMesh(xy=m.xy, poly_ptr=m.poly_ptr[:sample_elems + 1], poly_vtx=m.poly_vtx)
+    t0 = time.perf_counter()
+    schwarz.prolongation(sub_mesh, g, agg[:sample_elems], P_DEG, P_C)
+    t_r0t = (time.perf_counter() - t0) * ne / sample_elems
+    t0 = time.perf_counter()
+    A0 = (R0T.T @ (A @ R0T)).toarray()
+    A0 = 0.5 * (A0 + A0.T)
+    L0 = np.linalg.cholesky(A0)
+    t_a0 = time.perf_counter() - t0
+    # the iterations reuse the sampled factors cyclically: same sizes, so the same cost per apply
+    S = schwarz.Schwarz(local_dofs=dofs, local_chol=[chol[i % len(chol)] for i in range(NSUB)], R0T=R0T, A0=A0,
+                        A0_chol=L0)
+    t0 = time.perf_counter()
+    pcg.pcg(A, b, S.apply, fixed_iters=sample_iters)
+    t_iter = (time.perf_counter() - t0) / sample_iters
+    t_solve = t_local + t_r0t + t_a0 + t_iter * gpu_iters
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "seconds_per_solve": t_solve,
+            "sample": (f"numpy/scipy oracle on this workload, scaled to one solve: dense Cholesky of "
+                       f"{sample_subdomains}/{NSUB} subdomain matrices (x{NSUB / sample_subdomains:g}), L2 prolongation "
+                       f"of {sample_elems}/{ne} elements (x{ne / sample_elems:g}), full A_0 product and Cholesky, "
+                       f"{sample_iters} PCG iterations (x{gpu_iters / sample_iters:g} for the GPU's {gpu_iters}); "
+                       f"assembly untimed; BLAS threads = library default on {cores} cores")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from synth.coeff import checker_per_subdomain
+    from synth.voronoi import voronoi_mesh
+    from oracle import partition
+    from oracle.geometry import build_geometry
+    m = voronoi_mesh(N_ELEM, SEED)
+    g = build_geometry(m)
+    sub = partition.subdomains(g.centroid, NSUB)
+    rho = checker_per_subdomain(m, sub, CONTRAST)
+    prep = oracle_prep(m, rho)
+    vals = []
+    last = None
+    for step in range(args.warmup + args.steps):
+        last = oracle_sample(prep, args.ref_iters, sample_subdomains=2, sample_elems=256, sample_iters=1)
+        if step >= args.warmup:
+            vals.append(last["seconds_per_solve"])
+    t = statistics.mean(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "solver": "CPU oracle (numpy/scipy FP64)"},
+           "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"]},
+           "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    global N_ELEM, NSUB, NCOARSE, P_DEG, WORKLOAD
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dgasm", choices=["dgasm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=100)
+    ap.add_argument("--elems", type=int, default=N_ELEM, help="smaller workloads for profiling runs")
+    ap.add_argument("--nsub", type=int, default=NSUB)
+    ap.add_argument("--ncoarse", type=int, default=NCOARSE)
+    ap.add_argument("--degree", type=int, default=P_DEG)
+    args = ap.parse_args()
+    if (args.elems, args.nsub, args.ncoarse, args.degree) != (N_ELEM, NSUB, NCOARSE, P_DEG):
+        N_ELEM, NSUB, NCOARSE, P_DEG = args.elems, args.nsub, args.ncoarse, args.degree
+        WORKLOAD = (f"profiling case: {N_ELEM} Lloyd-Voronoi cells, p={P_DEG}, {NSUB} subdomains, {NCOARSE} "
+                    f"agglomerates at p_c=1, checkerboard 1e4 (not the headline workload)")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1903_11357_gb300 import dgasm as dg
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    stream = torch.cuda.current_stream()
+    m, rho, M, S = build_problem()
+    b_host = S.rhs()
+    b = torch.tensor(b_host, dtype=torch.float64, device="cuda")
+    ndof = S.ndof
+
+    def step(precision="fp64", keep=None):
+        P = dg.Prec(S, NSUB, NCOARSE, P_C, precision=precision, stream=stream)
+        x = torch.zeros_like(b)
+        rc, st = P.solve(b, x, rtol=1e-8, stream=stream)
+        if keep is not None:
+            keep.append((P, x))
+        return rc, st[0], P, x
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        rc, st, P, x = step()
+        assert rc == 0, rc
+    del P, x
+    # timed region
+    keep = []
+    sampler = ClockSampler(local_rank)
+    dg.profile_read(reset=True)
+    dg.profile_enable(True)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    per_step = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        rc, st, P, x = step(keep=keep)
+        e_b.record(stream)
+        per_step.append((e_a, e_b, st))
+        assert rc == 0, rc
+    ev1.record(stream)
+    barrier()
+    dg.profile_enable(False)
+    prof = dg.profile_read(reset=True)
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    t = torch.tensor([elapsed], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    lat = sorted(a.elapsed_time(bq) for a, bq, _ in per_step)
+    info = keep[0][0].info()
+    sts = [s for _, _, s in per_step]
+    iters = sts[-1]["iters"]
+    launches = sum(info_i["setup_launches"] for info_i in [P_.info() for P_, _ in keep]) + sum(s["launches"] for s in sts)
+    x_fp64 = keep[-1][1].clone()
+    del keep
+
+    # end to end through the C-ABI with host buffers (b copied in, x copied out inside the call)
+    x_host = np.zeros(ndof)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Pe = dg.Prec(S, NSUB, NCOARSE, P_C, precision="fp64", stream=stream)
+        rc, _ = Pe.solve(b_host, x_host, rtol=1e-8, stream=stream, host_buffers=True)
+        assert rc == 0
+        del Pe
+    barrier()
+    e2e_t = time.perf_counter() - t0
+
+    mixed = None
+    if not args.no_mixed:
+        barrier()
+        mx = []
+        for _ in range(args.warmup):
+            step("fp32")
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            rc, st32, P32, x32 = step("fp32", keep=mx)
+        e1.record(stream)
+        barrier()
+        t32 = e0.elapsed_time(e1) / 1000.0
+        err = float(torch.linalg.norm(x32 - x_fp64) / torch.linalg.norm(x_fp64))
+        mixed = {"precision": "fp32 local factors, fp64 outer", "solves_per_s": args.steps / t32,
+                 "ms_per_step": 1000.0 * t32 / args.steps, "iters": st32["iters"], "true_relres": st32["true_relres"],
+                 "rel_diff_vs_fp64": err, "speedup_vs_fp64": (args.steps / t32) / (args.steps / elapsed)}
+        del mx
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = read_peaks()
+    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = FP64_PEAK_FLOPS_PER_CLK * sm_max * 1e6 / 1e12
+    # roofline of the dominant kernel (largest accumulated device time)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    avg_s = dom_ms / 1000.0 / max(dom_n, 1)
+    tiles = info["local_tiles"]
+    if dom == "local":
+        flops = 2 * 2 * tiles * 1024 * 1.0          # forward + backward, 2 flop per FMA, one rhs
+        bytes_ = 2 * tiles * 1024 * 8 + ndof * 8 * 3
+    elif dom == "chol_update":
+        total_upd_flops = info["factor_flops"]
+        flops = total_upd_flops / max(prof["chol_update"][1], 1)
+        bytes_ = None
+    elif dom == "spmv":
+        npb = (P_DEG + 1) * (P_DEG + 2) // 2
+        flops = 2 * info["nnzb"] * npb * npb
+        bytes_ = info["nnzb"] * npb * npb * 8
+    else:
+        flops, bytes_ = None, None
+    roof = {"kernel": dom, "bound": "alu", "achieved": (flops / avg_s / 1e12) if flops else None,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": (flops / avg_s / 1e12 / fp64_peak) if flops else None,
+            "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
+            "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (issue rate measured by an FMA probe)"}
+    kernel_ms = {k: {"total_ms": v[0], "launches": v[1], "avg_ms": v[0] / max(v[1], 1)} for k, v in prof.items() if v[1]}
+    out = {
+        "metric": METRIC, "value": world * args.steps / t_max, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (plain FP64 ASPCG)", "parallelism": f"replicas x{world}",
+                   "l2": "working set > L2 (matrix 92 MB + local factors + Krylov vectors per step), no flush"},
+        "time_to_1e8_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "mean": sum(lat) / len(lat)},
+        "iters": iters, "true_relres": sts[-1]["true_relres"], "kappa_estimate": sts[-1]["kappa"],
+        "setup": {"plan_ms": info["plan_ms"], "setup_ms": info["setup_ms"], "local_tiles": tiles,
+                  "factor_flops": info["factor_flops"]},
+        "gpu_launches": int(launches),
+        "kernels": kernel_ms,
+        "roofline": roof,
+        "e2e": {"value": world * args.steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": ndof * 8,
+                "d2h_bytes_per_step": ndof * 8},
+        "mixed_fp32": mixed,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(oracle_prep(m, rho), iters)
+        out["cpu_baseline"].pop("seconds_per_solve", None)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

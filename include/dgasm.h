@@ -154,6 +154,21 @@ int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, double* z, void
 int dgasm_prec_partition(dgasm_prec_t pc, int* sub_of_elem, int* agg_of_elem);
 /* Bytes held on the device by the preconditioner (factors, coarse operator, permuted matrix). */
 int dgasm_prec_footprint(dgasm_prec_t pc, int64_t* bytes);
+/* Structure and cost of a preconditioner (for reporting and roofline accounting). */
+typedef struct {
+  int nsub;               /* subdomains N_H (Sec. 3) */
+  int nagg;               /* coarse agglomerates N_H of T_H (0 if one-level) */
+  int n0;                 /* coarse dofs nagg * (q+1)(q+2)/2 */
+  int precision;          /* dgasm_precision of the local factors */
+  int64_t local_dofs;     /* sum of the subdomain dof counts (= ndof) */
+  int64_t local_tiles;    /* 32x32 tiles in the envelopes of all local factors (one copy) */
+  int64_t factor_flops;   /* flops of the tile Cholesky of the local factors (tile-level count) */
+  int64_t nnzb;           /* blocks of the block-sparse matrix */
+  double plan_ms;         /* host part of dgasm_setup: partition, ordering, envelopes, task lists */
+  double setup_ms;        /* wall time of dgasm_setup */
+  int setup_launches;     /* kernels launched by dgasm_setup */
+} dgasm_prec_info_t;
+int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info);
 int dgasm_prec_destroy(dgasm_prec_t pc);
 
 /* ---- ASPCG solve (Sec. 7: PCG with P_ad from x0 = 0, stop when ||r||_2 / ||b||_2 < rtol) --------- */
@@ -175,6 +190,7 @@ typedef struct {
   double lambda_max;
   double kappa;         /* lambda_max / lambda_min: the estimate of K(P_ad) of Sec. 7 */
   double solve_ms;      /* device time of the solve */
+  int launches;         /* kernels launched by the solve */
 } dgasm_stats;
 
 /* Solves A x = b for nrhs right-hand sides (column-major ndof x nrhs, caller's dof order), device
@@ -193,6 +209,15 @@ int dgasm_solve_batch(int nprob, const dgasm_prec_t* pcs, const int* nrhs, const
 /* Convenience: Lanczos extremes of the tridiagonal built from k CG coefficients alpha[k], beta[k-1]
  * (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j), host only. */
 int dgasm_lanczos(int k, const double* alpha, const double* beta, double* lambda_min, double* lambda_max);
+
+/* ---- Kernel timing (CUDA events on the launching streams) --------------------------------------
+ * When enabled, every launch of the kinds below made by dgasm_setup / dgasm_solve is bracketed by
+ * CUDA events (inside the captured graphs as event nodes) and its device time is accumulated.
+ * Kinds: 0 SpMV, 1 x/r update + restriction, 2 local solves, 3 coarse solve, 4 p update,
+ * 5 Cholesky diagonal tiles, 6 Cholesky panels, 7 Cholesky trailing updates.  Process-wide. */
+int dgasm_profile_enable(int on);
+/* Accumulated time (ms) and launch count of one kind since the last reset (reset = 1 clears). */
+int dgasm_profile_read(int kind, double* total_ms, int64_t* launches, int reset);
 
 /* ---- Serving: continuous batching of solve requests ---------------------------------------------
  * A server owns a scheduler thread.  dgasm_submit enqueues a request (a system, setup options, nrhs

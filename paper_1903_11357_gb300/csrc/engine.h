@@ -13,6 +13,8 @@ constexpr int KMAX = 8;        // right-hand sides per problem
 constexpr int KC = 4;          // right-hand sides per local-solve CTA
 
 enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
+constexpr int K_SPMV_P = K_NKINDS + 8;   // per-degree SpMV prefix slots p = 1..8
+constexpr int K_NSLOTS = K_SPMV_P + 8;
 enum Counter { C_SPMV = 0, C_GRP = 1, C_PUPD = 2, C_NCOUNTERS = 4 };
 
 // One problem (one preconditioner with k right-hand sides) of a batch.
@@ -35,8 +37,8 @@ struct ProbDev {
   const int* sub_trow;
   const int* trow_F;
   const long long* trow_ptr;
-  const void* Lr;     // row-major tiles (backward sweep, diagonal tiles hold inv(L_II))
-  const void* Lc;     // column-major tiles (forward sweep)
+  const void* Lr;     // row-major tiles in backward-sweep order (diagonal tiles hold inv(L_II))
+  const void* Lc;     // column-major tiles in storage order (forward sweep)
   const double* scale;
   // groups and coarse space
   const int* grp_ptr;
@@ -66,17 +68,20 @@ struct ProbDev {
 struct BatchDev {
   const ProbDev* probs;
   int nprob;
-  const int* prefix[K_NKINDS + 8];  // item prefix per kind; K_NKINDS + 2*prec + (kc > 1) for local solves
+  int* err;          // device error word: nonzero when a bounded wait in a kernel gave up
+  const int* prefix[K_NSLOTS];  // item prefix per kind; K_NKINDS + 2*prec + (kc > 1) for local solves;
+                                // K_SPMV_P + p - 1 for the SpMV of degree-p problems
 };
 
 // ---- solve kernels (kernels_solve.cu) ----
 enum UpdateMode { MODE_INIT = 0, MODE_ITER = 1 };
-int launch_spmv(const BatchDev& B, int total, int operand /*0: q = A p, 1: q = A x, true residual*/, void* stream);
+int launch_spmv(const BatchDev& B, int p, int total, int operand /*0: q = A p, 1: q = A x, true residual*/, void* stream);
 int launch_update(const BatchDev& B, int total, int mode, int use_q, void* stream);
 int launch_local(const BatchDev& B, int slot, int total, int smem_bytes, void* stream);
 int launch_coarse(const BatchDev& B, int total, void* stream);
 int launch_pupdate(const BatchDev& B, int total, int mode, void* stream);
 int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);
+// dynamic shared memory of a local-solve launch over subdomains of at most ndof_max dofs
 int local_smem_bytes(int prec, int ndof_max, int kc);
 int launch_system_spmv(const int* rowptr, const int* col, const double* vals, int ne, int np, int np2s,
                        const double* x, double* y, void* stream);
@@ -96,10 +101,13 @@ int launch_scale(const int* rowptr, const int* col, const double* vals, int ne, 
 int launch_extract_rows(int prec, const EnvDev& E, const int* sub_e0, const int* rowptr, const int* col,
                         const double* vals, int np, int np2s, const double* scale, void* Lr, int nsub, int ne,
                         void* stream);
-int launch_chol_step(int prec, const EnvDev& E, void* Lr, int K, const int* diag_task, int n_diag,
-                     const int* panel_task, int n_panel, const int* upd_task, int n_upd, int* err, void* stream);
+int launch_chol_diag(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, int* err, void* stream);
+int launch_chol_panel(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, void* stream);
+int launch_chol_update(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, void* stream);
 int launch_to_colmajor(int prec, const void* Lr, void* Lc, long long ntiles, void* stream);
 int launch_to_bf16(const float* src, void* dst, long long n, void* stream);
+// dst tile t = src tile idx[t] (same element layout), for the backward-ordered copy of a factor
+int launch_gather_tiles(int prec, const void* src, const long long* idx, void* dst, long long ntiles, void* stream);
 int launch_r0t(const int* perm, const double* xy, const int* pptr, const int* pvtx, const double* bbox,
                const int* agg_int, const double* agg_bbox, int ne, int p, int q, const double* gl_t,
                const double* gl_w, int mq, double* r0t, void* stream);

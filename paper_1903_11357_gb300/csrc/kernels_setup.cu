@@ -103,14 +103,17 @@ __global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, 
     a[r][c] = (r >= c) ? (C)tile[t] : (C)0;
   }
   __syncthreads();
+  __shared__ C rdiag[T];   // 1 / L_jj
   for (int j = 0; j < T; ++j) {
     if (tid == 0) {
       C d = a[j][j];
       if (!(d > (C)0)) { if (bad < 0) bad = j; d = (C)1; }
-      a[j][j] = csqrt<C>(d);
+      d = csqrt<C>(d);
+      a[j][j] = d;
+      rdiag[j] = (C)1 / d;
     }
     __syncthreads();
-    if (tid > j && tid < T) a[tid][j] /= a[j][j];
+    if (tid > j && tid < T) a[tid][j] *= rdiag[j];
     __syncthreads();
     for (int t = tid; t < TT; t += blockDim.x) {
       int r = t / T, c = t % T;
@@ -122,11 +125,11 @@ __global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, 
   if (tid < T) {
     int c = tid;
     for (int r = 0; r < c; ++r) inv[r][c] = (C)0;
-    inv[c][c] = (C)1 / a[c][c];
+    inv[c][c] = rdiag[c];
     for (int r = c + 1; r < T; ++r) {
       C acc = (C)0;
       for (int m = c; m < r; ++m) acc += a[r][m] * inv[m][c];
-      inv[r][c] = -acc / a[r][r];
+      inv[r][c] = -acc * rdiag[r];
     }
   }
   __syncthreads();
@@ -201,6 +204,16 @@ __global__ void k_to_colmajor(const S* __restrict__ Lr, S* __restrict__ Lc, long
     __syncthreads();
     for (int u = threadIdx.x; u < TT; u += blockDim.x) dst[u] = buf[u % T][u / T];
     __syncthreads();
+  }
+}
+
+template <typename S>
+__global__ void k_gather_tiles(const S* __restrict__ src, const long long* __restrict__ idx, S* __restrict__ dst,
+                               long long ntiles) {
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const S* a = src + idx[t] * TT;
+    S* b = dst + t * TT;
+    for (int u = threadIdx.x; u < TT; u += blockDim.x) b[u] = a[u];
   }
 }
 
@@ -423,18 +436,24 @@ int launch_extract_rows(int prec, const EnvDev& E, const int* sub_e0, const int*
   return (int)cudaGetLastError();
 }
 
-int launch_chol_step(int prec, const EnvDev& E, void* L, int K, const int* diag_task, int n_diag, const int* panel_task,
-                     int n_panel, const int* upd_task, int n_upd, int* err, void* st) {
-  cudaStream_t s = (cudaStream_t)st;
-  if (prec == 0) {
-    if (n_diag) k_chol_diag<double><<<n_diag, 256, 0, s>>>(E, (double*)L, K, diag_task, err);
-    if (n_panel) k_chol_panel<double><<<n_panel, 256, 0, s>>>(E, (double*)L, K, panel_task);
-    if (n_upd) k_chol_update<double><<<n_upd, 256, 0, s>>>(E, (double*)L, K, upd_task);
-  } else {
-    if (n_diag) k_chol_diag<float><<<n_diag, 256, 0, s>>>(E, (float*)L, K, diag_task, err);
-    if (n_panel) k_chol_panel<float><<<n_panel, 256, 0, s>>>(E, (float*)L, K, panel_task);
-    if (n_upd) k_chol_update<float><<<n_upd, 256, 0, s>>>(E, (float*)L, K, upd_task);
-  }
+int launch_chol_diag(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, int* err, void* st) {
+  if (!n) return 0;
+  if (prec == 0) k_chol_diag<double><<<n, 256, 0, (cudaStream_t)st>>>(E, (double*)L, K, tasks, err);
+  else k_chol_diag<float><<<n, 256, 0, (cudaStream_t)st>>>(E, (float*)L, K, tasks, err);
+  return (int)cudaGetLastError();
+}
+
+int launch_chol_panel(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, void* st) {
+  if (!n) return 0;
+  if (prec == 0) k_chol_panel<double><<<n, 256, 0, (cudaStream_t)st>>>(E, (double*)L, K, tasks);
+  else k_chol_panel<float><<<n, 256, 0, (cudaStream_t)st>>>(E, (float*)L, K, tasks);
+  return (int)cudaGetLastError();
+}
+
+int launch_chol_update(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, void* st) {
+  if (!n) return 0;
+  if (prec == 0) k_chol_update<double><<<n, 256, 0, (cudaStream_t)st>>>(E, (double*)L, K, tasks);
+  else k_chol_update<float><<<n, 256, 0, (cudaStream_t)st>>>(E, (float*)L, K, tasks);
   return (int)cudaGetLastError();
 }
 
@@ -443,6 +462,14 @@ int launch_to_colmajor(int prec, const void* Lr, void* Lc, long long ntiles, voi
   if (g < 1) g = 1;
   if (prec == 0) k_to_colmajor<double><<<g, 256, 0, (cudaStream_t)st>>>((const double*)Lr, (double*)Lc, ntiles);
   else k_to_colmajor<float><<<g, 256, 0, (cudaStream_t)st>>>((const float*)Lr, (float*)Lc, ntiles);
+  return (int)cudaGetLastError();
+}
+
+int launch_gather_tiles(int prec, const void* src, const long long* idx, void* dst, long long ntiles, void* st) {
+  int g = (int)(ntiles < 152 * 16 ? ntiles : 152 * 16);
+  if (g < 1) g = 1;
+  if (prec == 0) k_gather_tiles<double><<<g, 256, 0, (cudaStream_t)st>>>((const double*)src, idx, (double*)dst, ntiles);
+  else k_gather_tiles<float><<<g, 256, 0, (cudaStream_t)st>>>((const float*)src, idx, (float*)dst, ntiles);
   return (int)cudaGetLastError();
 }
 

@@ -10,10 +10,6 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include <mutex>
-#include <set>
-#include <utility>
-
 #include "engine.h"
 
 namespace dgasm {
@@ -58,6 +54,15 @@ __device__ void block_sum_k(const double* v, int k, double* red /*[NW][KMAX]*/, 
   __syncthreads();
 }
 
+// sum of v[i * stride] for i < n by one warp, in a fixed order (lane-strided partial sums, then a fixed
+// shuffle tree); every lane returns the total
+__device__ __forceinline__ double warp_sum_strided(const double* v, int n, int stride) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += v[(long long)i * stride];
+  return warp_sum(s);
+}
+
 // returns true in the last CTA of this kernel for problem P (all CTAs must call it exactly once)
 __device__ bool last_block(unsigned int* counter, unsigned int n_items, int* flag_smem) {
   __threadfence();
@@ -75,15 +80,60 @@ __device__ bool last_block(unsigned int* counter, unsigned int n_items, int* fla
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
+// one thread per (element, row): q_e[r] = sum over the blocks of row e of B[r][c] x_col[c], with the
+// block width NP known at compile time (fully unrolled, two accumulator chains per right-hand side)
+template <int NP>
+__device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operand, const bool* act, double* part) {
+  const int e_begin = item * P.epi;
+  const int nel = min(P.epi, P.ne - e_begin);
+  const int t = threadIdx.x;
+  if (t >= nel * NP) return;
+  const int e = e_begin + t / NP, r = t % NP;
+  const double* vec = operand == 0 ? P.p : P.x;
+  const int k = P.k;
+  double acc[KMAX][2];
+#pragma unroll
+  for (int kk = 0; kk < KMAX; ++kk) acc[kk][0] = acc[kk][1] = 0.0;
+  const int kb0 = P.rowptr[e], kb1 = P.rowptr[e + 1];
+  for (int kb = kb0; kb < kb1; ++kb) {
+    const double* blk = P.vals + (long long)kb * P.np2s + r;
+    const double* xc = vec + (long long)__ldg(P.col + kb) * NP;
+    double a[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) a[c] = __ldg(blk + c * NP);
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk) {
+      if (kk >= k || !act[kk]) continue;
+      const double* xk = xc + (long long)kk * P.ndof;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) acc[kk][c & 1] = fma(a[c], xk[c], acc[kk][c & 1]);
+    }
+  }
+  const long long d = (long long)e * NP + r;
+#pragma unroll
+  for (int kk = 0; kk < KMAX; ++kk) {
+    if (kk >= k || !act[kk]) continue;
+    const double q = acc[kk][0] + acc[kk][1];
+    P.q[kk * (long long)P.ndof + d] = q;
+    if (operand == 0) {
+      part[kk] = P.p[kk * (long long)P.ndof + d] * q;
+    } else {
+      const double rr = P.b[kk * (long long)P.ndof + d] - q;
+      part[kk] = rr * rr;
+    }
+  }
+}
+
 // ---- SpMV: q = A p (operand 0, with partial (p, q)) or q = A x and (b - A x)^2 (operand 1) ------
-__global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand) {
+template <int NP>
+__global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand, int slot) {
   __shared__ double red[NW * KMAX];
   __shared__ double tot[KMAX];
   __shared__ int lastf;
-  const int pi = find_prob(B.prefix[K_SPMV], B.nprob, blockIdx.x);
+  const int pi = find_prob(B.prefix[slot], B.nprob, blockIdx.x);
   const ProbDev& P = B.probs[pi];
-  const int item = blockIdx.x - B.prefix[K_SPMV][pi];
-  const int k = P.k, np = P.np;
+  const int item = blockIdx.x - B.prefix[slot][pi];
+  const int k = P.k;
   bool act[KMAX];
   bool any = false;
 #pragma unroll
@@ -94,48 +144,15 @@ __global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand) {
   double part[KMAX];
 #pragma unroll
   for (int kk = 0; kk < KMAX; ++kk) part[kk] = 0.0;
-  if (any) {
-    const int e_begin = item * P.epi;
-    const int nel = min(P.epi, P.ne - e_begin);
-    const int t = threadIdx.x;
-    if (t < nel * np) {
-      const int e = e_begin + t / np, r = t % np;
-      const double* vec = operand == 0 ? P.p : P.x;
-      double acc[KMAX];
-#pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) acc[kk] = 0.0;
-      for (int kb = P.rowptr[e]; kb < P.rowptr[e + 1]; ++kb) {
-        const double* blk = P.vals + (long long)kb * P.np2s + r;
-        const double* xc = vec + (long long)P.col[kb] * np;
-        for (int c = 0; c < np; ++c) {
-          double a = __ldg(blk + c * np);
-#pragma unroll
-          for (int kk = 0; kk < KMAX; ++kk)
-            if (act[kk]) acc[kk] = fma(a, xc[(long long)kk * P.ndof + c], acc[kk]);
-        }
-      }
-      const long long d = (long long)e * np + r;
-#pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) {
-        if (!act[kk]) continue;
-        P.q[kk * (long long)P.ndof + d] = acc[kk];
-        if (operand == 0) {
-          part[kk] = P.p[kk * (long long)P.ndof + d] * acc[kk];
-        } else {
-          double rr = P.b[kk * (long long)P.ndof + d] - acc[kk];
-          part[kk] = rr * rr;
-        }
-      }
-    }
-  }
+  if (any) spmv_rows<NP>(P, item, operand, act, part);
   block_sum_k(part, k, red, tot);
   if (threadIdx.x < k) P.part_pq[(long long)item * k + threadIdx.x] = tot[threadIdx.x];
   if (!last_block(&P.counters[C_SPMV], P.n_chunk_items, &lastf)) return;
-  if (threadIdx.x < k) {
-    const int kk = threadIdx.x;
+  if ((threadIdx.x >> 5) < k) {
+    const int kk = threadIdx.x >> 5;
     if (!act[kk]) return;
-    double s = 0.0;
-    for (int i = 0; i < P.n_chunk_items; ++i) s += P.part_pq[(long long)i * k + kk];
+    const double s = warp_sum_strided(P.part_pq + kk, P.n_chunk_items, k);
+    if ((threadIdx.x & 31) != 0) return;
     if (operand == 1) {
       P.true_rr[kk] = P.bnorm[kk] > 0.0 ? sqrt(s) / P.bnorm[kk] : 0.0;
       return;
@@ -153,6 +170,7 @@ __global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand) {
 
 // ---- x/r update (or initial residual) with partial ||r||^2 and the coarse restriction ----------
 __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
+  __shared__ double red4[NW][KMAX][4];
   __shared__ double red[NW * KMAX];
   __shared__ double tot[KMAX];
   __shared__ int lastf;
@@ -172,16 +190,27 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
   for (int kk = 0; kk < KMAX; ++kk) alpha[kk] = (mode == MODE_ITER && act[kk]) ? P.alpha[kk] : 0.0;
   const int g0 = P.grp_ptr[g], g1 = P.grp_ptr[g + 1];
   const int nd = (g1 - g0) * np;
-  double prr[KMAX];
+  // one pass: x/r update, ||r||^2 and, for q = 1 (nq = 3), the restriction r_0[J] = sum R0T^T r
+  constexpr int NQ1 = 3;
+  double prr[KMAX], pr0[KMAX][NQ1];
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) prr[kk] = 0.0;
-  // restriction accumulators: at most KMAX x 3 (q = 1) are kept per thread; larger nq loop below
+  for (int kk = 0; kk < KMAX; ++kk) {
+    prr[kk] = 0.0;
+#pragma unroll
+    for (int c = 0; c < NQ1; ++c) pr0[kk][c] = 0.0;
+  }
+  const bool fused_r0 = nq == NQ1;
   const bool restrict_ = nq > 0;
   for (int base = 0; base < nd && any; base += NTHREADS) {
     const int t = base + threadIdx.x;
     if (t >= nd) break;
     const int e = P.grp_elems[g0 + t / np], a = t % np;
     const long long d = (long long)e * np + a;
+    double w[NQ1] = {0.0, 0.0, 0.0};
+    if (fused_r0) {
+#pragma unroll
+      for (int c = 0; c < NQ1; ++c) w[c] = P.r0t[d * NQ1 + c];
+    }
 #pragma unroll
     for (int kk = 0; kk < KMAX; ++kk) {
       if (!act[kk]) continue;
@@ -197,12 +226,34 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
       }
       P.r[o] = rv;
       prr[kk] = fma(rv, rv, prr[kk]);
+#pragma unroll
+      for (int c = 0; c < NQ1; ++c) pr0[kk][c] = fma(w[c], rv, pr0[kk][c]);
     }
   }
-  block_sum_k(prr, k, red, tot);
-  if (threadIdx.x < k) P.part_rr[(long long)g * k + threadIdx.x] = tot[threadIdx.x];
-  if (restrict_ && any) {
-    // r_0[J*nq + c] = sum_{e in J} sum_a R0T_e[a][c] r_e[a], reduced per (c) in a fixed order
+  // CTA reduction of ||r||^2 and the three restriction components (fixed shuffle tree + warp order)
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nv = fused_r0 ? 1 + NQ1 : 1;
+#pragma unroll
+    for (int kk = 0; kk < KMAX; ++kk) {
+      if (kk >= k) break;
+      for (int c = 0; c < nv; ++c) {
+        double v = c == 0 ? prr[kk] : pr0[kk][c - 1];
+        v = warp_sum(v);
+        if (lane == 0) red4[wid][kk][c] = v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < k * nv) {
+      const int kk = threadIdx.x / nv, c = threadIdx.x % nv;
+      double v = 0.0;
+      for (int ww = 0; ww < NW; ++ww) v += red4[ww][kk][c];
+      if (c == 0) P.part_rr[(long long)g * k + kk] = v;
+      else if (act[kk]) P.r0[(long long)kk * P.n0 + g * nq + c - 1] = v;
+    }
+  }
+  if (restrict_ && !fused_r0 && any) {
+    // general coarse degree: one reduction per coarse basis function
     for (int c = 0; c < nq; ++c) {
       double v[KMAX];
 #pragma unroll
@@ -211,21 +262,21 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
         const int t = base + threadIdx.x;
         if (t >= nd) break;
         const int e = P.grp_elems[g0 + t / np], a = t % np;
-        const double w = P.r0t[((long long)e * np + a) * nq + c];
+        const double wv = P.r0t[((long long)e * np + a) * nq + c];
 #pragma unroll
         for (int kk = 0; kk < KMAX; ++kk)
-          if (act[kk]) v[kk] = fma(w, P.r[kk * (long long)P.ndof + (long long)e * np + a], v[kk]);
+          if (act[kk]) v[kk] = fma(wv, P.r[kk * (long long)P.ndof + (long long)e * np + a], v[kk]);
       }
       block_sum_k(v, k, red, tot);
       if (threadIdx.x < k && act[threadIdx.x]) P.r0[(long long)threadIdx.x * P.n0 + g * nq + c] = tot[threadIdx.x];
     }
   }
   if (!last_block(&P.counters[C_GRP], P.ngrp, &lastf)) return;
-  if (threadIdx.x < k) {
-    const int kk = threadIdx.x;
+  if ((threadIdx.x >> 5) < k) {
+    const int kk = threadIdx.x >> 5;
     if (!act[kk]) return;
-    double s = 0.0;
-    for (int i = 0; i < P.ngrp; ++i) s += P.part_rr[(long long)i * k + kk];
+    const double s = warp_sum_strided(P.part_rr + kk, P.ngrp, k);
+    if ((threadIdx.x & 31) != 0) return;
     if (mode == MODE_INIT) {
       double bn = sqrt(s);
       P.bnorm[kk] = bn;
@@ -256,157 +307,6 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
       atomicSub(P.remaining, 1);
     }
   }
-}
-
-// ---- local solves z_i = A_i^{-1} r_i with the scaled tile-envelope factor -----------------------
-template <typename S> __device__ __forceinline__ float to_f(S v);
-template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <typename S, typename C> __device__ __forceinline__ C ld_c(const S* p);
-template <> __device__ __forceinline__ double ld_c<double, double>(const double* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ld_c<float, float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ld_c<__nv_bfloat16, float>(const __nv_bfloat16* p) {
-  return __bfloat162float(__ldg(p));
-}
-
-template <typename S, typename C, int KCT>
-__global__ void __launch_bounds__(NTHREADS) k_local(BatchDev B, int slot) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[NW * KMAX];
-  __shared__ double tot[KMAX];
-  const int* prefix = B.prefix[slot];
-  const int pi = find_prob(prefix, B.nprob, blockIdx.x);
-  const ProbDev& P = B.probs[pi];
-  const int li = blockIdx.x - prefix[pi];
-  const int s = li / P.n_rhs_chunks, ch = li % P.n_rhs_chunks;
-  const int k0 = ch * KCT;
-  const int kc = min(KCT, P.k - k0);
-  bool act[KCT];
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < KCT; ++j) {
-    act[j] = j < kc && P.done[k0 + j] == 0;
-    any |= act[j];
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int e0 = P.sub_e0[s];
-  const int n = (P.sub_e0[s + 1] - e0) * P.np;
-  const long long d0 = (long long)e0 * P.np;
-  const int nbt = (n + T - 1) / T, npad = nbt * T;
-  if (!any) return;
-  C* y = reinterpret_cast<C*>(smem_raw);  // [KCT][npad]
-  C* part = y + KCT * npad;                // [NW][KCT][T]
-  C* tmp = part + NW * KCT * T;            // [KCT][T]
-  for (int idx = threadIdx.x; idx < KCT * npad; idx += NTHREADS) {
-    const int j = idx / npad, i = idx - j * npad;
-    C v = (C)0;
-    if (i < n && act[j]) v = (C)(P.scale[d0 + i] * P.r[(long long)(k0 + j) * P.ndof + d0 + i]);
-    y[idx] = v;
-  }
-  __syncthreads();
-  const int tr0 = P.sub_trow[s];
-  const S* Lc = reinterpret_cast<const S*>(P.Lc);
-  const S* Lr = reinterpret_cast<const S*>(P.Lr);
-  // forward substitution: y_I <- inv(L_II) (y_I - sum_{J<I} L_IJ y_J), column-major tiles
-  for (int I = 0; I < nbt; ++I) {
-    const int F = P.trow_F[tr0 + I];
-    const long long base = P.trow_ptr[tr0 + I];
-    const int nt = I - F;
-    C acc[KCT];
-#pragma unroll
-    for (int j = 0; j < KCT; ++j) acc[j] = (C)0;
-    for (int jt = w; jt < nt; jt += NW) {
-      const S* tile = Lc + (base + jt) * TT + lane;
-      const C* yv = y + (F + jt) * T;
-#pragma unroll 8
-      for (int c = 0; c < T; ++c) {
-        const C a = ld_c<S, C>(tile + c * T);
-#pragma unroll
-        for (int j = 0; j < KCT; ++j) acc[j] += a * yv[j * npad + c];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < KCT; ++j) part[(w * KCT + j) * T + lane] = acc[j];
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) {
-        C v = y[j * npad + I * T + lane];
-        for (int ww = 0; ww < NW; ++ww) v -= part[(ww * KCT + j) * T + lane];
-        tmp[j * T + lane] = v;
-      }
-      __syncwarp();
-      const S* D = Lc + (base + nt) * TT + lane;
-      C o[KCT];
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) o[j] = (C)0;
-#pragma unroll 8
-      for (int c = 0; c < T; ++c) {
-        const C a = ld_c<S, C>(D + c * T);
-#pragma unroll
-        for (int j = 0; j < KCT; ++j) o[j] += a * tmp[j * T + c];
-      }
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) y[j * npad + I * T + lane] = o[j];
-    }
-    __syncthreads();
-  }
-  // backward substitution with L^T: x_J <- inv(L_JJ)^T y_J, then y_K -= L_JK^T x_J, row-major tiles
-  for (int J = nbt - 1; J >= 0; --J) {
-    const int F = P.trow_F[tr0 + J];
-    const long long base = P.trow_ptr[tr0 + J];
-    const int nt = J - F;
-    if (w == 0) {
-      const S* D = Lr + (base + nt) * TT + lane;
-      C o[KCT];
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) o[j] = (C)0;
-#pragma unroll 8
-      for (int r = 0; r < T; ++r) {
-        const C a = ld_c<S, C>(D + r * T);
-#pragma unroll
-        for (int j = 0; j < KCT; ++j) o[j] += a * y[j * npad + J * T + r];
-      }
-      __syncwarp();
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) y[j * npad + J * T + lane] = o[j];
-    }
-    __syncthreads();
-    for (int jt = w; jt < nt; jt += NW) {
-      const S* tile = Lr + (base + jt) * TT + lane;
-      const C* xv = y + J * T;
-      C acc[KCT];
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) acc[j] = (C)0;
-#pragma unroll 8
-      for (int r = 0; r < T; ++r) {
-        const C a = ld_c<S, C>(tile + r * T);
-#pragma unroll
-        for (int j = 0; j < KCT; ++j) acc[j] += a * xv[j * npad + r];
-      }
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) y[j * npad + (F + jt) * T + lane] -= acc[j];
-    }
-    __syncthreads();
-  }
-  // z_i = D^{-1/2} y, partial (r, z) for this subdomain
-  double prz[KMAX];
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) prz[j] = 0.0;
-  for (int i = threadIdx.x; i < n; i += NTHREADS) {
-    const double sc = P.scale[d0 + i];
-#pragma unroll
-    for (int j = 0; j < KCT; ++j) {
-      if (!act[j]) continue;
-      const long long o = (long long)(k0 + j) * P.ndof + d0 + i;
-      const double zv = sc * (double)y[j * npad + i];
-      P.z[o] = zv;
-      prz[j] = fma(P.r[o], zv, prz[j]);
-    }
-  }
-  block_sum_k(prz, KCT, red, tot);
-  if (threadIdx.x < kc) P.part_rz[(long long)s * P.k + k0 + threadIdx.x] = act[threadIdx.x] ? tot[threadIdx.x] : 0.0;
 }
 
 // ---- coarse solve z_0 = A_0^{-1} r_0: one warp per row of the explicit inverse -------------------
@@ -475,16 +375,17 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
     act[kk] = kk < k && P.done[kk] == 0;
     any |= act[kk];
   }
-  if (threadIdx.x < k) {
-    const int kk = threadIdx.x;
+  if ((threadIdx.x >> 5) < k) {
+    const int kk = threadIdx.x >> 5;
     double g = 0.0;
     if (act[kk]) {
-      for (int s = 0; s < P.nsub; ++s) g += P.part_rz[(long long)s * k + kk];
-      if (nq > 0)
-        for (int i = 0; i < P.n_coarse_items; ++i) g += P.part_c[(long long)i * k + kk];
+      g = warp_sum_strided(P.part_rz + kk, P.nsub, k);
+      if (nq > 0) g += warp_sum_strided(P.part_c + kk, P.n_coarse_items, k);
     }
-    gnew_s[kk] = g;
-    beta_s[kk] = (mode == MODE_INIT || !act[kk]) ? 0.0 : g / P.gamma[kk];
+    if ((threadIdx.x & 31) == 0) {
+      gnew_s[kk] = g;
+      beta_s[kk] = (mode == MODE_INIT || !act[kk]) ? 0.0 : g / P.gamma[kk];
+    }
   }
   __syncthreads();
   if (any) {
@@ -562,68 +463,29 @@ __global__ void k_system_spmv(const int* __restrict__ rowptr, const int* __restr
   y[(long long)e * np + r] = acc;
 }
 
-// Opt in to the largest dynamic shared memory once per kernel instantiation (and device), before any
-// stream capture: the first launch of each instantiation happens in the uncaptured initial step.
-template <typename K>
-int ensure_smem(K fn, int smem) {
-  static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
-  if (smem <= 48 * 1024) return 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(mu);
-  if (done.count({(const void*)fn, dev})) return 0;
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
-  if (e != cudaSuccess) return (int)e;
-  done.insert({(const void*)fn, dev});
-  return 0;
-}
-
-template <typename S, typename C>
-int launch_local_t(const BatchDev& B, int slot, int kcl, int total, int smem, cudaStream_t st) {
-  if (kcl == 0) {
-    auto fn = k_local<S, C, 1>;
-    if (int e = ensure_smem(fn, smem)) return e;
-    fn<<<total, NTHREADS, smem, st>>>(B, slot);
-  } else {
-    auto fn = k_local<S, C, KC>;
-    if (int e = ensure_smem(fn, smem)) return e;
-    fn<<<total, NTHREADS, smem, st>>>(B, slot);
-  }
-  return (int)cudaGetLastError();
-}
-
 }  // namespace
 
-int local_smem_bytes(int prec, int ndof_max, int kc) {
-  int npad = ((ndof_max + T - 1) / T) * T;
-  int csize = prec == 0 ? 8 : 4;
-  int kct = kc > 1 ? KC : 1;
-  return csize * (kct * npad + NW * kct * T + kct * T);
-}
-
-int launch_spmv(const BatchDev& B, int total, int operand, void* st) {
-  k_spmv<<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, operand);
+// one launch per polynomial degree present in the batch: slot K_SPMV_P + p - 1 holds the item prefix of
+// the problems of degree p
+int launch_spmv(const BatchDev& B, int p, int total, int operand, void* st) {
+  const int slot = K_SPMV_P + p - 1;
+  cudaStream_t s = (cudaStream_t)st;
+  switch (p) {
+    case 1: k_spmv<3><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 2: k_spmv<6><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 3: k_spmv<10><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 4: k_spmv<15><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 5: k_spmv<21><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 6: k_spmv<28><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 7: k_spmv<36><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    default: k_spmv<45><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+  }
   return (int)cudaGetLastError();
 }
 
 int launch_update(const BatchDev& B, int total, int mode, int /*use_q*/, void* st) {
   k_update<<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
   return (int)cudaGetLastError();
-}
-
-// slot = K_NKINDS + 2 * prec + (kc > 1)
-int launch_local(const BatchDev& B, int slot, int total, int smem, void* st) {
-  const int prec = (slot - K_NKINDS) / 2, kcl = (slot - K_NKINDS) % 2;
-  cudaStream_t s = (cudaStream_t)st;
-  switch (prec) {
-    case DGASM_FP64: return launch_local_t<double, double>(B, slot, kcl, total, smem, s);
-    case DGASM_FP32:
-    case DGASM_TF32: return launch_local_t<float, float>(B, slot, kcl, total, smem, s);
-    default: return launch_local_t<__nv_bfloat16, float>(B, slot, kcl, total, smem, s);
-  }
 }
 
 int launch_coarse(const BatchDev& B, int total, void* st) {

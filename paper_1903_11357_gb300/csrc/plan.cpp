@@ -38,6 +38,16 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
     }
     sub_trow[s + 1] = sub_trow[s] + nbt;
   }
+  bwd_src.clear();
+  bwd_src.reserve(ntiles);
+  for (int s = 0; s < nsub; ++s) {
+    const int nbt = (int)Fs[s].size(), tr0 = sub_trow[s];
+    for (int J = nbt - 1; J >= 0; --J) {
+      for (int I = J + 1; I < nbt; ++I)
+        if (Fs[s][I] <= J) bwd_src.push_back(trow_ptr[tr0 + I] + (J - Fs[s][I]));
+      bwd_src.push_back(trow_ptr[tr0 + J] + (J - Fs[s][J]));
+    }
+  }
   diag_off.assign(max_nbt + 1, 0);
   panel_off.assign(max_nbt + 1, 0);
   upd_off.assign(max_nbt + 1, 0);

@@ -21,6 +21,9 @@ struct Envelope {
   std::vector<int> sub_trow;           // [nsub+1] offsets into the tile-row arrays
   std::vector<int> trow_F;             // first tile column of each tile row
   std::vector<long long> trow_ptr;     // tile index of the first tile of each tile row
+  // backward stream: position b (subdomain s occupies the same index range as its forward tiles) holds
+  // the tile bwd_src[b]; per subdomain, column J from the last: tiles (I, J), I > J, then (J, J)
+  std::vector<long long> bwd_src;
   long long ntiles = 0;
   int max_nbt = 0;
   // Cholesky tasks, grouped by step K: diag (s, K), panel (s, I), update (s, I, J), I >= J

@@ -1,0 +1,357 @@
+// dgasm_setup: partition and ordering (host), then on the device the extraction of each A_i (Sec. 3),
+// its tile Cholesky factorisation, the L2 prolongation R_0^T (Eq. R0T), A_0 = R_0 A R_0^T (Eq. A0) and
+// the FP64 factor and inverse of A_0.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "engine.h"
+#include "plan.h"
+#include "profile.h"
+#include "solver.h"
+
+using namespace dgasm;
+
+namespace dgasm {
+
+namespace {
+
+int fact_elem_bytes(int prec) { return prec == DGASM_FP64 ? 8 : 4; }
+int store_elem_bytes(int prec) { return prec == DGASM_FP64 ? 8 : (prec == DGASM_BF16 ? 2 : 4); }
+
+int upload_env(const Envelope& E, EnvBufs& D) {
+  std::vector<int> ndof(E.ndof);
+  DG_TRY(upload(D.ndof, ndof));
+  DG_TRY(upload(D.sub_trow, E.sub_trow));
+  DG_TRY(upload(D.trow_F, E.trow_F));
+  DG_TRY(upload(D.trow_ptr, E.trow_ptr));
+  DG_TRY(upload(D.diag_task, E.diag_task));
+  DG_TRY(upload(D.panel_task, E.panel_task));
+  DG_TRY(upload(D.upd_task, E.upd_task));
+  DG_TRY(upload(D.bwd_src, E.bwd_src));
+  D.dev.nsub = E.nsub;
+  D.dev.ndof = D.ndof.as<int>();
+  D.dev.sub_trow = D.sub_trow.as<int>();
+  D.dev.trow_F = D.trow_F.as<int>();
+  D.dev.trow_ptr = D.trow_ptr.as<long long>();
+  return DGASM_OK;
+}
+
+// factor the tile pool Lr (row-major, factor precision) in place, step by step
+int factor_env(int prec, const Envelope& E, EnvBufs& D, void* Lr, int* err, cudaStream_t st, EventPairs* ev,
+               int* launches) {
+  const int fp = prec == DGASM_FP64 ? 0 : 1;
+  for (int K = 0; K < E.max_nbt; ++K) {
+    int nd = E.diag_off[K + 1] - E.diag_off[K];
+    int npn = E.panel_off[K + 1] - E.panel_off[K];
+    int nu = E.upd_off[K + 1] - E.upd_off[K];
+    int id = ev && nd ? ev->begin(PK_CHOL_DIAG, st) : -1;
+    int rc = launch_chol_diag(fp, D.dev, Lr, K, D.diag_task.as<int>() + E.diag_off[K], nd, err, st);
+    if (ev) ev->end(id, st);
+    if (rc) return cuda_error(rc, "tile Cholesky diagonal step");
+    id = ev && npn ? ev->begin(PK_CHOL_PANEL, st) : -1;
+    rc = launch_chol_panel(fp, D.dev, Lr, K, D.panel_task.as<int>() + 2 * (size_t)E.panel_off[K], npn, st);
+    if (ev) ev->end(id, st);
+    if (rc) return cuda_error(rc, "tile Cholesky panel step");
+    id = ev && nu ? ev->begin(PK_CHOL_UPDATE, st) : -1;
+    rc = launch_chol_update(fp, D.dev, Lr, K, D.upd_task.as<int>() + 3 * (size_t)E.upd_off[K], nu, st);
+    if (ev) ev->end(id, st);
+    if (rc) return cuda_error(rc, "tile Cholesky update step");
+    *launches += (nd > 0) + (npn > 0) + (nu > 0);
+  }
+  return DGASM_OK;
+}
+
+}  // namespace
+
+}  // namespace dgasm
+
+// ---- setup ---------------------------------------------------------------------------------------
+namespace dgasm {
+
+// Validation, streams and the host plan (partition, ordering, envelopes, task lists): no device work
+// besides the one-time upload of the system matrix.
+int prec_plan(dgasm_system_s* s, const dgasm_setup_opts* o, std::unique_ptr<dgasm_prec_s>& pc) {
+  if (!s || !o) return set_error(DGASM_EINVAL, "dgasm_setup: NULL argument");
+  if (o->precision < DGASM_FP64 || o->precision > DGASM_BF16) return set_error(DGASM_EINVAL, "unknown precision %d", o->precision);
+  const bool coarse = o->ncoarse > 0 || o->agg_of_elem;
+  if (coarse && (o->p_c < 1 || o->p_c > s->p)) return set_error(DGASM_EINVAL, "p_c=%d must lie in [1, p=%d]", o->p_c, s->p);
+  const auto t_start = std::chrono::steady_clock::now();
+  pc.reset(new (std::nothrow) dgasm_prec_s());
+  if (!pc) return set_error(DGASM_ENOMEM, "host allocation failed");
+  pc->t_start = t_start;
+  pc->sys = s;
+  pc->precision = o->precision;
+  DG_TRY(s->ensure_device());
+  DG_TRY(pc->init_streams(o->stream));
+  Plan& P = pc->P;
+  DG_TRY(build_plan(*s, o->nsub, o->ncoarse, coarse ? o->p_c : 1, o->sub_of_elem, o->agg_of_elem, P));
+  pc->n0 = P.nagg * P.nq;
+  pc->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  return DGASM_OK;
+}
+
+// Device bytes of a built preconditioner (peak during its setup) plus the Krylov state for nrhs
+// right-hand sides and maxit recorded iterations.
+size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
+  const Plan& P = pc.P;
+  const size_t ndof = (size_t)P.ne * P.np, t = (size_t)P.env.ntiles * TILE * TILE, n0 = pc.n0;
+  size_t b = P.col.size() * (size_t)pc.sys->np2s * 8 + ndof * 8 + P.col.size() * 12 + (size_t)P.ne * 20;
+  b += t * (pc.precision == DGASM_FP64 ? 24 : 12) + P.env.bwd_src.size() * 8;
+  b += (P.env.upd_task.size() + P.env.panel_task.size() + P.env.diag_task.size() + P.env.trow_F.size() * 3) * 4;
+  if (n0) b += ndof * P.nq * 8 + n0 * n0 * 8 * 3 + (size_t)P.env0.ntiles * TILE * TILE * 16;
+  const int epi = NTHREADS / P.np;
+  b += 8 * ((size_t)6 * nrhs * ndof + 2 * nrhs * std::max<size_t>(n0, 1) + 2 * (size_t)nrhs * maxit +
+            (size_t)nrhs * ((P.ne + epi - 1) / epi + P.ngrp + P.nsub + n0 / 8 + 1)) + 4096;
+  return b;
+}
+
+int prec_build(dgasm_prec_s* pc) {
+  dgasm_system_s* s = pc->sys;
+  Plan& P = pc->P;
+  EventPairs* ev = profiling() ? &pc->setup_ev : nullptr;
+  if (ev) ev->reset();
+  int nl = 0;
+  cudaStream_t st = pc->stream;
+  const int ne = P.ne, np = P.np, np2s = s->np2s;
+  // plan arrays
+  DG_TRY(upload(pc->perm, P.perm));
+  DG_TRY(upload(pc->rowptr, P.rowptr));
+  DG_TRY(upload(pc->col, P.col));
+  DG_TRY(upload(pc->src_blk, P.src_blk));
+  DG_TRY(upload(pc->sub_e0, P.sub_e0));
+  DG_TRY(upload(pc->grp_ptr, P.grp_ptr));
+  DG_TRY(upload(pc->grp_elems, P.grp_elems));
+  DG_TRY(upload(pc->agg_int, P.agg_int));
+  DG_TRY(upload_env(P.env, pc->env));
+  std::vector<int> err0{0, -1, -1, 0, 0, -1, -1, 0};
+  DG_TRY(upload(pc->err, err0));
+  // permuted matrix and scaling
+  const long long nnzb = (long long)P.col.size();
+  DG_TRY(pc->vals.alloc(sizeof(double) * nnzb * np2s));
+  DG_CUDA(launch_permute_blocks(s->d_vals.as<double>(), pc->src_blk.as<long long>(), pc->vals.as<double>(), nnzb, np2s, st));
+  nl += 2;
+  DG_TRY(pc->scale.alloc(sizeof(double) * (size_t)ne * np));
+  DG_CUDA(launch_scale(pc->rowptr.as<int>(), pc->col.as<int>(), pc->vals.as<double>(), ne, np, np2s, pc->scale.as<double>(), st));
+  // local factors
+  const int fprec = pc->precision;
+  const size_t ftiles = (size_t)P.env.ntiles * TILE * TILE;
+  DevBuf Lf;  // factorisation pool (row-major)
+  DG_TRY(Lf.alloc(ftiles * fact_elem_bytes(fprec)));
+  DG_CUDA(cudaMemsetAsync(Lf.ptr, 0, Lf.bytes, st));
+  DG_CUDA(launch_extract_rows(fprec == DGASM_FP64 ? 0 : 1, pc->env.dev, pc->sub_e0.as<int>(), pc->rowptr.as<int>(),
+                              pc->col.as<int>(), pc->vals.as<double>(), np, np2s, pc->scale.as<double>(), Lf.ptr,
+                              P.nsub, ne, st));
+  nl += 1;
+  DG_TRY(factor_env(fprec, P.env, pc->env, Lf.ptr, pc->err.as<int>(), st, ev, &nl));
+  // forward copy: column-major tiles in storage order; backward copy: row-major tiles in the order
+  // of the backward sweep (see Envelope::bwd_src)
+  {
+    const int fp = fprec == DGASM_FP64 ? 0 : 1;
+    DevBuf Lcf, Lbf;
+    DG_TRY(Lcf.alloc(ftiles * fact_elem_bytes(fprec)));
+    DG_TRY(Lbf.alloc(ftiles * fact_elem_bytes(fprec)));
+    DG_CUDA(launch_to_colmajor(fp, Lf.ptr, Lcf.ptr, P.env.ntiles, st));
+    DG_CUDA(launch_gather_tiles(fp, Lf.ptr, pc->env.bwd_src.as<long long>(), Lbf.ptr, P.env.ntiles, st));
+    nl += 2;
+    if (fprec == DGASM_BF16) {
+      DG_TRY(pc->Lr.alloc(ftiles * 2));
+      DG_TRY(pc->Lc.alloc(ftiles * 2));
+      DG_CUDA(launch_to_bf16(Lbf.as<float>(), pc->Lr.ptr, (long long)ftiles, st));
+      DG_CUDA(launch_to_bf16(Lcf.as<float>(), pc->Lc.ptr, (long long)ftiles, st));
+      nl += 2;
+      DG_CUDA(cudaStreamSynchronize(st));
+    } else {
+      DG_CUDA(cudaStreamSynchronize(st));
+      pc->Lc = std::move(Lcf);
+      pc->Lr = std::move(Lbf);
+    }
+    Lf.reset();
+  }
+  // coarse space: R_0^T, A_0 = R_0 A R_0^T, FP64 factor and explicit inverse
+  if (pc->n0 > 0) {
+    const int n0 = pc->n0, q = P.q, nq = P.nq, mq = s->p + 2;
+    std::vector<double> gt, gw;
+    gauss_legendre01(mq, gt, gw);
+    DevBuf d_gt, d_gw, d_aggbox;
+    DG_TRY(upload(d_gt, gt));
+    DG_TRY(upload(d_gw, gw));
+    DG_TRY(upload(d_aggbox, P.agg_bbox));
+    DG_TRY(pc->r0t.alloc(sizeof(double) * (size_t)ne * np * nq));
+    DG_CUDA(launch_r0t(pc->perm.as<int>(), s->d_xy.as<double>(), s->d_pptr.as<int>(), s->d_pvtx.as<int>(),
+                       s->d_bbox.as<double>(), pc->agg_int.as<int>(), d_aggbox.as<double>(), ne, s->p, q,
+                       d_gt.as<double>(), d_gw.as<double>(), mq, pc->r0t.as<double>(), st));
+    DevBuf A0;
+    DG_TRY(A0.alloc(sizeof(double) * (size_t)n0 * n0));
+    DG_CUDA(cudaMemsetAsync(A0.ptr, 0, A0.bytes, st));
+    DG_CUDA(launch_galerkin(pc->grp_ptr.as<int>(), pc->grp_elems.as<int>(), pc->agg_int.as<int>(), pc->rowptr.as<int>(),
+                            pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), P.nagg, np, np2s, nq,
+                            A0.as<double>(), st));
+    DG_TRY(upload_env(P.env0, pc->env0));
+    DevBuf scale0, Lr0, Lc0;
+    DG_TRY(scale0.alloc(sizeof(double) * n0));
+    const size_t t0 = (size_t)P.env0.ntiles * TILE * TILE;
+    DG_TRY(Lr0.alloc(sizeof(double) * t0));
+    DG_CUDA(cudaMemsetAsync(Lr0.ptr, 0, Lr0.bytes, st));
+    DG_CUDA(launch_coarse_extract(A0.as<double>(), n0, scale0.as<double>(), pc->env0.dev, Lr0.as<double>(), st));
+    nl += 4;
+    DG_TRY(factor_env(DGASM_FP64, P.env0, pc->env0, Lr0.ptr, pc->err.as<int>() + 4, st, ev, &nl));
+    DG_TRY(Lc0.alloc(sizeof(double) * t0));
+    DG_CUDA(launch_to_colmajor(0, Lr0.ptr, Lc0.ptr, P.env0.ntiles, st));
+    {
+      DevBuf Lb0;
+      DG_TRY(Lb0.alloc(sizeof(double) * t0));
+      DG_CUDA(launch_gather_tiles(0, Lr0.ptr, pc->env0.bwd_src.as<long long>(), Lb0.ptr, P.env0.ntiles, st));
+      DG_CUDA(cudaStreamSynchronize(st));
+      Lr0 = std::move(Lb0);
+    }
+    // A_0^{-1} = columns of the local-solve kernel applied to the identity
+    DG_TRY(pc->A0inv.alloc(sizeof(double) * (size_t)n0 * n0));
+    DG_TRY(pc->coarse_inverse(scale0, Lr0, Lc0));
+    nl += 3;
+  }
+  // check factorisation errors
+  int herr[8];
+  DG_CUDA(cudaMemcpyAsync(herr, pc->err.ptr, sizeof(herr), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (herr[0]) return set_error(DGASM_ENOTSPD, "non-positive pivot in the Cholesky factor of subdomain %d at row %d", herr[1], herr[2]);
+  if (herr[4]) return set_error(DGASM_ENOTSPD, "non-positive pivot in the Cholesky factor of the coarse operator A_0");
+  if (ev) ev->accumulate();
+  pc->setup_launches = nl;
+  pc->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - pc->t_start).count();
+  pc->src_blk.reset();
+  return DGASM_OK;
+}
+
+}  // namespace dgasm
+
+extern "C" int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_prec_t* out) {
+  clear_error();
+  if (!out) return set_error(DGASM_EINVAL, "dgasm_setup: out is NULL");
+  *out = nullptr;
+  std::unique_ptr<dgasm_prec_s> pc;
+  DG_TRY(prec_plan(s, o, pc));
+  DG_TRY(prec_build(pc.get()));
+  *out = pc.release();
+  return DGASM_OK;
+}
+
+
+// ---- dgasm_prec_s members ----------------------------------------------------------------------------
+int dgasm_prec_s::init_streams(void* user_stream) {
+  if (user_stream) {
+    stream = (cudaStream_t)user_stream;
+  } else {
+    DG_CUDA(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
+    stream = own_stream;
+  }
+  DG_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  DG_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  DG_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  return DGASM_OK;
+}
+
+dgasm_prec_s::~dgasm_prec_s() {
+  engine.reset();
+  if (side) cudaStreamDestroy(side);
+  if (own_stream) cudaStreamDestroy(own_stream);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+}
+
+int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
+  const int n0 = this->n0;
+  cudaStream_t st = stream;
+  // a one-subdomain problem with n0 right-hand sides: the unit vectors
+  DevBuf ident, sub_e0c, misc, probs, prefix;
+  DG_TRY(ident.alloc(sizeof(double) * (size_t)n0 * n0));
+  DG_CUDA(launch_identity(ident.as<double>(), n0, st));
+  std::vector<int> se{0, 1};
+  DG_TRY(upload(sub_e0c, se));
+  const int chunks = (n0 + KC - 1) / KC;
+  const size_t rz_off = (sizeof(int) * (n0 + 2) + 15) & ~(size_t)15;
+  DG_TRY(misc.alloc(rz_off + sizeof(double) * (size_t)n0));
+  DG_CUDA(cudaMemsetAsync(misc.ptr, 0, misc.bytes, st));
+  ProbDev D;
+  std::memset(&D, 0, sizeof(D));
+  D.np = n0; D.ndof = n0; D.nsub = 1; D.k = n0; D.kc = KC; D.n_rhs_chunks = chunks; D.prec = DGASM_FP64;
+  D.sub_e0 = sub_e0c.as<int>(); D.sub_trow = env0.sub_trow.as<int>(); D.trow_F = env0.trow_F.as<int>();
+  D.trow_ptr = env0.trow_ptr.as<long long>(); D.Lr = Lr0.ptr; D.Lc = Lc0.ptr; D.scale = scale0.as<double>();
+  D.r = ident.as<double>(); D.z = A0inv.as<double>();
+  D.done = (int*)misc.ptr;
+  D.part_rz = (double*)((char*)misc.ptr + rz_off);
+  std::vector<ProbDev> hp{D};
+  DG_TRY(probs.alloc(sizeof(ProbDev)));
+  DG_CUDA(cudaMemcpyAsync(probs.ptr, hp.data(), sizeof(ProbDev), cudaMemcpyHostToDevice, st));
+  std::vector<int> pre{0, chunks};
+  DG_TRY(prefix.alloc(sizeof(int) * 2));
+  DG_CUDA(cudaMemcpyAsync(prefix.ptr, pre.data(), sizeof(int) * 2, cudaMemcpyHostToDevice, st));
+  BatchDev B;
+  std::memset(&B, 0, sizeof(B));
+  B.probs = probs.as<ProbDev>();
+  B.nprob = 1;
+  B.err = (int*)misc.ptr + n0;
+  const int slot = K_NKINDS + 2 * DGASM_FP64 + 1;
+  B.prefix[slot] = prefix.as<int>();
+  DG_CUDA(launch_local(B, slot, chunks, local_smem_bytes(DGASM_FP64, n0, KC), st));
+  int herr = 0;
+  DG_CUDA(cudaMemcpyAsync(&herr, B.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (herr) return set_error(DGASM_ECUDA, "a bounded wait in the coarse inverse gave up (error word set)");
+  return DGASM_OK;
+}
+
+size_t dgasm_prec_s::footprint() const {
+  size_t b = perm.bytes + rowptr.bytes + col.bytes + vals.bytes + sub_e0.bytes + scale.bytes + Lr.bytes + Lc.bytes +
+             grp_ptr.bytes + grp_elems.bytes + agg_int.bytes + r0t.bytes + A0inv.bytes + err.bytes;
+  const EnvBufs* es[2] = {&env, &env0};
+  for (const EnvBufs* e : es)
+    b += e->ndof.bytes + e->sub_trow.bytes + e->trow_F.bytes + e->trow_ptr.bytes + e->diag_task.bytes +
+         e->panel_task.bytes + e->upd_task.bytes + e->bwd_src.bytes;
+  return b;
+}
+
+extern "C" int dgasm_prec_partition(dgasm_prec_t pc, int* sub, int* agg) {
+  if (!pc) return set_error(DGASM_EINVAL, "NULL preconditioner");
+  if (sub) std::copy(pc->P.sub_of.begin(), pc->P.sub_of.end(), sub);
+  if (agg && !pc->P.agg_of.empty()) std::copy(pc->P.agg_of.begin(), pc->P.agg_of.end(), agg);
+  return DGASM_OK;
+}
+
+extern "C" int dgasm_prec_footprint(dgasm_prec_t pc, int64_t* bytes) {
+  if (!pc || !bytes) return set_error(DGASM_EINVAL, "NULL argument");
+  *bytes = (int64_t)pc->footprint();
+  return DGASM_OK;
+}
+
+extern "C" int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info) {
+  if (!pc || !info) return set_error(DGASM_EINVAL, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  const Plan& P = pc->P;
+  info->nsub = P.nsub;
+  info->nagg = P.nagg;
+  info->n0 = pc->n0;
+  info->precision = pc->precision;
+  info->local_dofs = (int64_t)P.ne * P.np;
+  info->local_tiles = P.env.ntiles;
+  int64_t upd = (int64_t)P.env.upd_task.size() / 3, pan = (int64_t)P.env.panel_task.size() / 2, dg = (int64_t)P.env.diag_task.size();
+  const int64_t t3 = (int64_t)TILE * TILE * TILE;
+  info->factor_flops = upd * 2 * t3 + pan * t3 + dg * (t3 / 3 + t3 / 3);
+  info->nnzb = (int64_t)P.col.size();
+  info->plan_ms = pc->plan_ms;
+  info->setup_ms = pc->setup_ms;
+  info->setup_launches = pc->setup_launches;
+  return DGASM_OK;
+}
+
+extern "C" int dgasm_prec_destroy(dgasm_prec_t pc) {
+  delete pc;
+  return DGASM_OK;
+}
+

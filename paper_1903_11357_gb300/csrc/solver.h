@@ -1,6 +1,8 @@
 // Preconditioner handle and batched-solve state (host side).
 #pragma once
 
+#include <chrono>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -9,11 +11,12 @@
 #include "common.h"
 #include "engine.h"
 #include "plan.h"
+#include "profile.h"
 
 namespace dgasm {
 
 struct EnvBufs {
-  DevBuf ndof, sub_trow, trow_F, trow_ptr, diag_task, panel_task, upd_task;
+  DevBuf ndof, sub_trow, trow_F, trow_ptr, diag_task, panel_task, upd_task, bwd_src;
   EnvDev dev{};
 };
 
@@ -28,18 +31,55 @@ struct Workspace {
             double rtol) const;
 };
 
-struct BatchState {
+// A batch of problems prepared for the batched kernels: device descriptor tables, item prefix sums,
+// a captured graph of CHUNK iterations, and the event pairs used when profiling.
+struct Engine {
+  static constexpr int CHUNK = 8;
+  int nprob = 0;
+  std::vector<dgasm_prec_s*> pcs;
+  std::vector<int> nrhs;
+  std::vector<ProbDev> hp;
+  std::vector<int> pre;
+  int max_smem[8] = {0};
+  int tot_spmv = 0, tot_grp = 0, tot_coarse = 0;
+  int total_rhs = 0;
   DevBuf tables;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int* d_remaining = nullptr;
+  int* d_err = nullptr;
   int* h_remaining = nullptr;
-  int launches = 0;
-  float ms = 0.f;
-  BatchState();
-  ~BatchState();
+  BatchDev B{};
+  cudaStream_t stream = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev0 = nullptr, ev1 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int per_iter_launches = 0;
+  long long launches = 0;
+  EventPairs init_ev, graph_ev;
+  Engine();
+  ~Engine();
+  Engine(const Engine&) = delete;
+  Engine& operator=(const Engine&) = delete;
+  // Prepares the tables; `remaining` = right-hand sides not yet done (-1: all, for a fresh solve).
+  int build(int n, dgasm_prec_s* const* pcs, const int* nrhs, const double* const* b, double* const* x,
+            const dgasm_solve_opts* const* opts, cudaStream_t stream, int remaining);
+  int reset_state();                 // clears done flags, counters and iteration counts
+  int init();                        // r = b, z = B r, p = z, gamma = (r, z)
+  int iterate(int max_iters, int* ran);  // CHUNK-iteration graphs until all done or max_iters
+  int finish();                      // true residual and x in the caller's order
+  int apply_out();                   // z = B r into the caller's buffer (preconditioner apply)
+  // statistics of every right-hand side (problem order); per-problem return codes in rcs if given
+  int collect(dgasm_stats* st, double ms, std::vector<int>* rcs);
+  // per problem: 1 when all its right-hand sides are done; not_done_rhs counts the open ones
+  int read_done(std::vector<int>& done, int* not_done_rhs);
+ private:
+  int precond(int mode, EventPairs* ev);
+  int spmv(int operand, EventPairs* ev);
 };
 
-int run_batch(int nprob, dgasm_prec_s* const* pcs, const int* nrhs, const double* const* b, double* const* x,
-              const dgasm_solve_opts* o, dgasm_stats* st, BatchState& S, bool apply_only);
+int solve_all(Engine& E, int n, dgasm_prec_s* const* pcs, const int* nrhs, const double* const* b, double* const* x,
+              const dgasm_solve_opts* o, cudaStream_t stream, dgasm_stats* st);
+int prec_plan(dgasm_system_s* s, const dgasm_setup_opts* o, std::unique_ptr<dgasm_prec_s>& pc);
+size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit);
+int prec_build(dgasm_prec_s* pc);
 
 }  // namespace dgasm
 
@@ -48,13 +88,16 @@ struct dgasm_prec_s {
   dgasm::Plan P;
   int precision = DGASM_FP64;
   int n0 = 0;
+  double plan_ms = 0, setup_ms = 0;
+  std::chrono::steady_clock::time_point t_start;
+  int setup_launches = 0;
   cudaStream_t stream = nullptr, own_stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
   dgasm::DevBuf perm, rowptr, col, vals, src_blk, sub_e0, scale, Lr, Lc, grp_ptr, grp_elems, agg_int, r0t, A0inv, err, io;
   dgasm::EnvBufs env, env0;
   dgasm::Workspace ws;
-  dgasm::BatchState bstate;
+  dgasm::EventPairs setup_ev;
+  std::unique_ptr<dgasm::Engine> engine;  // reused by dgasm_solve
   std::mutex mu;
   int init_streams(void* user_stream);
   int coarse_inverse(dgasm::DevBuf& scale0, dgasm::DevBuf& Lr0, dgasm::DevBuf& Lc0);

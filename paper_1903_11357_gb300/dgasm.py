@@ -36,7 +36,17 @@ class SolveOpts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres", C.c_double), ("true_relres", C.c_double),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("kappa", C.c_double),
-                ("solve_ms", C.c_double)]
+                ("solve_ms", C.c_double), ("launches", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PrecInfo(C.Structure):
+    _fields_ = [("nsub", C.c_int), ("nagg", C.c_int), ("n0", C.c_int), ("precision", C.c_int),
+                ("local_dofs", C.c_int64), ("local_tiles", C.c_int64), ("factor_flops", C.c_int64),
+                ("nnzb", C.c_int64), ("plan_ms", C.c_double), ("setup_ms", C.c_double),
+                ("setup_launches", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -83,6 +93,17 @@ def lib():
                                   C.POINTER(Stats)],
             "dgasm_lanczos": [C.c_int, dp, dp, dp, dp],
             "dgasm_set_allocator": [vp, vp, vp],
+            "dgasm_prec_info": [vp, C.c_void_p],
+            "dgasm_profile_enable": [C.c_int],
+            "dgasm_profile_read": [C.c_int, dp, i64p, C.c_int],
+            "dgasm_server_create": [C.c_size_t, C.c_int, vp, C.POINTER(vp)],
+            "dgasm_submit": [vp, vp, C.POINTER(SetupOpts), C.c_int, vp, vp, C.POINTER(SolveOpts),
+                             C.POINTER(C.c_uint64)],
+            "dgasm_poll": [vp, C.c_uint64, C.POINTER(Stats)],
+            "dgasm_wait": [vp, C.c_uint64, C.c_int, C.POINTER(Stats)],
+            "dgasm_cancel": [vp, C.c_uint64],
+            "dgasm_server_stats": [vp, i64p, i64p, i64p, i64p],
+            "dgasm_server_destroy": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -245,6 +266,11 @@ class Prec:
         check(lib().dgasm_prec_partition(self.h, _ip(sub), _ip(agg)))
         return sub, agg
 
+    def info(self):
+        i = PrecInfo()
+        check(lib().dgasm_prec_info(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
     def footprint(self):
         b = C.c_int64()
         check(lib().dgasm_prec_footprint(self.h, C.byref(b)))
@@ -294,3 +320,88 @@ def lanczos(alphas, betas):
     lo, hi = C.c_double(), C.c_double()
     check(lib().dgasm_lanczos(len(a), _dp(a), _dp(b), C.byref(lo), C.byref(hi)))
     return lo.value, hi.value
+
+
+PROFILE_KINDS = ["spmv", "update", "local", "coarse", "pupdate", "chol_diag", "chol_panel", "chol_update"]
+
+
+def profile_enable(on=True):
+    check(lib().dgasm_profile_enable(1 if on else 0))
+
+
+def profile_read(reset=False):
+    """{kind: (total_ms, launches)} accumulated since the last reset."""
+    out = {}
+    for i, name in enumerate(PROFILE_KINDS):
+        ms, n = C.c_double(), C.c_int64()
+        check(lib().dgasm_profile_read(i, C.byref(ms), C.byref(n), 1 if reset else 0))
+        out[name] = (ms.value, n.value)
+    return out
+
+
+class Server:
+    """Continuous-batching solve server (dgasm_server_*)."""
+
+    def __init__(self, hbm_budget: int, max_slots: int, stream=None):
+        h = C.c_void_p()
+        check(lib().dgasm_server_create(int(hbm_budget), int(max_slots), _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, system: System, nsub, ncoarse, p_c, b, x, precision="fp64", rtol=1e-8, maxit=10000,
+               sub_of_elem=None, agg_of_elem=None):
+        o = SetupOpts()
+        o.nsub, o.ncoarse, o.p_c = nsub, ncoarse, p_c
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        keep = [b, x]
+        if sub_of_elem is not None:
+            a = np.ascontiguousarray(sub_of_elem, np.int32)
+            keep.append(a)
+            o.sub_of_elem = _ip(a)
+        if agg_of_elem is not None:
+            a = np.ascontiguousarray(agg_of_elem, np.int32)
+            keep.append(a)
+            o.agg_of_elem = _ip(a)
+        so = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=0, x0_given=0, host_buffers=0, stream=None)
+        k = 1 if b.dim() == 1 else b.shape[0]
+        t = C.c_uint64()
+        check(lib().dgasm_submit(self.h, system.h, C.byref(o), k, _dev_ptr(b), _dev_ptr(x), C.byref(so), C.byref(t)))
+        self._keep[t.value] = (keep, k)
+        return t.value
+
+    def _result(self, ticket, rc, st):
+        if rc == PENDING:
+            return rc, None
+        keep = self._keep.pop(ticket, None)
+        k = keep[1] if keep else 1
+        if rc < 0 and rc != ENOCONV:
+            return rc, None
+        return rc, [st[i].as_dict() for i in range(k)]
+
+    def poll(self, ticket):
+        st = (Stats * 8)()
+        rc = lib().dgasm_poll(self.h, ticket, st)
+        return self._result(ticket, rc, st)
+
+    def wait(self, ticket, timeout_ms=-1):
+        st = (Stats * 8)()
+        rc = lib().dgasm_wait(self.h, ticket, int(timeout_ms), st)
+        if rc == ETIMEOUT:
+            return rc, None
+        return self._result(ticket, rc, st)
+
+    def cancel(self, ticket):
+        return lib().dgasm_cancel(self.h, ticket)
+
+    def stats(self):
+        v = [C.c_int64() for _ in range(4)]
+        check(lib().dgasm_server_stats(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(["done", "rounds", "stalls", "bytes_in_use"], [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dgasm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
