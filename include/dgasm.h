@@ -128,6 +128,22 @@ int dgasm_system_blocks(dgasm_system_t s, int64_t* nnzb, int* rowptr, int* col, 
 int dgasm_system_spmv(dgasm_system_t s, const double* x, double* y, void* stream);
 int dgasm_system_destroy(dgasm_system_t s);
 
+/* y = A x and the energy product x^T A x, without any device allocation (the paper has no counterpart:
+ * this serves callers that cannot allocate, e.g. code running inside a CUDA stream capture, where
+ * cudaMalloc cannot be captured, code whose device memory belongs to another runtime's caching
+ * allocator, or real-time loops that forbid allocation after start-up).  x, y are device arrays of ndof
+ * doubles in the caller's dof order, xAx a device pointer to one double; all three are the caller's.
+ * The per-block partial sums live in a fixed 512 KB (+256 B) __device__ array inside the library, so a
+ * call handles at most 65536 thread blocks of 256 threads (65536 * floor(256 / n_p) elements, e.g.
+ * 1.6 million elements at p = 3); larger systems get DGASM_ETOOBIG.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  The array is shared by every call on a device and keeps the last call's
+ * contents (its counter is cleared at the start of each call), so calls that overlap on the GPU (on
+ * different streams, or from different threads) race: serialise them.  The matrix must already be on
+ * the device (dgasm_system_spmv or dgasm_setup upload it on first use); otherwise DGASM_EINVAL.
+ * Asynchronous on the stream; y is bitwise identical to dgasm_system_spmv's. */
+int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, double* y, double* xAx, void* stream);
+
 /* ---- Two-level Schwarz preconditioner (Sec. 3: local solvers, coarse solver, Eq. R0T, Eq. A0) --- */
 typedef struct {
   int nsub;                 /* number of subdomains (1..ne); ignored if sub_of_elem is given */

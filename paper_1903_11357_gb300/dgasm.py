@@ -104,6 +104,7 @@ def lib():
             "dgasm_cancel": [vp, C.c_uint64],
             "dgasm_server_stats": [vp, i64p, i64p, i64p, i64p],
             "dgasm_server_destroy": [vp],
+            "dgasm_system_spmv_dot_noalloc": [vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
