@@ -37,8 +37,11 @@ struct ProbDev {
   const int* sub_trow;
   const int* trow_F;
   const long long* trow_ptr;
-  const void* Lr;     // row-major tiles in backward-sweep order (diagonal tiles hold inv(L_II))
-  const void* Lc;     // column-major tiles in storage order (forward sweep)
+  const long long* stream_ptr;  // [nsub+1] offsets of each subdomain's solve streams
+  const int* sub_sr;            // [nsub+1] first global super-row of each subdomain
+  const int* sr_ilast;          // per global super-row: last tile row coupled to its columns
+  const void* Lr;     // backward stream: row-major tiles in consumption order
+  const void* Lc;     // forward stream: column-major tiles in consumption order
   const double* scale;
   // groups and coarse space
   const int* grp_ptr;
@@ -108,6 +111,12 @@ int launch_to_colmajor(int prec, const void* Lr, void* Lc, long long ntiles, voi
 int launch_to_bf16(const float* src, void* dst, long long n, void* stream);
 // dst tile t = src tile idx[t] (same element layout), for the backward-ordered copy of a factor
 int launch_gather_tiles(int prec, const void* src, const long long* idx, void* dst, long long ntiles, void* stream);
+// inverse blocks of the super-rows (task triples: subdomain, first tile row, tile rows)
+int launch_dinv(int prec, const EnvDev& E, const void* L, const int* task, const long long* dinv_ptr, void* X, int nsr,
+                void* stream);
+// solve streams from factor tiles (src >= 0) and inverse-block tiles (src < 0)
+int launch_stream_gather(int prec, const void* L, const void* X, const long long* src, void* dst, long long n,
+                         int transpose, void* stream);
 int launch_r0t(const int* perm, const double* xy, const int* pptr, const int* pvtx, const double* bbox,
                const int* agg_int, const double* agg_bbox, int ne, int p, int q, const double* gl_t,
                const double* gl_w, int mq, double* r0t, void* stream);

@@ -31,6 +31,7 @@ namespace {
 
 constexpr int T = 32;
 constexpr int TT = T * T;
+constexpr int SR = 4;                  // tile rows per super-row (matches the plan)
 constexpr int NCW = 8;                 // consumer warps
 constexpr int NCT = NCW * 32;          // consumer threads
 constexpr int NTH = NCT + 32;          // + producer warp
@@ -122,6 +123,8 @@ __device__ __forceinline__ void gemv4(const S* __restrict__ tile, const C* __res
 
 template <typename S, typename C, int KCT>
 __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_off, int nstage, int ch) {
+  constexpr int NCH = KCT == 1 ? 2 : 1;   // independent accumulation chains per coupling accumulator
+  constexpr int DCH = KCT == 1 ? 2 : 1;   // and per diagonal-block accumulator
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[NCW + 1][KCT];
   __shared__ int abort_flag;
@@ -145,17 +148,18 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
   const int n = (P.sub_e0[s + 1] - e0) * P.np;
   const long long d0 = (long long)e0 * P.np;
   const int nbt = (n + T - 1) / T, npad = nbt * T;
+  const int nsr = (nbt + SR - 1) / SR;
   const int tr0 = P.sub_trow[s];
-  const long long f0 = P.trow_ptr[tr0];
-  const long long ntile = P.trow_ptr[tr0 + nbt - 1] + (nbt - 1 - P.trow_F[tr0 + nbt - 1]) + 1 - f0;
-  C* y = reinterpret_cast<C*>(smem);                 // [KCT][npad]
-  C* part = y + KCT * npad;                           // [NCW][KCT][T]
-  C* tmp = part + 2 * NCW * KCT * T;                  // [KCT][T], then the tile-row F values
-  S* ring = reinterpret_cast<S*>(smem + ring_off);    // [nstage][ch][TT]
+  const long long f0 = P.stream_ptr[s];
+  const long long nstream = P.stream_ptr[s + 1] - f0;
+  C* y = reinterpret_cast<C*>(smem);                  // [KCT][npad]
+  C* part = y + KCT * npad;                            // [NCW][SR][KCT][T]
+  C* dpart = part + NCW * SR * KCT * T;                // [NCW][SR][KCT][T]
+  C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR * 4][KCT]
+  int* Fs = reinterpret_cast<int*>(tvs + NCW * SR * 4 * KCT);   // tile-row F values
+  S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][ch][TT]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * ch * TT);
   unsigned long long* empty = full + nstage;
-  const S* Lc = reinterpret_cast<const S*>(P.Lc);
-  const S* Lr = reinterpret_cast<const S*>(P.Lr);
   if (tid == 0) {
     abort_flag = 0;
     for (int i = 0; i < nstage; ++i) {
@@ -167,18 +171,18 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
   __syncthreads();
 
   if (w == NCW) {
-    // ---- producer: forward tiles in the storage order of Lc (row by row, diagonal last), then for each
-    // column J from the last: the tiles (I, J), I > J, of the row-major copy Lr, and the diagonal (J, J)
+    // ---- producer: the forward stream, then the backward stream, nstream tiles each, in chunks of ch
+    // consecutive tiles (one bulk copy per chunk)
     if (lane == 0) {
-      // two contiguous streams of ntile tiles each (forward: Lc, backward: Lr), each cut into chunks of
-      // CH consecutive tiles, one bulk copy per chunk
+      const S* Lc = reinterpret_cast<const S*>(P.Lc);
+      const S* Lr = reinterpret_cast<const S*>(P.Lr);
       int sl = 0;
       unsigned round = 0;   // how many times the ring has wrapped
       bool ok = true;
       for (int pass = 0; pass < 2 && ok; ++pass) {
         const S* base = (pass == 0 ? Lc : Lr) + f0 * TT;
-        for (long long t = 0; t < ntile && ok; t += ch) {
-          const int len = (int)min((long long)ch, ntile - t);
+        for (long long t = 0; t < nstream && ok; t += ch) {
+          const int len = (int)min((long long)ch, nstream - t);
           if (round > 0 && !mbar_wait(empty + sl, (round - 1) & 1, &abort_flag, B.err)) { ok = false; break; }
           const unsigned bytes = (unsigned)(len * TT * sizeof(S));
           mbar_expect_tx(full + sl, bytes);
@@ -188,9 +192,8 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
       }
     }
   } else {
-    // ---- consumers: warp w owns tile columns (forward) / tile rows (backward) c0 .. c0+3
+    // ---- consumers: warp w owns tile columns (forward) / tile rows (backward) c0 .. c0+3 of every tile
     const int c0 = 4 * w;
-    int* Fs = reinterpret_cast<int*>(tmp + KCT * T);   // trow_F of this subdomain
     for (int i = tid; i < nbt; i += NCT) Fs[i] = P.trow_F[tr0 + i];
     for (int idx = tid; idx < KCT * npad; idx += NCT) {
       const int j = idx / npad, i = idx - j * npad;
@@ -199,20 +202,15 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
       y[idx] = v;
     }
     consumer_sync();
-    C* dpart = part + NCW * KCT * T;   // second partial buffer (diagonal products)
-    // one tile row: acc = sum of the off-diagonal tiles (already accumulated by the caller), then
-    // t = y_R - sum_w acc_w on this warp's chunk, o = diagonal tile times t, y_R = sum_w o_w
-    // consumer cursor: ring slot, its phase parity, position inside the chunk, and the chunk length
+    // stream cursor: ring slot, its phase parity, position in the chunk, chunk length
     int cs = 0, cpos = 0;
     unsigned cph = 0;
-    long long taken = 0;   // tiles consumed in the current stream (forward, then backward)
-    int clen = (int)min((long long)ch, ntile);
-    // waits for the chunk holding the next tile; returns its address or nullptr after an abort
+    long long taken = 0;
+    int clen = (int)min((long long)ch, nstream);
     auto acquire = [&]() -> const S* {
       if (cpos == 0 && !mbar_wait(full + cs, cph, &abort_flag, B.err)) return nullptr;
       return ring + ((size_t)cs * ch + cpos) * TT;
     };
-    // releases the tile; the chunk goes back to the producer after its last tile
     auto release = [&]() {
       ++taken;
       if (++cpos == clen) {
@@ -220,91 +218,154 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
         if (lane == 0) mbar_arrive(empty + cs);
         cpos = 0;
         if (++cs == nstage) { cs = 0; cph ^= 1u; }
-        if (taken == ntile) taken = 0;   // the backward stream starts with a fresh chunk
-        clen = (int)min((long long)ch, ntile - taken);
+        if (taken == nstream) taken = 0;   // the backward stream starts with a fresh chunk
+        clen = (int)min((long long)ch, nstream - taken);
       }
     };
-    auto finish_row = [&](int R, C* acc) {
+    // Lane l reduces block entry e = l >> 1 (tile row e >> 2 of the super-row, line c0 + (e & 3)) over
+    // four warps' partials (half l & 1), then across the two halves: a fixed order on every warp.
+    const int re = lane >> 1, rii = re >> 2, ru = re & 3, rh = lane & 1;
+    auto reduce_entry = [&](const C* buf, int j) -> C {
+      C v = buf[(((4 * rh) * SR + rii) * KCT + j) * T + c0 + ru];
 #pragma unroll
-      for (int j = 0; j < KCT; ++j) part[(w * KCT + j) * T + lane] = acc[j];
+      for (int ww = 1; ww < 4; ++ww) v += buf[(((4 * rh + ww) * SR + rii) * KCT + j) * T + c0 + ru];
+      return v + shfl_xor_c(v, 1);
+    };
+    C* tw = tvs + w * SR * 4 * KCT;   // this warp's right-hand sides of the diagonal block product
+    // one super-row (tile rows I0 .. I0+ntr-1): acc holds the coupling sums; t = y_S - sum over warps,
+    // y_S = X t (forward) or X^T t (backward) with X the inverse of the diagonal block
+    auto finish_super = [&](int I0, int ntr, C (*acc)[KCT][NCH], bool fwd) {
+#pragma unroll
+      for (int ii = 0; ii < SR; ++ii)
+#pragma unroll
+        for (int j = 0; j < KCT; ++j) {
+          C v = (C)0;
+#pragma unroll
+          for (int h = 0; h < NCH; ++h) v += acc[ii][j][h];
+          part[((w * SR + ii) * KCT + j) * T + lane] = ii < ntr ? v : (C)0;
+        }
       consumer_sync();
-      // lane l reduces entry c0 + (l >> 3) over the eight warps' partials (l & 7): a fixed
-      // three-step shuffle tree, so each warp spends four FP64 additions per right-hand side
-      const int ru = lane >> 3, rw = lane & 7;
-      C tv[KCT * 4];
 #pragma unroll
       for (int j = 0; j < KCT; ++j) {
-        C v = part[(rw * KCT + j) * T + c0 + ru];
-        v += shfl_xor_c(v, 1);
-        v += shfl_xor_c(v, 2);
-        v += shfl_xor_c(v, 4);
-        const C t = y[j * npad + R * T + c0 + ru] - v;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) tv[j * 4 + u] = shfl_c(t, u * 8);
+        const C tot = reduce_entry(part, j);
+        const C t = rii < ntr ? y[j * npad + (I0 + rii) * T + c0 + ru] - tot : (C)0;
+        if (rh == 0) tw[re * KCT + j] = t;
       }
-      C o[KCT];
+      __syncwarp();
+      C o[SR][KCT][DCH];
 #pragma unroll
-      for (int j = 0; j < KCT; ++j) o[j] = (C)0;
-      const S* dtile = acquire();
-      if (dtile) {
-        const S* tl = dtile + c0 * T + lane;
-        C t[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) t[u] = cvt<S, C>(tl[u * T]);
+      for (int ii = 0; ii < SR; ++ii)
 #pragma unroll
         for (int j = 0; j < KCT; ++j)
-          o[j] = fma(t[0], tv[j * 4], t[1] * tv[j * 4 + 1]) + fma(t[2], tv[j * 4 + 2], t[3] * tv[j * 4 + 3]);
-      }
-      release();
 #pragma unroll
-      for (int j = 0; j < KCT; ++j) dpart[(w * KCT + j) * T + lane] = o[j];
+          for (int h = 0; h < DCH; ++h) o[ii][j][h] = (C)0;
+#pragma unroll
+      for (int i = 0; i < SR; ++i) {
+        if (i >= ntr) break;
+#pragma unroll
+        for (int jj = 0; jj <= i; ++jj) {
+          const S* tile = acquire();
+          if (tile) {
+            const S* tl = tile + c0 * T + lane;
+            C tv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tv[u] = cvt<S, C>(tl[u * T]);
+            // forward: X_(i,jj) times block jj into output block i; backward: X_(i,jj)^T times block i
+            // into output block jj
+            const int src = fwd ? jj : i;
+#pragma unroll
+            for (int j = 0; j < KCT; ++j) {
+              const C* vv = tw + (src * 4) * KCT + j;
+              C& x = fwd ? o[i][j][jj % DCH] : o[jj][j][i % DCH];
+              x = fma(tv[0], vv[0], x);
+              x = fma(tv[1], vv[KCT], x);
+              x = fma(tv[2], vv[2 * KCT], x);
+              x = fma(tv[3], vv[3 * KCT], x);
+            }
+          }
+          release();
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < SR; ++ii)
+#pragma unroll
+        for (int j = 0; j < KCT; ++j) {
+          C v = o[ii][j][0];
+#pragma unroll
+          for (int h = 1; h < DCH; ++h) v += o[ii][j][h];
+          dpart[((w * SR + ii) * KCT + j) * T + lane] = v;
+        }
       consumer_sync();
 #pragma unroll
       for (int j = 0; j < KCT; ++j) {
-        C v = dpart[(rw * KCT + j) * T + c0 + ru];
-        v += shfl_xor_c(v, 1);
-        v += shfl_xor_c(v, 2);
-        v += shfl_xor_c(v, 4);
-        if (rw == 0) y[j * npad + R * T + c0 + ru] = v;
+        const C tot = reduce_entry(dpart, j);
+        if (rh == 0 && rii < ntr) y[j * npad + (I0 + rii) * T + c0 + ru] = tot;
       }
       __syncwarp();
     };
-    // forward substitution
-    for (int I = 0; I < nbt; ++I) {
-      const int F = Fs[I];
-      const int nt = I - F;
-      C acc4[KCT][4];   // four accumulation chains, added in a fixed order at the end of the row
+    C acc[SR][KCT][NCH];
+    auto zero_acc = [&]() {
 #pragma unroll
-      for (int j = 0; j < KCT; ++j)
+      for (int ii = 0; ii < SR; ++ii)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc4[j][u] = (C)0;
-      for (int jt = 0; jt < nt; ++jt) {
-        const S* tile = acquire();
-        if (tile) gemv4<S, C, KCT>(tile + c0 * T + lane, y + (F + jt) * T + c0, npad, acc4);
-        release();
+        for (int j = 0; j < KCT; ++j)
+#pragma unroll
+          for (int h = 0; h < NCH; ++h) acc[ii][j][h] = (C)0;
+    };
+    // one coupling tile: a[j][0] += sum_u tile line (c0+u) * v[j][c0+u], then the chains rotate so the
+    // next tile accumulates into the next chain (static register indices throughout)
+    auto couple = [&](const S* tile, const C* v, C (&a)[KCT][NCH]) {
+      const S* tl = tile + c0 * T + lane;
+      C tv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) tv[u] = cvt<S, C>(tl[u * T]);
+#pragma unroll
+      for (int j = 0; j < KCT; ++j) {
+        const C* vj = v + j * npad;
+        C x = a[j][0];
+        x = fma(tv[0], vj[0], x);
+        x = fma(tv[1], vj[1], x);
+        x = fma(tv[2], vj[2], x);
+        x = fma(tv[3], vj[3], x);
+#pragma unroll
+        for (int h = 0; h + 1 < NCH; ++h) a[j][h] = a[j][h + 1];
+        a[j][NCH - 1] = x;
       }
-      C acc[KCT];
+    };
+    // forward substitution, super-row by super-row
+    for (int q = 0; q < nsr; ++q) {
+      const int I0 = q * SR, ntr = min(SR, nbt - I0);
+      zero_acc();
 #pragma unroll
-      for (int j = 0; j < KCT; ++j) acc[j] = (acc4[j][0] + acc4[j][1]) + (acc4[j][2] + acc4[j][3]);
-      finish_row(I, acc);
+      for (int ii = 0; ii < SR; ++ii) {
+        if (ii >= ntr) break;
+        for (int J = Fs[I0 + ii]; J < I0; ++J) {
+          const S* tile = acquire();
+          if (tile) couple(tile, y + J * T + c0, acc[ii]);
+          release();
+        }
+      }
+      finish_super(I0, ntr, acc, true);
     }
-    // backward substitution with L^T, column by column
-    for (int J = nbt - 1; J >= 0; --J) {
-      C acc4[KCT][4];
+    // backward substitution with L^T, super-row by super-row from the last: the tile rows I after the
+    // super-row that couple to its columns, each with its tiles (I, J), J ascending
+    for (int q = nsr - 1; q >= 0; --q) {
+      const int I0 = q * SR, ntr = min(SR, nbt - I0), I1 = I0 + ntr;
+      const int Ilast = P.sr_ilast[P.sub_sr[s] + q];
+      zero_acc();
+      for (int I = I1; I <= Ilast; ++I) {
+        const int FI = Fs[I];
+        if (FI > I1 - 1) continue;
+        const int jstart = FI > I0 ? FI - I0 : 0;
 #pragma unroll
-      for (int j = 0; j < KCT; ++j)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc4[j][u] = (C)0;
-      for (int I = J + 1; I < nbt; ++I) {
-        if (Fs[I] > J) continue;
-        const S* tile = acquire();
-        if (tile) gemv4<S, C, KCT>(tile + c0 * T + lane, y + I * T + c0, npad, acc4);
-        release();
+        for (int jj = 0; jj < SR; ++jj) {
+          if (jj < jstart || jj >= ntr) continue;
+          const S* tile = acquire();
+          if (tile) couple(tile, y + I * T + c0, acc[jj]);
+          release();
+        }
       }
-      C acc[KCT];
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) acc[j] = (acc4[j][0] + acc4[j][1]) + (acc4[j][2] + acc4[j][3]);
-      finish_row(J, acc);
+      finish_super(I0, ntr, acc, false);
     }
   }
   __syncthreads();
@@ -346,7 +407,7 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int*
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int npad = ((ndof_max + T - 1) / T) * T;
-  const int head = (int)sizeof(C) * (kct * npad + 2 * NCW * kct * T + kct * T) + 4 * (npad / T + 4);
+  const int head = (int)sizeof(C) * (kct * npad + 2 * NCW * SR * kct * T + NCW * SR * 4 * kct) + 4 * (npad / T + 4);
   const int off = (head + 127) & ~127;
   const int budget = optin - 2048 - off;   // static shared memory and slack
   int c = (32 * 1024) / (int)(TT * sizeof(S));

@@ -217,6 +217,81 @@ __global__ void k_gather_tiles(const S* __restrict__ src, const long long* __res
   }
 }
 
+// Inverse of the lower-triangular diagonal block of one super-row (tile rows I0 .. I0+ntr-1), whose
+// diagonal tiles already hold inv(L_ii):  X_ii = inv(L_ii),  X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj
+// (block forward substitution; L_ik = 0 left of the envelope).  Tiles row-major, order (i, j), j <= i.
+template <typename S>
+__global__ void __launch_bounds__(256) k_dinv(EnvDev E, const S* __restrict__ L, const int* __restrict__ task,
+                                              const long long* __restrict__ dinv_ptr, S* __restrict__ X) {
+  using C = typename Compute<S>::type;
+  __shared__ C a[T][T + 1];
+  __shared__ C b[T][T + 1];
+  __shared__ C w[T][T + 1];
+  const int q = blockIdx.x;
+  const int s = task[3 * q], I0 = task[3 * q + 1], ntr = task[3 * q + 2];
+  const long long xb = dinv_ptr[q];
+  auto xt = [&](int i, int j) { return X + (xb + i * (i + 1) / 2 + j) * TT; };
+  const int tid = threadIdx.x, c = tid % T, r0 = tid / T;
+  for (int i = 0; i < ntr; ++i) {
+    const S* src = L + tile_index(E, s, I0 + i, I0 + i) * TT;
+    S* dst = xt(i, i);
+    for (int t = tid; t < TT; t += blockDim.x) dst[t] = src[t];
+  }
+  __syncthreads();
+  for (int i = 1; i < ntr; ++i) {
+    const int Fi = E.trow_F[E.sub_trow[s] + I0 + i];
+    for (int j = 0; j < i; ++j) {
+      C acc[4] = {0, 0, 0, 0};
+      for (int kk = j; kk < i; ++kk) {
+        if (I0 + kk < Fi) continue;
+        const S* A = L + tile_index(E, s, I0 + i, I0 + kk) * TT;
+        const S* B = xt(kk, j);
+        for (int t = tid; t < TT; t += blockDim.x) {
+          a[t / T][t % T] = (C)A[t];
+          b[t / T][t % T] = (C)B[t];
+        }
+        __syncthreads();
+        for (int m = 0; m < T; ++m) {
+          const C bv = b[m][c];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] += a[r0 + 8 * u][m] * bv;
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w[r0 + 8 * u][c] = acc[u];
+      const S* D = xt(i, i);
+      for (int t = tid; t < TT; t += blockDim.x) a[t / T][t % T] = (C)D[t];
+      __syncthreads();
+      S* dst = xt(i, j);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 8 * u;
+        C v = (C)0;
+        for (int m = 0; m <= r; ++m) v += a[r][m] * w[m][c];
+        dst[r * T + c] = (S)(-v);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// stream tile p = (src[p] >= 0 ? factor tile src[p] : inverse-block tile -src[p]-1), transposed if asked
+template <typename S>
+__global__ void k_stream_gather(const S* __restrict__ L, const S* __restrict__ X, const long long* __restrict__ src,
+                                S* __restrict__ dst, long long n, int transpose) {
+  __shared__ S buf[T][T + 1];
+  for (long long p = blockIdx.x; p < n; p += gridDim.x) {
+    const long long v = src[p];
+    const S* a = v >= 0 ? L + v * TT : X + (-v - 1) * TT;
+    S* d = dst + p * TT;
+    for (int u = threadIdx.x; u < TT; u += blockDim.x) buf[u / T][u % T] = a[u];
+    __syncthreads();
+    for (int u = threadIdx.x; u < TT; u += blockDim.x) d[u] = transpose ? buf[u % T][u / T] : buf[u / T][u % T];
+    __syncthreads();
+  }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
     dst[t] = __float2bfloat16_rn(src[t]);
@@ -470,6 +545,27 @@ int launch_gather_tiles(int prec, const void* src, const long long* idx, void* d
   if (g < 1) g = 1;
   if (prec == 0) k_gather_tiles<double><<<g, 256, 0, (cudaStream_t)st>>>((const double*)src, idx, (double*)dst, ntiles);
   else k_gather_tiles<float><<<g, 256, 0, (cudaStream_t)st>>>((const float*)src, idx, (float*)dst, ntiles);
+  return (int)cudaGetLastError();
+}
+
+int launch_dinv(int prec, const EnvDev& E, const void* L, const int* task, const long long* dinv_ptr, void* X, int nsr,
+                void* st) {
+  if (nsr <= 0) return 0;
+  if (prec == 0) k_dinv<double><<<nsr, 256, 0, (cudaStream_t)st>>>(E, (const double*)L, task, dinv_ptr, (double*)X);
+  else k_dinv<float><<<nsr, 256, 0, (cudaStream_t)st>>>(E, (const float*)L, task, dinv_ptr, (float*)X);
+  return (int)cudaGetLastError();
+}
+
+int launch_stream_gather(int prec, const void* L, const void* X, const long long* src, void* dst, long long n,
+                         int transpose, void* st) {
+  int g = (int)(n < 152 * 16 ? n : 152 * 16);
+  if (g < 1) g = 1;
+  if (prec == 0)
+    k_stream_gather<double><<<g, 256, 0, (cudaStream_t)st>>>((const double*)L, (const double*)X, src, (double*)dst, n,
+                                                              transpose);
+  else
+    k_stream_gather<float><<<g, 256, 0, (cudaStream_t)st>>>((const float*)L, (const float*)X, src, (float*)dst, n,
+                                                             transpose);
   return (int)cudaGetLastError();
 }
 

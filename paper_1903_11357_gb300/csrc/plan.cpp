@@ -38,16 +38,47 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
     }
     sub_trow[s + 1] = sub_trow[s] + nbt;
   }
+  // super-rows, their inverse blocks and the two solve streams
+  sub_sr.assign(nsub + 1, 0);
+  dinv_ptr.assign(1, 0);
+  dinv_task.clear();
+  stream_ptr.assign(nsub + 1, 0);
+  fwd_src.clear();
   bwd_src.clear();
-  bwd_src.reserve(ntiles);
+  sr_ilast.clear();
   for (int s = 0; s < nsub; ++s) {
     const int nbt = (int)Fs[s].size(), tr0 = sub_trow[s];
-    for (int J = nbt - 1; J >= 0; --J) {
-      for (int I = J + 1; I < nbt; ++I)
-        if (Fs[s][I] <= J) bwd_src.push_back(trow_ptr[tr0 + I] + (J - Fs[s][I]));
-      bwd_src.push_back(trow_ptr[tr0 + J] + (J - Fs[s][J]));
+    const int nsr = (nbt + SR - 1) / SR;
+    const int q0 = sub_sr[s];
+    sub_sr[s + 1] = q0 + nsr;
+    sr_ilast.resize(q0 + nsr, 0);
+    for (int q = 0; q < nsr; ++q) {
+      const int I0 = q * SR, ntr = std::min(SR, nbt - I0);
+      dinv_task.push_back(s);
+      dinv_task.push_back(I0);
+      dinv_task.push_back(ntr);
+      dinv_ptr.push_back(dinv_ptr.back() + ntr * (ntr + 1) / 2);
     }
+    for (int q = 0; q < nsr; ++q) {
+      const int I0 = q * SR, ntr = std::min(SR, nbt - I0);
+      for (int I = I0; I < I0 + ntr; ++I)
+        for (int J = Fs[s][I]; J < I0; ++J) fwd_src.push_back(trow_ptr[tr0 + I] + (J - Fs[s][I]));
+      for (int t = 0; t < ntr * (ntr + 1) / 2; ++t) fwd_src.push_back(-(dinv_ptr[q0 + q] + t + 1));
+    }
+    for (int q = nsr - 1; q >= 0; --q) {
+      const int I0 = q * SR, ntr = std::min(SR, nbt - I0), I1 = I0 + ntr;
+      int last = I1 - 1;   // last tile row coupled to this super-row's columns
+      for (int I = I1; I < nbt; ++I) {
+        if (Fs[s][I] > I1 - 1) continue;
+        last = I;
+        for (int J = std::max(Fs[s][I], I0); J < I1; ++J) bwd_src.push_back(trow_ptr[tr0 + I] + (J - Fs[s][I]));
+      }
+      sr_ilast[q0 + q] = last;
+      for (int t = 0; t < ntr * (ntr + 1) / 2; ++t) bwd_src.push_back(-(dinv_ptr[q0 + q] + t + 1));
+    }
+    stream_ptr[s + 1] = (long long)fwd_src.size();
   }
+  ndinv = dinv_ptr.back();
   diag_off.assign(max_nbt + 1, 0);
   panel_off.assign(max_nbt + 1, 0);
   upd_off.assign(max_nbt + 1, 0);

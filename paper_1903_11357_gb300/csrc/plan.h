@@ -9,6 +9,7 @@
 namespace dgasm {
 
 constexpr int TILE = 32;  // tile edge of the local Cholesky factors
+constexpr int SR = 4;     // tile rows per super-row of the triangular solves
 
 void rcb_parts(const MeshData& m, std::vector<int> elems, int k, std::vector<int>& part_of, int first_part);
 int compute_partition(const MeshData& m, int nsub, int ncoarse, std::vector<int>& sub, std::vector<int>* agg);
@@ -21,10 +22,23 @@ struct Envelope {
   std::vector<int> sub_trow;           // [nsub+1] offsets into the tile-row arrays
   std::vector<int> trow_F;             // first tile column of each tile row
   std::vector<long long> trow_ptr;     // tile index of the first tile of each tile row
-  // backward stream: position b (subdomain s occupies the same index range as its forward tiles) holds
-  // the tile bwd_src[b]; per subdomain, column J from the last: tiles (I, J), I > J, then (J, J)
-  std::vector<long long> bwd_src;
   long long ntiles = 0;
+  // Super-rows: groups of SR consecutive tile rows.  The triangular solves use, per super-row q, the
+  // explicit inverse X_q of its lower-triangular diagonal block (ntr(ntr+1)/2 tiles, ntr <= SR, row-major
+  // tile order (i, j), j <= i), and the factor tiles that couple different super-rows.
+  std::vector<int> sub_sr;               // [nsub+1] first global super-row of each subdomain
+  std::vector<long long> dinv_ptr;       // [nsr+1] first tile of each super-row's inverse block
+  long long ndinv = 0;
+  // Streams in the order the sweeps consume them (equal lengths per subdomain):
+  //   forward, super-row q ascending: for its tile rows I, tiles (I, J) with F(I) <= J < first row of q;
+  //            then X_q;
+  //   backward, super-row q descending: for each tile row I after q (ascending, up to sr_ilast[q]),
+  //            the tiles (I, J) of the columns J of q with F(I) <= J, J ascending; then X_q.
+  // Entry >= 0 is a factor tile index, entry < 0 is -(inverse-block tile index + 1).
+  std::vector<long long> stream_ptr;     // [nsub+1]
+  std::vector<long long> fwd_src, bwd_src;
+  std::vector<int> dinv_task;            // per super-row: (subdomain, first tile row, tile rows)
+  std::vector<int> sr_ilast;             // per super-row: last tile row coupled to its columns
   int max_nbt = 0;
   // Cholesky tasks, grouped by step K: diag (s, K), panel (s, I), update (s, I, J), I >= J
   std::vector<int> diag_off, panel_off, upd_off;  // [max_nbt + 1]

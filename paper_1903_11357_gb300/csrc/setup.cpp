@@ -35,6 +35,12 @@ int upload_env(const Envelope& E, EnvBufs& D) {
   DG_TRY(upload(D.panel_task, E.panel_task));
   DG_TRY(upload(D.upd_task, E.upd_task));
   DG_TRY(upload(D.bwd_src, E.bwd_src));
+  DG_TRY(upload(D.fwd_src, E.fwd_src));
+  DG_TRY(upload(D.stream_ptr, E.stream_ptr));
+  DG_TRY(upload(D.dinv_task, E.dinv_task));
+  DG_TRY(upload(D.dinv_ptr, E.dinv_ptr));
+  DG_TRY(upload(D.sub_sr, E.sub_sr));
+  DG_TRY(upload(D.sr_ilast, E.sr_ilast));
   D.dev.nsub = E.nsub;
   D.dev.ndof = D.ndof.as<int>();
   D.dev.sub_trow = D.sub_trow.as<int>();
@@ -65,6 +71,39 @@ int factor_env(int prec, const Envelope& E, EnvBufs& D, void* Lr, int* err, cuda
     if (rc) return cuda_error(rc, "tile Cholesky update step");
     *launches += (nd > 0) + (npn > 0) + (nu > 0);
   }
+  return DGASM_OK;
+}
+
+// From the factored tile pool Lf (row-major, diagonal tiles inverted): the super-row inverse blocks,
+// then the forward stream (column-major tiles) and the backward stream (row-major tiles) in the order
+// the triangular solves consume them.  Lf is released.
+int build_streams(int fprec, const Envelope& E, EnvBufs& D, DevBuf& Lf, DevBuf& Lc, DevBuf& Lr, cudaStream_t st,
+                  int* nl) {
+  const int fp = fprec == DGASM_FP64 ? 0 : 1;
+  const size_t eb = fact_elem_bytes(fprec);
+  const long long ns = (long long)E.fwd_src.size();
+  const int nsr = (int)E.dinv_ptr.size() - 1;
+  DevBuf X, Sf, Sb;
+  DG_TRY(X.alloc((size_t)std::max<long long>(E.ndinv, 1) * TILE * TILE * eb));
+  DG_CUDA(launch_dinv(fp, D.dev, Lf.ptr, D.dinv_task.as<int>(), D.dinv_ptr.as<long long>(), X.ptr, nsr, st));
+  DG_TRY(Sf.alloc((size_t)ns * TILE * TILE * eb));
+  DG_TRY(Sb.alloc((size_t)ns * TILE * TILE * eb));
+  DG_CUDA(launch_stream_gather(fp, Lf.ptr, X.ptr, D.fwd_src.as<long long>(), Sf.ptr, ns, 1, st));
+  DG_CUDA(launch_stream_gather(fp, Lf.ptr, X.ptr, D.bwd_src.as<long long>(), Sb.ptr, ns, 0, st));
+  *nl += 3;
+  if (fprec == DGASM_BF16) {
+    DG_TRY(Lc.alloc((size_t)ns * TILE * TILE * 2));
+    DG_TRY(Lr.alloc((size_t)ns * TILE * TILE * 2));
+    DG_CUDA(launch_to_bf16(Sf.as<float>(), Lc.ptr, ns * TILE * TILE, st));
+    DG_CUDA(launch_to_bf16(Sb.as<float>(), Lr.ptr, ns * TILE * TILE, st));
+    *nl += 2;
+    DG_CUDA(cudaStreamSynchronize(st));
+  } else {
+    DG_CUDA(cudaStreamSynchronize(st));
+    Lc = std::move(Sf);
+    Lr = std::move(Sb);
+  }
+  Lf.reset();
   return DGASM_OK;
 }
 
@@ -103,7 +142,9 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
   const Plan& P = pc.P;
   const size_t ndof = (size_t)P.ne * P.np, t = (size_t)P.env.ntiles * TILE * TILE, n0 = pc.n0;
   size_t b = P.col.size() * (size_t)pc.sys->np2s * 8 + ndof * 8 + P.col.size() * 12 + (size_t)P.ne * 20;
-  b += t * (pc.precision == DGASM_FP64 ? 24 : 12) + P.env.bwd_src.size() * 8;
+  const size_t ts = (size_t)P.env.fwd_src.size() * TILE * TILE, td = (size_t)P.env.ndinv * TILE * TILE;
+  b += (t + td) * (pc.precision == DGASM_FP64 ? 8 : 4) + ts * (pc.precision == DGASM_FP64 ? 16 : 8) +
+       P.env.fwd_src.size() * 16;
   b += (P.env.upd_task.size() + P.env.panel_task.size() + P.env.diag_task.size() + P.env.trow_F.size() * 3) * 4;
   if (n0) b += ndof * P.nq * 8 + n0 * n0 * 8 * 3 + (size_t)P.env0.ntiles * TILE * TILE * 16;
   const int epi = NTHREADS / P.np;
@@ -150,30 +191,8 @@ int prec_build(dgasm_prec_s* pc) {
                               P.nsub, ne, st));
   nl += 1;
   DG_TRY(factor_env(fprec, P.env, pc->env, Lf.ptr, pc->err.as<int>(), st, ev, &nl));
-  // forward copy: column-major tiles in storage order; backward copy: row-major tiles in the order
-  // of the backward sweep (see Envelope::bwd_src)
-  {
-    const int fp = fprec == DGASM_FP64 ? 0 : 1;
-    DevBuf Lcf, Lbf;
-    DG_TRY(Lcf.alloc(ftiles * fact_elem_bytes(fprec)));
-    DG_TRY(Lbf.alloc(ftiles * fact_elem_bytes(fprec)));
-    DG_CUDA(launch_to_colmajor(fp, Lf.ptr, Lcf.ptr, P.env.ntiles, st));
-    DG_CUDA(launch_gather_tiles(fp, Lf.ptr, pc->env.bwd_src.as<long long>(), Lbf.ptr, P.env.ntiles, st));
-    nl += 2;
-    if (fprec == DGASM_BF16) {
-      DG_TRY(pc->Lr.alloc(ftiles * 2));
-      DG_TRY(pc->Lc.alloc(ftiles * 2));
-      DG_CUDA(launch_to_bf16(Lbf.as<float>(), pc->Lr.ptr, (long long)ftiles, st));
-      DG_CUDA(launch_to_bf16(Lcf.as<float>(), pc->Lc.ptr, (long long)ftiles, st));
-      nl += 2;
-      DG_CUDA(cudaStreamSynchronize(st));
-    } else {
-      DG_CUDA(cudaStreamSynchronize(st));
-      pc->Lc = std::move(Lcf);
-      pc->Lr = std::move(Lbf);
-    }
-    Lf.reset();
-  }
+  // super-row inverse blocks, then the forward (column-major) and backward (row-major) solve streams
+  DG_TRY(build_streams(fprec, P.env, pc->env, Lf, pc->Lc, pc->Lr, st, &nl));
   // coarse space: R_0^T, A_0 = R_0 A R_0^T, FP64 factor and explicit inverse
   if (pc->n0 > 0) {
     const int n0 = pc->n0, q = P.q, nq = P.nq, mq = s->p + 2;
@@ -194,7 +213,7 @@ int prec_build(dgasm_prec_s* pc) {
                             pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), P.nagg, np, np2s, nq,
                             A0.as<double>(), st));
     DG_TRY(upload_env(P.env0, pc->env0));
-    DevBuf scale0, Lr0, Lc0;
+    DevBuf scale0, Lr0, Lc0, Lb0;
     DG_TRY(scale0.alloc(sizeof(double) * n0));
     const size_t t0 = (size_t)P.env0.ntiles * TILE * TILE;
     DG_TRY(Lr0.alloc(sizeof(double) * t0));
@@ -202,18 +221,10 @@ int prec_build(dgasm_prec_s* pc) {
     DG_CUDA(launch_coarse_extract(A0.as<double>(), n0, scale0.as<double>(), pc->env0.dev, Lr0.as<double>(), st));
     nl += 4;
     DG_TRY(factor_env(DGASM_FP64, P.env0, pc->env0, Lr0.ptr, pc->err.as<int>() + 4, st, ev, &nl));
-    DG_TRY(Lc0.alloc(sizeof(double) * t0));
-    DG_CUDA(launch_to_colmajor(0, Lr0.ptr, Lc0.ptr, P.env0.ntiles, st));
-    {
-      DevBuf Lb0;
-      DG_TRY(Lb0.alloc(sizeof(double) * t0));
-      DG_CUDA(launch_gather_tiles(0, Lr0.ptr, pc->env0.bwd_src.as<long long>(), Lb0.ptr, P.env0.ntiles, st));
-      DG_CUDA(cudaStreamSynchronize(st));
-      Lr0 = std::move(Lb0);
-    }
+    DG_TRY(build_streams(DGASM_FP64, P.env0, pc->env0, Lr0, Lc0, Lb0, st, &nl));
     // A_0^{-1} = columns of the local-solve kernel applied to the identity
     DG_TRY(pc->A0inv.alloc(sizeof(double) * (size_t)n0 * n0));
-    DG_TRY(pc->coarse_inverse(scale0, Lr0, Lc0));
+    DG_TRY(pc->coarse_inverse(scale0, Lb0, Lc0));
     nl += 3;
   }
   // check factorisation errors
@@ -282,7 +293,9 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
   std::memset(&D, 0, sizeof(D));
   D.np = n0; D.ndof = n0; D.nsub = 1; D.k = n0; D.kc = KC; D.n_rhs_chunks = chunks; D.prec = DGASM_FP64;
   D.sub_e0 = sub_e0c.as<int>(); D.sub_trow = env0.sub_trow.as<int>(); D.trow_F = env0.trow_F.as<int>();
-  D.trow_ptr = env0.trow_ptr.as<long long>(); D.Lr = Lr0.ptr; D.Lc = Lc0.ptr; D.scale = scale0.as<double>();
+  D.trow_ptr = env0.trow_ptr.as<long long>(); D.stream_ptr = env0.stream_ptr.as<long long>();
+  D.sub_sr = env0.sub_sr.as<int>(); D.sr_ilast = env0.sr_ilast.as<int>();
+  D.Lr = Lr0.ptr; D.Lc = Lc0.ptr; D.scale = scale0.as<double>();
   D.r = ident.as<double>(); D.z = A0inv.as<double>();
   D.done = (int*)misc.ptr;
   D.part_rz = (double*)((char*)misc.ptr + rz_off);
@@ -313,7 +326,8 @@ size_t dgasm_prec_s::footprint() const {
   const EnvBufs* es[2] = {&env, &env0};
   for (const EnvBufs* e : es)
     b += e->ndof.bytes + e->sub_trow.bytes + e->trow_F.bytes + e->trow_ptr.bytes + e->diag_task.bytes +
-         e->panel_task.bytes + e->upd_task.bytes + e->bwd_src.bytes;
+         e->panel_task.bytes + e->upd_task.bytes + e->bwd_src.bytes + e->fwd_src.bytes + e->stream_ptr.bytes +
+         e->dinv_task.bytes + e->dinv_ptr.bytes + e->sub_sr.bytes + e->sr_ilast.bytes;
   return b;
 }
 

@@ -91,6 +91,8 @@ def test_cfg1_solve_parity_fp64(contrast):
 
 
 def test_multi_rhs_equals_single():
+    """Several right-hand sides share one pass over the factors; the local solve groups its accumulation
+    chains per right-hand-side count, so results agree with one-at-a-time solves to rounding."""
     c = build_case(300, 4, 2, 4, 16)
     rng = np.random.default_rng(5)
     B = rng.standard_normal((3, len(c["b"])))
@@ -99,8 +101,9 @@ def test_multi_rhs_equals_single():
     assert rc == 0 and len(st) == 3
     for j in range(3):
         x1 = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
-        c["P"].solve(dev(B[j]), x1, rtol=1e-8)
-        assert torch.equal(x1, X[j])
+        rc1, st1 = c["P"].solve(dev(B[j]), x1, rtol=1e-8)
+        assert abs(st1[0]["iters"] - st[j]["iters"]) <= 1
+        assert float(torch.linalg.norm(x1 - X[j])) <= 1e-9 * float(torch.linalg.norm(x1))
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])

@@ -57,7 +57,7 @@ def test_admission_by_memory_budget_and_errors():
     S = make_system(400, 7, 3)
     P = dg.Prec(S, 4, 16, 1)
     need = P.footprint()
-    sv = dg.Server(hbm_budget=int(need * 1.6), max_slots=4)   # room for one request at a time
+    sv = dg.Server(hbm_budget=int(need * 2.5), max_slots=4)   # room for one request at a time
     bs = [rhs(S, 1, 20 + i) for i in range(3)]
     xs = [torch.zeros_like(b) for b in bs]
     ts = [sv.submit(S, 4, 16, 1, b, x) for b, x in zip(bs, xs)]
