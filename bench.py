@@ -322,9 +322,9 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
     avg_s = dom_ms / 1000.0 / max(dom_n, 1)
-    tiles = info["local_tiles"]
+    tiles = info["stream_tiles"]
     if dom == "local":
-        flops = 2 * 2 * tiles * 1024 * 1.0          # forward + backward, 2 flop per FMA, one rhs
+        flops = 2 * 2 * tiles * 1024 * 1.0          # forward + backward sweep, 2 flop per FMA, one rhs
         bytes_ = 2 * tiles * 1024 * 8 + ndof * 8 * 3
     elif dom == "chol_update":
         total_upd_flops = info["factor_flops"]
@@ -351,8 +351,8 @@ def main():
         "time_to_1e8_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "mean": sum(lat) / len(lat)},
         "iters": iters, "true_relres": sts[-1]["true_relres"], "kappa_estimate": sts[-1]["kappa"],
-        "setup": {"plan_ms": info["plan_ms"], "setup_ms": info["setup_ms"], "local_tiles": tiles,
-                  "factor_flops": info["factor_flops"]},
+        "setup": {"plan_ms": info["plan_ms"], "setup_ms": info["setup_ms"], "local_tiles": info["local_tiles"],
+                  "stream_tiles": tiles, "factor_flops": info["factor_flops"]},
         "gpu_launches": int(launches),
         "kernels": kernel_ms,
         "roofline": roof,

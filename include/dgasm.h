@@ -178,6 +178,8 @@ typedef struct {
   int precision;          /* dgasm_precision of the local factors */
   int64_t local_dofs;     /* sum of the subdomain dof counts (= ndof) */
   int64_t local_tiles;    /* 32x32 tiles in the envelopes of all local factors (one copy) */
+  int64_t stream_tiles;   /* 32x32 tiles read by one sweep of the local solves (envelope tiles outside the
+                             diagonal super-row blocks plus the inverted super-row blocks) */
   int64_t factor_flops;   /* flops of the tile Cholesky of the local factors (tile-level count) */
   int64_t nnzb;           /* blocks of the block-sparse matrix */
   double plan_ms;         /* host part of dgasm_setup: partition, ordering, envelopes, task lists */

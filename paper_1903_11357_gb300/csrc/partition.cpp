@@ -22,13 +22,16 @@ static void rcb_rec(const double* cx, const double* cy, std::vector<int>& elems,
     ymin = std::min(ymin, cy[e]); ymax = std::max(ymax, cy[e]);
   }
   const double* c = (xmax - xmin >= ymax - ymin) ? cx : cy;
-  std::sort(elems.begin() + lo, elems.begin() + hi, [c](int a, int b) {
-    if (c[a] != c[b]) return c[a] < c[b];
-    return a < b;
-  });
   int kl = k / 2;
   size_t n = hi - lo;
   size_t nl = (n * (size_t)kl) / (size_t)k;
+  // the first nl elements in the (coordinate, element id) order: a strict total order, so selecting them
+  // with nth_element gives exactly the set a full sort would
+  if (nl > 0 && nl < n)
+    std::nth_element(elems.begin() + lo, elems.begin() + lo + nl, elems.begin() + hi, [c](int a, int b) {
+      if (c[a] != c[b]) return c[a] < c[b];
+      return a < b;
+    });
   rcb_rec(cx, cy, elems, lo, lo + nl, kl, part_of, next_part);
   rcb_rec(cx, cy, elems, lo + nl, hi, k - kl, part_of, next_part);
 }

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <numeric>
 #include <queue>
+#include <thread>
 
 #include "plan.h"
 
@@ -46,6 +47,8 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
   fwd_src.clear();
   bwd_src.clear();
   sr_ilast.clear();
+  fwd_src.reserve((size_t)ntiles + (size_t)ntiles / 2);
+  bwd_src.reserve((size_t)ntiles + (size_t)ntiles / 2);
   for (int s = 0; s < nsub; ++s) {
     const int nbt = (int)Fs[s].size(), tr0 = sub_trow[s];
     const int nsr = (nbt + SR - 1) / SR;
@@ -85,6 +88,9 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
   diag_task.clear();
   panel_task.clear();
   upd_task.clear();
+  diag_task.reserve((size_t)nsub * max_nbt);
+  panel_task.reserve((size_t)ntiles * 2);
+  upd_task.reserve((size_t)ntiles * 3 * 8);
   std::vector<int> S;
   for (int K = 0; K < max_nbt; ++K) {
     for (int s = 0; s < nsub; ++s) {
@@ -110,62 +116,60 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
 
 namespace {
 
-// Reverse Cuthill-McKee of the element graph restricted to `elems` (caller ids); returns the order.
+// Reverse Cuthill-McKee of the element graph restricted to `elems` (caller ids, ascending); returns the
+// order.  `loc` is a scratch array over all elements (entries for `elems` are overwritten).
 std::vector<int> rcm_order(const std::vector<int>& elems, const std::vector<int>& rowptr, const std::vector<int>& col,
-                           const std::vector<int>& sub_of, int s) {
-  int n = (int)elems.size();
-  std::vector<int> local(n);
-  // map caller id -> local index via sorted lookup
-  std::vector<int> sorted(elems);
-  std::sort(sorted.begin(), sorted.end());
-  auto loc = [&](int e) { return (int)(std::lower_bound(sorted.begin(), sorted.end(), e) - sorted.begin()); };
-  std::vector<std::vector<int>> adj(n);
+                           const std::vector<int>& sub_of, int s, std::vector<int>& loc) {
+  const int n = (int)elems.size();
+  for (int i = 0; i < n; ++i) loc[elems[i]] = i;
+  std::vector<int> aptr(n + 1, 0), adj;
+  adj.reserve(8 * (size_t)n);
   for (int i = 0; i < n; ++i) {
-    int e = sorted[i];
+    const int e = elems[i];
     for (int k = rowptr[e]; k < rowptr[e + 1]; ++k) {
-      int c = col[k];
-      if (c != e && sub_of[c] == s) adj[i].push_back(loc(c));
+      const int c = col[k];
+      if (c != e && sub_of[c] == s) adj.push_back(loc[c]);
     }
+    aptr[i + 1] = (int)adj.size();
   }
-  std::vector<int> deg(n);
-  for (int i = 0; i < n; ++i) deg[i] = (int)adj[i].size();
-  auto bfs = [&](int root, std::vector<int>& order, std::vector<int>& level) {
+  auto deg = [&](int i) { return aptr[i + 1] - aptr[i]; };
+  std::vector<int> order, level(n), visited(n, 0), result, nb;
+  order.reserve(n);
+  result.reserve(n);
+  auto bfs = [&](int root) {
     order.clear();
-    level.assign(n, -1);
-    std::vector<int> q{root};
+    std::fill(level.begin(), level.end(), -1);
+    order.push_back(root);
     level[root] = 0;
-    size_t h = 0;
-    while (h < q.size()) {
-      int u = q[h++];
-      order.push_back(u);
-      std::vector<int> nb;
-      for (int v : adj[u]) if (level[v] < 0) { level[v] = level[u] + 1; nb.push_back(v); }
-      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
-      for (int v : nb) q.push_back(v);
+    for (size_t h = 0; h < order.size(); ++h) {
+      const int u = order[h];
+      nb.clear();
+      for (int k = aptr[u]; k < aptr[u + 1]; ++k)
+        if (level[adj[k]] < 0) { level[adj[k]] = level[u] + 1; nb.push_back(adj[k]); }
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg(a) != deg(b) ? deg(a) < deg(b) : a < b; });
+      order.insert(order.end(), nb.begin(), nb.end());
     }
   };
-  std::vector<int> order, level, visited(n, 0), result;
-  result.reserve(n);
   for (int start = 0; start < n; ++start) {
     if (visited[start]) continue;
     // pseudo-peripheral root of this component (George-Liu iteration)
     int root = start;
     int best_depth = -1;
-    for (int it = 0; it < 8; ++it) {
-      bfs(root, order, level);
-      int depth = level[order.back()];
+    for (int it = 0; it < 4; ++it) {
+      bfs(root);
+      const int depth = level[order.back()];
       if (depth <= best_depth) break;
       best_depth = depth;
       int cand = order.back();
-      for (int u : order) if (level[u] == depth && deg[u] < deg[cand]) cand = u;
+      for (int u : order) if (level[u] == depth && deg(u) < deg(cand)) cand = u;
       root = cand;
     }
-    bfs(root, order, level);
+    bfs(root);
     for (int u : order) { visited[u] = 1; result.push_back(u); }
   }
   std::reverse(result.begin(), result.end());
   std::vector<int> out(n);
-  for (int i = 0; i < n; ++i) out[i] = sorted[result[i]];
+  for (int i = 0; i < n; ++i) out[i] = elems[result[i]];
   return out;
 }
 
@@ -233,11 +237,23 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   // internal order: subdomain by subdomain, RCM inside
   std::vector<std::vector<int>> members(nsub);
   for (int e = 0; e < ne; ++e) members[P.sub_of[e]].push_back(e);
+  // RCM of each subdomain, in parallel (subdomains are independent; results do not depend on threads)
+  std::vector<std::vector<int>> ords(nsub);
+  {
+    const unsigned nt = std::max(1u, std::min({16u, std::thread::hardware_concurrency(), (unsigned)nsub}));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+      th.emplace_back([&, t]() {
+        std::vector<int> loc(ne, 0);
+        for (int s = (int)t; s < nsub; s += (int)nt) ords[s] = rcm_order(members[s], sys.rowptr, sys.col, P.sub_of, s, loc);
+      });
+    for (auto& x : th) x.join();
+  }
   P.perm.clear();
+  P.perm.reserve(ne);
   P.sub_e0.assign(nsub + 1, 0);
   for (int s = 0; s < nsub; ++s) {
-    std::vector<int> ord = rcm_order(members[s], sys.rowptr, sys.col, P.sub_of, s);
-    P.perm.insert(P.perm.end(), ord.begin(), ord.end());
+    P.perm.insert(P.perm.end(), ords[s].begin(), ords[s].end());
     P.sub_e0[s + 1] = (int)P.perm.size();
   }
   P.iperm.assign(ne, 0);
@@ -246,6 +262,8 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   P.rowptr.assign(ne + 1, 0);
   P.col.clear();
   P.src_blk.clear();
+  P.col.reserve(sys.col.size());
+  P.src_blk.reserve(sys.col.size());
   std::vector<std::pair<int, int>> row;
   for (int i = 0; i < ne; ++i) {
     int e = P.perm[i];

@@ -354,6 +354,7 @@ extern "C" int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info) {
   info->precision = pc->precision;
   info->local_dofs = (int64_t)P.ne * P.np;
   info->local_tiles = P.env.ntiles;
+  info->stream_tiles = (int64_t)P.env.fwd_src.size();
   int64_t upd = (int64_t)P.env.upd_task.size() / 3, pan = (int64_t)P.env.panel_task.size() / 2, dg = (int64_t)P.env.diag_task.size();
   const int64_t t3 = (int64_t)TILE * TILE * TILE;
   info->factor_flops = upd * 2 * t3 + pan * t3 + dg * (t3 / 3 + t3 / 3);

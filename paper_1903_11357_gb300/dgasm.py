@@ -44,7 +44,8 @@ class Stats(C.Structure):
 
 class PrecInfo(C.Structure):
     _fields_ = [("nsub", C.c_int), ("nagg", C.c_int), ("n0", C.c_int), ("precision", C.c_int),
-                ("local_dofs", C.c_int64), ("local_tiles", C.c_int64), ("factor_flops", C.c_int64),
+                ("local_dofs", C.c_int64), ("local_tiles", C.c_int64), ("stream_tiles", C.c_int64),
+                ("factor_flops", C.c_int64),
                 ("nnzb", C.c_int64), ("plan_ms", C.c_double), ("setup_ms", C.c_double),
                 ("setup_launches", C.c_int)]
 
