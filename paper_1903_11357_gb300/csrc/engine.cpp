@@ -111,9 +111,11 @@ int Engine::build(int n, dgasm_prec_s* const* pcs_, const int* nrhs_, const doub
   pcs.assign(pcs_, pcs_ + n);
   nrhs.assign(nrhs_, nrhs_ + n);
   total_rhs = 0;
+  km = 1;
   for (int i = 0; i < n; ++i) {
     if (nrhs[i] < 1 || nrhs[i] > KMAX) return set_error(DGASM_EINVAL, "nrhs=%d must lie in [1, %d]", nrhs[i], KMAX);
     total_rhs += nrhs[i];
+    if (nrhs[i] > 1) km = KMAX;
   }
   hp.assign(n, ProbDev{});
   pre.assign(K_NSLOTS * (n + 1), 0);
@@ -191,7 +193,7 @@ int Engine::spmv(int operand, EventPairs* ev) {
   const int n = nprob;
   for (int p = 1; p <= 8; ++p) {
     const int tot = pre[(K_SPMV_P + p - 1) * (n + 1) + n];
-    if (tot) DG_CUDA(timed_launch(PK_SPMV, stream, ev, launches, [&] { return launch_spmv(B, p, tot, operand, stream); }));
+    if (tot) DG_CUDA(timed_launch(PK_SPMV, stream, ev, launches, [&] { return launch_spmv(B, p, tot, operand, km, stream); }));
   }
   return DGASM_OK;
 }
@@ -200,7 +202,7 @@ int Engine::precond(int mode, EventPairs* ev) {
   const int n = nprob;
   DG_CUDA(cudaEventRecord(ev_fork, stream));
   DG_CUDA(cudaStreamWaitEvent(side, ev_fork, 0));
-  if (tot_coarse) DG_CUDA(timed_launch(PK_COARSE, side, ev, launches, [&] { return launch_coarse(B, tot_coarse, side); }));
+  if (tot_coarse) DG_CUDA(timed_launch(PK_COARSE, side, ev, launches, [&] { return launch_coarse(B, tot_coarse, km, side); }));
   DG_CUDA(cudaEventRecord(ev_join, side));
   for (int slot = 0; slot < 8; ++slot) {
     const int tot = pre[(K_NKINDS + slot) * (n + 1) + n];
@@ -209,13 +211,13 @@ int Engine::precond(int mode, EventPairs* ev) {
                            [&] { return launch_local(B, K_NKINDS + slot, tot, max_smem[slot], stream); }));
   }
   DG_CUDA(cudaStreamWaitEvent(stream, ev_join, 0));
-  DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, stream); }));
+  DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, km, stream); }));
   return DGASM_OK;
 }
 
 int Engine::init() {
   init_ev.reset();
-  DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT, 0, stream); }));
+  DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT, km, stream); }));
   DG_TRY(precond(MODE_INIT, &init_ev));
   return DGASM_OK;
 }
@@ -231,7 +233,7 @@ int Engine::iterate(int max_iters, int* ran) {
     int rc = 0;
     for (int it = 0; it < CHUNK && rc == 0; ++it) {
       rc = spmv(0, &graph_ev);
-      if (!rc) rc = timed_launch(PK_UPDATE, stream, &graph_ev, launches, [&] { return launch_update(B, tot_grp, MODE_ITER, 0, stream); });
+      if (!rc) rc = timed_launch(PK_UPDATE, stream, &graph_ev, launches, [&] { return launch_update(B, tot_grp, MODE_ITER, km, stream); });
       if (!rc) {
         int r3 = precond(MODE_ITER, &graph_ev);
         if (r3 < 0) rc = r3;

@@ -78,11 +78,13 @@ struct BatchDev {
 
 // ---- solve kernels (kernels_solve.cu) ----
 enum UpdateMode { MODE_INIT = 0, MODE_ITER = 1 };
-int launch_spmv(const BatchDev& B, int p, int total, int operand /*0: q = A p, 1: q = A x, true residual*/, void* stream);
-int launch_update(const BatchDev& B, int total, int mode, int use_q, void* stream);
+// km: 1 when every problem of the batch has one right-hand side, else KMAX
+int launch_spmv(const BatchDev& B, int p, int total, int operand /*0: q = A p, 1: q = A x, true residual*/, int km,
+                void* stream);
+int launch_update(const BatchDev& B, int total, int mode, int km, void* stream);
 int launch_local(const BatchDev& B, int slot, int total, int smem_bytes, void* stream);
-int launch_coarse(const BatchDev& B, int total, void* stream);
-int launch_pupdate(const BatchDev& B, int total, int mode, void* stream);
+int launch_coarse(const BatchDev& B, int total, int km, void* stream);
+int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* stream);
 int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);
 // dynamic shared memory of a local-solve launch over subdomains of at most ndof_max dofs
 int local_smem_bytes(int prec, int ndof_max, int kc);

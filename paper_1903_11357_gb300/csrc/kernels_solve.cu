@@ -36,10 +36,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // deterministic CTA sum of k values per thread; result in out[0..k) (shared), all threads synced
+template <int KM>
 __device__ void block_sum_k(const double* v, int k, double* red /*[NW][KMAX]*/, double* out) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     if (kk < k) {
       double s = warp_sum(v[kk]);
       if (lane == 0) red[w * KMAX + kk] = s;
@@ -82,7 +83,7 @@ __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
 // one thread per (element, row): q_e[r] = sum over the blocks of row e of B[r][c] x_col[c], with the
 // block width NP known at compile time (fully unrolled, two accumulator chains per right-hand side)
-template <int NP>
+template <int NP, int KM>
 __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operand, const bool* act, double* part) {
   const int e_begin = item * P.epi;
   const int nel = min(P.epi, P.ne - e_begin);
@@ -91,9 +92,9 @@ __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operan
   const int e = e_begin + t / NP, r = t % NP;
   const double* vec = operand == 0 ? P.p : P.x;
   const int k = P.k;
-  double acc[KMAX][2];
+  double acc[KM][2];
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) acc[kk][0] = acc[kk][1] = 0.0;
+  for (int kk = 0; kk < KM; ++kk) acc[kk][0] = acc[kk][1] = 0.0;
   const int kb0 = P.rowptr[e], kb1 = P.rowptr[e + 1];
   for (int kb = kb0; kb < kb1; ++kb) {
     const double* blk = P.vals + (long long)kb * P.np2s + r;
@@ -102,7 +103,7 @@ __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operan
 #pragma unroll
     for (int c = 0; c < NP; ++c) a[c] = __ldg(blk + c * NP);
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) {
+    for (int kk = 0; kk < KM; ++kk) {
       if (kk >= k || !act[kk]) continue;
       const double* xk = xc + (long long)kk * P.ndof;
 #pragma unroll
@@ -111,7 +112,7 @@ __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operan
   }
   const long long d = (long long)e * NP + r;
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     if (kk >= k || !act[kk]) continue;
     const double q = acc[kk][0] + acc[kk][1];
     P.q[kk * (long long)P.ndof + d] = q;
@@ -125,7 +126,7 @@ __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operan
 }
 
 // ---- SpMV: q = A p (operand 0, with partial (p, q)) or q = A x and (b - A x)^2 (operand 1) ------
-template <int NP>
+template <int NP, int KM>
 __global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand, int slot) {
   __shared__ double red[NW * KMAX];
   __shared__ double tot[KMAX];
@@ -134,18 +135,18 @@ __global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand, int 
   const ProbDev& P = B.probs[pi];
   const int item = blockIdx.x - B.prefix[slot][pi];
   const int k = P.k;
-  bool act[KMAX];
+  bool act[KM];
   bool any = false;
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     act[kk] = kk < k && (operand == 1 || P.done[kk] == 0);
     any |= act[kk];
   }
-  double part[KMAX];
+  double part[KM];
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) part[kk] = 0.0;
-  if (any) spmv_rows<NP>(P, item, operand, act, part);
-  block_sum_k(part, k, red, tot);
+  for (int kk = 0; kk < KM; ++kk) part[kk] = 0.0;
+  if (any) spmv_rows<NP, KM>(P, item, operand, act, part);
+  block_sum_k<KM>(part, k, red, tot);
   if (threadIdx.x < k) P.part_pq[(long long)item * k + threadIdx.x] = tot[threadIdx.x];
   if (!last_block(&P.counters[C_SPMV], P.n_chunk_items, &lastf)) return;
   if ((threadIdx.x >> 5) < k) {
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand, int 
 }
 
 // ---- x/r update (or initial residual) with partial ||r||^2 and the coarse restriction ----------
+template <int KM>
 __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
   __shared__ double red4[NW][KMAX][4];
   __shared__ double red[NW * KMAX];
@@ -178,23 +180,23 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
   const ProbDev& P = B.probs[pi];
   const int g = blockIdx.x - B.prefix[K_GRP][pi];
   const int k = P.k, np = P.np, nq = P.nq;
-  bool act[KMAX];
+  bool act[KM];
   bool any = false;
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     act[kk] = kk < k && P.done[kk] == 0;
     any |= act[kk];
   }
-  double alpha[KMAX];
+  double alpha[KM];
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) alpha[kk] = (mode == MODE_ITER && act[kk]) ? P.alpha[kk] : 0.0;
+  for (int kk = 0; kk < KM; ++kk) alpha[kk] = (mode == MODE_ITER && act[kk]) ? P.alpha[kk] : 0.0;
   const int g0 = P.grp_ptr[g], g1 = P.grp_ptr[g + 1];
   const int nd = (g1 - g0) * np;
   // one pass: x/r update, ||r||^2 and, for q = 1 (nq = 3), the restriction r_0[J] = sum R0T^T r
   constexpr int NQ1 = 3;
-  double prr[KMAX], pr0[KMAX][NQ1];
+  double prr[KM], pr0[KM][NQ1];
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     prr[kk] = 0.0;
 #pragma unroll
     for (int c = 0; c < NQ1; ++c) pr0[kk][c] = 0.0;
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
       for (int c = 0; c < NQ1; ++c) w[c] = P.r0t[d * NQ1 + c];
     }
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) {
+    for (int kk = 0; kk < KM; ++kk) {
       if (!act[kk]) continue;
       const long long o = kk * (long long)P.ndof + d;
       double rv;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nv = fused_r0 ? 1 + NQ1 : 1;
 #pragma unroll
-    for (int kk = 0; kk < KMAX; ++kk) {
+    for (int kk = 0; kk < KM; ++kk) {
       if (kk >= k) break;
       for (int c = 0; c < nv; ++c) {
         double v = c == 0 ? prr[kk] : pr0[kk][c - 1];
@@ -255,19 +257,19 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
   if (restrict_ && !fused_r0 && any) {
     // general coarse degree: one reduction per coarse basis function
     for (int c = 0; c < nq; ++c) {
-      double v[KMAX];
+      double v[KM];
 #pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) v[kk] = 0.0;
+      for (int kk = 0; kk < KM; ++kk) v[kk] = 0.0;
       for (int base = 0; base < nd; base += NTHREADS) {
         const int t = base + threadIdx.x;
         if (t >= nd) break;
         const int e = P.grp_elems[g0 + t / np], a = t % np;
         const double wv = P.r0t[((long long)e * np + a) * nq + c];
 #pragma unroll
-        for (int kk = 0; kk < KMAX; ++kk)
+        for (int kk = 0; kk < KM; ++kk)
           if (act[kk]) v[kk] = fma(wv, P.r[kk * (long long)P.ndof + (long long)e * np + a], v[kk]);
       }
-      block_sum_k(v, k, red, tot);
+      block_sum_k<KM>(v, k, red, tot);
       if (threadIdx.x < k && act[threadIdx.x]) P.r0[(long long)threadIdx.x * P.n0 + g * nq + c] = tot[threadIdx.x];
     }
   }
@@ -310,6 +312,7 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
 }
 
 // ---- coarse solve z_0 = A_0^{-1} r_0: one warp per row of the explicit inverse -------------------
+template <int KM>
 __global__ void __launch_bounds__(NTHREADS) k_coarse(BatchDev B) {
   __shared__ double wpart[NW][KMAX];
   const int pi = find_prob(B.prefix[K_COARSE], B.nprob, blockIdx.x);
@@ -318,28 +321,28 @@ __global__ void __launch_bounds__(NTHREADS) k_coarse(BatchDev B) {
   const int k = P.k, n0 = P.n0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int row = item * NW + w;
-  bool act[KMAX];
+  bool act[KM];
   bool any = false;
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     act[kk] = kk < k && P.done[kk] == 0;
     any |= act[kk];
   }
   if (!any) return;
-  double acc[KMAX];
+  double acc[KM];
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) acc[kk] = 0.0;
+  for (int kk = 0; kk < KM; ++kk) acc[kk] = 0.0;
   if (row < n0) {
     const double* Arow = P.A0inv + (long long)row * n0;
     for (int j = lane; j < n0; j += 32) {
       const double a = __ldg(Arow + j);
 #pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk)
+      for (int kk = 0; kk < KM; ++kk)
         if (act[kk]) acc[kk] = fma(a, P.r0[(long long)kk * n0 + j], acc[kk]);
     }
   }
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     if (kk >= k) break;
     double v = warp_sum(acc[kk]);
     if (lane == 0) {
@@ -360,6 +363,7 @@ __global__ void __launch_bounds__(NTHREADS) k_coarse(BatchDev B) {
 }
 
 // ---- p = z + R_0^T z_0 + beta p, beta = (r, z)_new / (r, z)_old ----------------------------------
+template <int KM>
 __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
   __shared__ double beta_s[KMAX];
   __shared__ double gnew_s[KMAX];
@@ -368,10 +372,10 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
   const ProbDev& P = B.probs[pi];
   const int item = blockIdx.x - B.prefix[K_SPMV][pi];
   const int k = P.k, np = P.np, nq = P.nq;
-  bool act[KMAX];
+  bool act[KM];
   bool any = false;
 #pragma unroll
-  for (int kk = 0; kk < KMAX; ++kk) {
+  for (int kk = 0; kk < KM; ++kk) {
     act[kk] = kk < k && P.done[kk] == 0;
     any |= act[kk];
   }
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
       const long long d = (long long)e * np + a;
       const int J = nq > 0 ? P.agg_int[e] : 0;
 #pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) {
+      for (int kk = 0; kk < KM; ++kk) {
         if (!act[kk]) continue;
         const long long o = kk * (long long)P.ndof + d;
         double zv = P.z[o];
@@ -467,34 +471,44 @@ __global__ void k_system_spmv(const int* __restrict__ rowptr, const int* __restr
 
 // one launch per polynomial degree present in the batch: slot K_SPMV_P + p - 1 holds the item prefix of
 // the problems of degree p
-int launch_spmv(const BatchDev& B, int p, int total, int operand, void* st) {
+template <int KM>
+int launch_spmv_k(const BatchDev& B, int p, int total, int operand, cudaStream_t s) {
   const int slot = K_SPMV_P + p - 1;
-  cudaStream_t s = (cudaStream_t)st;
   switch (p) {
-    case 1: k_spmv<3><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 2: k_spmv<6><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 3: k_spmv<10><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 4: k_spmv<15><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 5: k_spmv<21><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 6: k_spmv<28><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 7: k_spmv<36><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    default: k_spmv<45><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 1: k_spmv<3, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 2: k_spmv<6, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 3: k_spmv<10, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 4: k_spmv<15, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 5: k_spmv<21, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 6: k_spmv<28, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 7: k_spmv<36, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    default: k_spmv<45, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
   }
   return (int)cudaGetLastError();
 }
 
-int launch_update(const BatchDev& B, int total, int mode, int /*use_q*/, void* st) {
-  k_update<<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
+// one launch per polynomial degree present in the batch: slot K_SPMV_P + p - 1 holds the item prefix of
+// the problems of degree p; km = 1 when every problem of the batch has one right-hand side
+int launch_spmv(const BatchDev& B, int p, int total, int operand, int km, void* st) {
+  return km == 1 ? launch_spmv_k<1>(B, p, total, operand, (cudaStream_t)st)
+                 : launch_spmv_k<KMAX>(B, p, total, operand, (cudaStream_t)st);
+}
+
+int launch_update(const BatchDev& B, int total, int mode, int km, void* st) {
+  if (km == 1) k_update<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
+  else k_update<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
   return (int)cudaGetLastError();
 }
 
-int launch_coarse(const BatchDev& B, int total, void* st) {
-  k_coarse<<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
+int launch_coarse(const BatchDev& B, int total, int km, void* st) {
+  if (km == 1) k_coarse<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
+  else k_coarse<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
   return (int)cudaGetLastError();
 }
 
-int launch_pupdate(const BatchDev& B, int total, int mode, void* st) {
-  k_pupdate<<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
+int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* st) {
+  if (km == 1) k_pupdate<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
+  else k_pupdate<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
   return (int)cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ struct Engine {
   int max_smem[8] = {0};
   int tot_spmv = 0, tot_grp = 0, tot_coarse = 0;
   int total_rhs = 0;
+  int km = 1;   // 1 when every problem has one right-hand side
   DevBuf tables;
   int* d_remaining = nullptr;
   int* d_err = nullptr;
