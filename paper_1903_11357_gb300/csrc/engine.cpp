@@ -64,6 +64,7 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.trow_ptr = pc.env.trow_ptr.as<long long>(); D.stream_ptr = pc.env.stream_ptr.as<long long>();
   D.sub_sr = pc.env.sub_sr.as<int>(); D.sr_ilast = pc.env.sr_ilast.as<int>();
   D.Lr = pc.Lr.ptr; D.Lc = pc.Lc.ptr; D.scale = pc.scale.as<double>();
+  D.stream_total = (long long)pc.P.env.fwd_src.size();
   D.grp_ptr = pc.grp_ptr.as<int>(); D.grp_elems = pc.grp_elems.as<int>(); D.agg_int = pc.agg_int.as<int>();
   D.r0t = pc.r0t.as<double>(); D.A0inv = pc.A0inv.as<double>();
   D.b_user = b_user; D.x_user = x_user;

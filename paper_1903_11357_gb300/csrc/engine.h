@@ -40,8 +40,9 @@ struct ProbDev {
   const long long* stream_ptr;  // [nsub+1] offsets of each subdomain's solve streams
   const int* sub_sr;            // [nsub+1] first global super-row of each subdomain
   const int* sr_ilast;          // per global super-row: last tile row coupled to its columns
-  const void* Lr;     // backward stream: row-major tiles in consumption order
-  const void* Lc;     // forward stream: column-major tiles in consumption order
+  long long stream_total;  // tiles in each of the two streams (all subdomains)
+  const void* Lr;     // backward stream: row-major tiles in consumption order, as [2][stream_total][16 x 32]
+  const void* Lc;     // forward stream: column-major tiles in consumption order, same split layout
   const double* scale;
   // groups and coarse space
   const int* grp_ptr;

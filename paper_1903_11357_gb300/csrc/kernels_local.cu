@@ -1,21 +1,29 @@
 // Local subdomain solves z_i = R_i^T A_i^{-1} R_i r (Sec. 3, local solvers) with the scaled tile-envelope
 // Cholesky factor A~_i = L L^T (A~_i = D^{-1/2} A_i D^{-1/2}): forward substitution with L, backward
-// substitution with L^T, diagonal tiles stored as inv(L_II) so both become tile GEMVs.
+// substitution with L^T.
 //
-// One CTA per (subdomain, right-hand-side chunk).  Warp 8 is a producer: one elected lane streams the
-// factor tiles from HBM into a ring of shared-memory slots with bulk asynchronous copies (cp.async.bulk,
-// completion counted on an mbarrier per slot).  Both copies of the factor are stored in the order the
-// sweeps consume them (forward: rows of column-major tiles; backward: columns of row-major tiles), so
-// the producer streams two contiguous ranges, 32 KB per copy (the cost of a bulk copy is mostly per
-// operation, not per byte).
-// Warps 0..7 consume every tile together: warp w owns the four tile columns 4w..4w+3 (the matching four
-// entries of every solution block), so each warp only ever needs its own entries of y and the FP64
-// work of a tile row is split evenly over the SM's four sub-partitions.  Both sweeps are written as
-// dot products: forward y_I = inv(L_II) (r_I - sum_J L_IJ y_J) over the column-major copy of row I,
-// backward x_J = inv(L_JJ)^T (y_J - sum_{I>J} L_IJ^T x_I) over the row-major copy of column J.  Each
-// tile row costs two barriers: one after the off-diagonal partial sums, one after the diagonal product.
-// Every mbarrier wait is bounded; on timeout the kernel records an error in the batch error word and
-// stops waiting.
+// The rows are processed in super-rows of SR = 4 tile rows (128 rows).  The setup stores, in the order the
+// sweeps consume them, the factor tiles that couple different super-rows and the explicit inverse X_q of
+// each super-row's lower-triangular diagonal block, so a super-row costs tile GEMVs, one reduction, a
+// product with X_q (or X_q^T) and one more reduction:
+//   forward   y_q = X_q (r_q - sum_{J before q} L_qJ y_J)
+//   backward  x_q = X_q^T (y_q - sum_{I after q} L_Iq^T x_I).
+//
+// A cluster of two CTAs (two SMs) works on one (subdomain, right-hand-side chunk).  Each stream is stored
+// as two arrays of half tiles, lines 0-15 and lines 16-31 of every 32 x 32 tile (a line is a column of the
+// column-major forward tiles, a row of the row-major backward tiles); CTA rank r streams half r.  In each
+// CTA warp 8 is a producer: one elected lane copies runs of half tiles from HBM into a ring of shared-memory
+// slots with bulk asynchronous copies (cp.async.bulk, 32 KB per slot, completion counted on an mbarrier per
+// slot).  Warps 0..7 consume: warp w of rank r owns lines 16r + 2w and 16r + 2w + 1 of every tile (lane =
+// the other tile index), so the FP64 work is spread evenly over both SMs' sub-partitions and a warp only
+// ever needs its own entries of each solution block.
+//
+// Reductions.  The warps' partial sums of a block entry are added in a fixed tree inside each CTA; the
+// entries the peer owns are sent to it with st.async, which counts its bytes on the peer's exchange
+// mbarrier, and each entry's total is (rank 0 sum) + (rank 1 sum).  The result therefore does not depend
+// on timing, on the batch a subdomain is launched in or on which SMs run it.  Every wait is bounded; on
+// timeout the kernel records an error in the batch error word, stops waiting, and before returning waits
+// (again bounded) for its own copies and the peer's stores still in flight.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -31,10 +39,12 @@ namespace {
 
 constexpr int T = 32;
 constexpr int TT = T * T;
+constexpr int HT = TT / 2;             // half tile: 16 lines of 32
 constexpr int SR = 4;                  // tile rows per super-row (matches the plan)
 constexpr int NCW = 8;                 // consumer warps
 constexpr int NCT = NCW * 32;          // consumer threads
 constexpr int NTH = NCT + 32;          // + producer warp
+constexpr int LW = 2;                  // tile lines per consumer warp
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at the GB300 clock
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -47,7 +57,7 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned parit
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
@@ -71,6 +81,31 @@ __device__ bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int
   return true;
 }
 
+// bounded wait that ignores the abort flag (used to let transfers in flight land before returning)
+__device__ void mbar_drain(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return;
+}
+
+// wait for the peer's partial sums.  The peer sends them whatever happens to its own waits, so this
+// wait ignores the abort flag and has a longer limit than the ring waits; if it still gives up, the
+// exchange is marked dead and no later reduction arms or waits on the exchange barriers.
+__device__ void xbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort_flag, volatile int* xdead,
+                          int* err) {
+  if (*xdead) return;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*xdead) return;
+    if (clock64() - t0 > 3 * WAIT_CYCLES) {
+      *xdead = 1;
+      *abort_flag = 1;
+      atomicExch(err, 1);
+      return;
+    }
+  }
+}
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -83,6 +118,38 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+
+// shared::cluster address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned mapa(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+// store into the peer's shared memory; the store's bytes complete a transaction on the peer's barrier
+__device__ __forceinline__ void st_async(unsigned addr, double v, unsigned bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(addr), "d"(v), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(unsigned addr, float v, unsigned bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(addr), "f"(v), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void st_cluster(unsigned addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// all threads of both CTAs; orders every shared-memory access before it (release / acquire)
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory"); }
@@ -103,35 +170,39 @@ __device__ __forceinline__ int find_prob(const int* __restrict__ prefix, int npr
 }
 
 template <typename C> __device__ __forceinline__ C shfl_xor_c(C v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
-template <typename C> __device__ __forceinline__ C shfl_c(C v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 template <typename S, typename C> __device__ __forceinline__ C cvt(S v) { return (C)v; }
 template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// acc[j][u] += tile[(c0+u)*T + lane] * v[j][c0+u] for the four tile lines u of this warp's chunk: four
-// independent accumulation chains, so the four FMAs of a tile are in flight together
-template <typename S, typename C, int KCT>
-__device__ __forceinline__ void gemv4(const S* __restrict__ tile, const C* __restrict__ v, int vstride, C (*acc)[4]) {
-  C t[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) t[u] = cvt<S, C>(tile[u * T]);
-#pragma unroll
-  for (int j = 0; j < KCT; ++j)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc[j][u] = fma(t[u], v[j * vstride + u], acc[j][u]);
+// Sum over the eight warps' partials of entry (ii, j, c) of `buf` ([NCW][SR][KCT][T]) by the four lanes
+// q = 0..3 of a lane quad: lane q adds warps 2q and 2q+1, then two butterfly steps; every lane of the quad
+// ends with the same value, (w0+w1)+(w2+w3) + (w4+w5)+(w6+w7).
+template <typename C, int KCT>
+__device__ __forceinline__ C quad_sum(const C* buf, int ii, int j, int c, int q) {
+  const C* b = buf + ((2 * q * SR + ii) * KCT + j) * T + c;
+  C v = b[0] + b[SR * KCT * T];
+  v += shfl_xor_c(v, 1);
+  v += shfl_xor_c(v, 2);
+  return v;
 }
 
 template <typename S, typename C, int KCT>
-__global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_off, int nstage, int ch) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
+    k_local(BatchDev B, int slot, int ring_off, int nstage, int ch) {
   constexpr int NCH = KCT == 1 ? 2 : 1;   // independent accumulation chains per coupling accumulator
   constexpr int DCH = KCT == 1 ? 2 : 1;   // and per diagonal-block accumulator
+  constexpr int NX = SR * 16 * KCT;       // entries exchanged per reduction (each direction)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[NCW + 1][KCT];
-  __shared__ int abort_flag;
+  __shared__ double peer_rz[KCT];
+  __shared__ int abort_flag, xdead;
+  __shared__ __align__(8) unsigned long long xbar[2];   // the peer's partial sums have landed
+  const unsigned rank = cluster_rank(), peer = rank ^ 1u;
   const int* prefix = B.prefix[slot];
-  const int pi = find_prob(prefix, B.nprob, blockIdx.x);
+  const int item = blockIdx.x >> 1;
+  const int pi = find_prob(prefix, B.nprob, item);
   const ProbDev& P = B.probs[pi];
-  const int li = blockIdx.x - prefix[pi];
+  const int li = item - prefix[pi];
   const int s = li / P.n_rhs_chunks, kch = li % P.n_rhs_chunks;
   const int k0 = kch * KCT;
   const int kc = min(KCT, P.k - k0);
@@ -142,7 +213,7 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
     act[j] = j < kc && P.done[k0 + j] == 0;
     any |= act[j];
   }
-  if (!any) return;
+  if (!any) return;   // both CTAs of the pair read the same flags and leave together
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int e0 = P.sub_e0[s];
   const int n = (P.sub_e0[s + 1] - e0) * P.np;
@@ -152,64 +223,79 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
   const int tr0 = P.sub_trow[s];
   const long long f0 = P.stream_ptr[s];
   const long long nstream = P.stream_ptr[s + 1] - f0;
-  C* y = reinterpret_cast<C*>(smem);                  // [KCT][npad]
+  C* y = reinterpret_cast<C*>(smem);                  // [KCT][npad], own lines used
   C* part = y + KCT * npad;                            // [NCW][SR][KCT][T]
   C* dpart = part + NCW * SR * KCT * T;                // [NCW][SR][KCT][T]
-  C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR * 4][KCT]
-  int* Fs = reinterpret_cast<int*>(tvs + NCW * SR * 4 * KCT);   // tile-row F values
-  S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][ch][TT]
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * ch * TT);
+  C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR][LW][KCT]
+  C* xbuf = tvs + NCW * SR * LW * KCT;                 // [2][SR][KCT][16]: the peer's sums of own entries
+  int* Fs = reinterpret_cast<int*>(xbuf + 2 * NX);     // tile-row F values
+  S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][ch][HT]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * ch * HT);
   unsigned long long* empty = full + nstage;
   if (tid == 0) {
     abort_flag = 0;
+    xdead = 0;
     for (int i = 0; i < nstage; ++i) {
       mbar_init(full + i, 1);
       mbar_init(empty + i, NCW);
     }
+    mbar_init(&xbar[0], 1);
+    mbar_init(&xbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  cluster_sync();   // the peer's barriers exist before any store reaches them
 
   if (w == NCW) {
-    // ---- producer: the forward stream, then the backward stream, nstream tiles each, in chunks of ch
-    // consecutive tiles (one bulk copy per chunk)
+    // ---- producer: half `rank` of the forward stream, then of the backward stream, nstream tiles each,
+    // in runs of ch tiles (one bulk copy per run)
     if (lane == 0) {
-      const S* Lc = reinterpret_cast<const S*>(P.Lc);
-      const S* Lr = reinterpret_cast<const S*>(P.Lr);
+      const long long tot = P.stream_total;
+      const S* Lc = reinterpret_cast<const S*>(P.Lc) + (rank * tot + f0) * HT;
+      const S* Lr = reinterpret_cast<const S*>(P.Lr) + (rank * tot + f0) * HT;
       int sl = 0;
       unsigned round = 0;   // how many times the ring has wrapped
+      long long issued = 0;
       bool ok = true;
       for (int pass = 0; pass < 2 && ok; ++pass) {
-        const S* base = (pass == 0 ? Lc : Lr) + f0 * TT;
-        for (long long t = 0; t < nstream && ok; t += ch) {
+        const S* base = pass == 0 ? Lc : Lr;
+        for (long long t = 0; t < nstream; t += ch) {
           const int len = (int)min((long long)ch, nstream - t);
           if (round > 0 && !mbar_wait(empty + sl, (round - 1) & 1, &abort_flag, B.err)) { ok = false; break; }
-          const unsigned bytes = (unsigned)(len * TT * sizeof(S));
+          const unsigned bytes = (unsigned)(len * HT * sizeof(S));
           mbar_expect_tx(full + sl, bytes);
-          bulk_g2s(ring + (size_t)sl * ch * TT, base + t * TT, bytes, full + sl);
+          bulk_g2s(ring + (size_t)sl * ch * HT, base + t * HT, bytes, full + sl);
+          ++issued;
           if (++sl == nstage) { sl = 0; ++round; }
         }
       }
+      // let every copy issued land (they all have when the consumers finished normally)
+      for (int i = 0; i < nstage && i < issued; ++i) {
+        const long long fills = (issued - i + nstage - 1) / nstage;
+        mbar_drain(full + i, (unsigned)((fills - 1) & 1));
+      }
     }
   } else {
-    // ---- consumers: warp w owns tile columns (forward) / tile rows (backward) c0 .. c0+3 of every tile
-    const int c0 = 4 * w;
+    // ---- consumers: warp w owns the lines l0, l0 + 1 of every tile
+    const int lw = LW * w;               // line within this CTA's half
+    const int l0 = 16 * (int)rank + lw;  // line within the tile
     for (int i = tid; i < nbt; i += NCT) Fs[i] = P.trow_F[tr0 + i];
-    for (int idx = tid; idx < KCT * npad; idx += NCT) {
-      const int j = idx / npad, i = idx - j * npad;
+    for (int idx = tid; idx < KCT * nbt * 16; idx += NCT) {
+      const int j = idx / (nbt * 16), m = idx - j * nbt * 16;
+      const int i = (m >> 4) * T + 16 * (int)rank + (m & 15);
       C v = (C)0;
       if (i < n && act[j]) v = (C)(P.scale[d0 + i] * P.r[(long long)(k0 + j) * P.ndof + d0 + i]);
-      y[idx] = v;
+      y[j * npad + i] = v;
     }
     consumer_sync();
-    // stream cursor: ring slot, its phase parity, position in the chunk, chunk length
+    // stream cursor: ring slot, its phase parity, position in the run, run length
     int cs = 0, cpos = 0;
     unsigned cph = 0;
     long long taken = 0;
     int clen = (int)min((long long)ch, nstream);
     auto acquire = [&]() -> const S* {
       if (cpos == 0 && !mbar_wait(full + cs, cph, &abort_flag, B.err)) return nullptr;
-      return ring + ((size_t)cs * ch + cpos) * TT;
+      return ring + ((size_t)cs * ch + cpos) * HT + lw * T + lane;
     };
     auto release = [&]() {
       ++taken;
@@ -218,22 +304,52 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
         if (lane == 0) mbar_arrive(empty + cs);
         cpos = 0;
         if (++cs == nstage) { cs = 0; cph ^= 1u; }
-        if (taken == nstream) taken = 0;   // the backward stream starts with a fresh chunk
+        if (taken == nstream) taken = 0;   // the backward stream starts with a fresh run
         clen = (int)min((long long)ch, nstream - taken);
       }
     };
-    // Lane l reduces block entry e = l >> 1 (tile row e >> 2 of the super-row, line c0 + (e & 3)) over
-    // four warps' partials (half l & 1), then across the two halves: a fixed order on every warp.
-    const int re = lane >> 1, rii = re >> 2, ru = re & 3, rh = lane & 1;
-    auto reduce_entry = [&](const C* buf, int j) -> C {
-      C v = buf[(((4 * rh) * SR + rii) * KCT + j) * T + c0 + ru];
+    // Reduction number xcount of the partials in buf (written, followed by consumer_sync): send the sums
+    // of the peer's entries, sum this warp's own entries, wait for the peer's sums, and hand each own
+    // entry's total to use(ii, j, u, total) on the first lane of its quad.  Reductions alternate between
+    // two exchange buffers and barriers; the peer cannot send reduction m + 2 before it has received
+    // reduction m + 1, which this CTA sends only after it has read the buffer of reduction m, and thread 0
+    // arms a barrier for reduction m + 2 only after the wait of reduction m.
+    unsigned xcount = 0;
+    const int q4 = lane & 3;
+    C* tw = tvs + w * SR * LW * KCT;
+    auto reduce = [&](const C* buf, auto&& use) {
+      const unsigned xb = xcount & 1u, xph = (xcount >> 1) & 1u;
+      ++xcount;
+      if (tid == 0 && !xdead) mbar_expect_tx(&xbar[xb], (unsigned)(NX * sizeof(C)));
+      const unsigned pbar = mapa(&xbar[xb], peer);
+      const unsigned pbuf = mapa(xbuf + xb * NX, peer);
 #pragma unroll
-      for (int ww = 1; ww < 4; ++ww) v += buf[(((4 * rh + ww) * SR + rii) * KCT + j) * T + c0 + ru];
-      return v + shfl_xor_c(v, 1);
+      for (int rr = 0; rr < KCT; ++rr) {   // NX / (NCT / 4) = KCT rounds
+        const int e = rr * (NCT / 4) + (tid >> 2);
+        const int ii = e / (16 * KCT), j = (e / 16) % KCT, cl = e % 16;
+        const C v = quad_sum<C, KCT>(buf, ii, j, 16 * (int)peer + cl, q4);
+        if (q4 == 0) st_async(pbuf + (unsigned)(((ii * KCT + j) * 16 + cl) * sizeof(C)), v, pbar);
+      }
+      C mine[KCT];
+#pragma unroll
+      for (int rr = 0; rr < KCT; ++rr) {   // SR * LW * KCT own entries per warp, 8 per round
+        const int e = rr * 8 + (lane >> 2);
+        const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
+        mine[rr] = quad_sum<C, KCT>(buf, ii, j, l0 + u, q4);
+      }
+      xbar_wait(&xbar[xb], xph, &abort_flag, &xdead, B.err);
+      if (q4 == 0) {
+#pragma unroll
+        for (int rr = 0; rr < KCT; ++rr) {
+          const int e = rr * 8 + (lane >> 2);
+          const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
+          use(ii, j, u, mine[rr] + xbuf[xb * NX + (ii * KCT + j) * 16 + lw + u]);
+        }
+      }
+      __syncwarp();
     };
-    C* tw = tvs + w * SR * 4 * KCT;   // this warp's right-hand sides of the diagonal block product
-    // one super-row (tile rows I0 .. I0+ntr-1): acc holds the coupling sums; t = y_S - sum over warps,
-    // y_S = X t (forward) or X^T t (backward) with X the inverse of the diagonal block
+    // one super-row (tile rows I0 .. I0+ntr-1): acc holds the coupling sums; t = y_q - (sum of all
+    // partials), y_q = X_q t (forward) or X_q^T t (backward)
     auto finish_super = [&](int I0, int ntr, C (*acc)[KCT][NCH], bool fwd) {
 #pragma unroll
       for (int ii = 0; ii < SR; ++ii)
@@ -245,13 +361,9 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
           part[((w * SR + ii) * KCT + j) * T + lane] = ii < ntr ? v : (C)0;
         }
       consumer_sync();
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) {
-        const C tot = reduce_entry(part, j);
-        const C t = rii < ntr ? y[j * npad + (I0 + rii) * T + c0 + ru] - tot : (C)0;
-        if (rh == 0) tw[re * KCT + j] = t;
-      }
-      __syncwarp();
+      reduce(part, [&](int ii, int j, int u, C tot) {
+        tw[(ii * LW + u) * KCT + j] = ii < ntr ? y[j * npad + (I0 + ii) * T + l0 + u] - tot : (C)0;
+      });
       C o[SR][KCT][DCH];
 #pragma unroll
       for (int ii = 0; ii < SR; ++ii)
@@ -266,21 +378,17 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
         for (int jj = 0; jj <= i; ++jj) {
           const S* tile = acquire();
           if (tile) {
-            const S* tl = tile + c0 * T + lane;
-            C tv[4];
+            C tv[LW];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) tv[u] = cvt<S, C>(tl[u * T]);
+            for (int u = 0; u < LW; ++u) tv[u] = cvt<S, C>(tile[u * T]);
             // forward: X_(i,jj) times block jj into output block i; backward: X_(i,jj)^T times block i
             // into output block jj
             const int src = fwd ? jj : i;
 #pragma unroll
             for (int j = 0; j < KCT; ++j) {
-              const C* vv = tw + (src * 4) * KCT + j;
               C& x = fwd ? o[i][j][jj % DCH] : o[jj][j][i % DCH];
-              x = fma(tv[0], vv[0], x);
-              x = fma(tv[1], vv[KCT], x);
-              x = fma(tv[2], vv[2 * KCT], x);
-              x = fma(tv[3], vv[3 * KCT], x);
+#pragma unroll
+              for (int u = 0; u < LW; ++u) x = fma(tv[u], tw[(src * LW + u) * KCT + j], x);
             }
           }
           release();
@@ -296,12 +404,9 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
           dpart[((w * SR + ii) * KCT + j) * T + lane] = v;
         }
       consumer_sync();
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) {
-        const C tot = reduce_entry(dpart, j);
-        if (rh == 0 && rii < ntr) y[j * npad + (I0 + rii) * T + c0 + ru] = tot;
-      }
-      __syncwarp();
+      reduce(dpart, [&](int ii, int j, int u, C tot) {
+        if (ii < ntr) y[j * npad + (I0 + ii) * T + l0 + u] = tot;
+      });
     };
     C acc[SR][KCT][NCH];
     auto zero_acc = [&]() {
@@ -312,21 +417,18 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
 #pragma unroll
           for (int h = 0; h < NCH; ++h) acc[ii][j][h] = (C)0;
     };
-    // one coupling tile: a[j][0] += sum_u tile line (c0+u) * v[j][c0+u], then the chains rotate so the
+    // one coupling tile: a[j][0] += sum_u tile line (l0+u) * v[j][l0+u], then the chains rotate so the
     // next tile accumulates into the next chain (static register indices throughout)
     auto couple = [&](const S* tile, const C* v, C (&a)[KCT][NCH]) {
-      const S* tl = tile + c0 * T + lane;
-      C tv[4];
+      C tv[LW];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) tv[u] = cvt<S, C>(tl[u * T]);
+      for (int u = 0; u < LW; ++u) tv[u] = cvt<S, C>(tile[u * T]);
 #pragma unroll
       for (int j = 0; j < KCT; ++j) {
         const C* vj = v + j * npad;
         C x = a[j][0];
-        x = fma(tv[0], vj[0], x);
-        x = fma(tv[1], vj[1], x);
-        x = fma(tv[2], vj[2], x);
-        x = fma(tv[3], vj[3], x);
+#pragma unroll
+        for (int u = 0; u < LW; ++u) x = fma(tv[u], vj[u], x);
 #pragma unroll
         for (int h = 0; h + 1 < NCH; ++h) a[j][h] = a[j][h + 1];
         a[j][NCH - 1] = x;
@@ -341,7 +443,7 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
         if (ii >= ntr) break;
         for (int J = Fs[I0 + ii]; J < I0; ++J) {
           const S* tile = acquire();
-          if (tile) couple(tile, y + J * T + c0, acc[ii]);
+          if (tile) couple(tile, y + J * T + l0, acc[ii]);
           release();
         }
       }
@@ -361,7 +463,7 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
         for (int jj = 0; jj < SR; ++jj) {
           if (jj < jstart || jj >= ntr) continue;
           const S* tile = acquire();
-          if (tile) couple(tile, y + I * T + c0, acc[jj]);
+          if (tile) couple(tile, y + I * T + l0, acc[jj]);
           release();
         }
       }
@@ -369,12 +471,15 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
     }
   }
   __syncthreads();
-  // z_i = D^{-1/2} y, partial (r, z) for this subdomain (producer warp contributes zeros)
+  // z_i = D^{-1/2} y on own entries, partial (r, z) of this CTA; rank 1 hands its sums to rank 0, which
+  // writes (rank 0 sum) + (rank 1 sum)
   double prz[KCT];
 #pragma unroll
   for (int j = 0; j < KCT; ++j) prz[j] = 0.0;
   if (w < NCW) {
-    for (int i = tid; i < n; i += NCT) {
+    for (int m = tid; m < nbt * 16; m += NCT) {
+      const int i = (m >> 4) * T + 16 * (int)rank + (m & 15);
+      if (i >= n) continue;
       const double sc = P.scale[d0 + i];
 #pragma unroll
       for (int j = 0; j < KCT; ++j) {
@@ -392,14 +497,17 @@ __global__ void __launch_bounds__(NTH) k_local(BatchDev B, int slot, int ring_of
     if (lane == 0) red[w][j] = v;
   }
   __syncthreads();
+  double csum = 0.0;
   if (tid < kc) {
-    double sum = 0.0;
-    for (int ww = 0; ww <= NCW; ++ww) sum += red[ww][tid];
-    P.part_rz[(long long)s * P.k + k0 + tid] = act[tid] ? sum : 0.0;
+    for (int ww = 0; ww <= NCW; ++ww) csum += red[ww][tid];
+    if (rank == 1) st_cluster(mapa(&peer_rz[tid], 0), csum);
   }
+  cluster_sync();   // also: no access to this CTA's shared memory from the peer after this point
+  if (rank == 0 && tid < kc) P.part_rz[(long long)s * P.k + k0 + tid] = P.done[k0 + tid] == 0 ? csum + peer_rz[tid] : 0.0;
 }
 
-// shared memory: y, partial sums and F values, then a ring of nstage slots of ch tiles (32 KB per slot)
+// shared memory: y, partial sums, exchange buffers and F values, then a ring of nstage slots of ch half
+// tiles (32 KB per slot)
 template <typename S, typename C>
 int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int* total) {
   int dev = 0;
@@ -407,13 +515,15 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int*
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int npad = ((ndof_max + T - 1) / T) * T;
-  const int head = (int)sizeof(C) * (kct * npad + 2 * NCW * SR * kct * T + NCW * SR * 4 * kct) + 4 * (npad / T + 4);
+  const int head = (int)sizeof(C) * (kct * npad + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 2 * SR * kct * 16) +
+                   4 * (npad / T + 4);
   const int off = (head + 127) & ~127;
   const int budget = optin - 2048 - off;   // static shared memory and slack
-  int c = (32 * 1024) / (int)(TT * sizeof(S));
+  const int hb = (int)(HT * sizeof(S));
+  int c = (32 * 1024) / hb;
   int ns = 0;
   for (; c >= 1; c /= 2) {
-    ns = budget / (c * (int)(TT * sizeof(S)) + 16);
+    ns = budget / (c * hb + 16);
     if (ns >= 3) break;
   }
   if (c < 1) c = 1;
@@ -422,12 +532,12 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int*
   *ring_off = off;
   *nstage = ns;
   *ch = c;
-  *total = off + ns * c * (int)(TT * sizeof(S)) + ns * 16;
+  *total = off + ns * c * hb + ns * 16;
   return 0;
 }
 
 template <typename K>
-int ensure_smem(K fn, int smem) {
+int ensure_smem(K fn) {
   static std::mutex mu;
   static std::set<std::pair<const void*, int>> done;
   int dev = 0;
@@ -439,25 +549,22 @@ int ensure_smem(K fn, int smem) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
   if (e != cudaSuccess) return (int)e;
   done.insert({(const void*)fn, dev});
-  (void)smem;
   return 0;
 }
 
-template <typename S, typename C>
-int launch_local_t(const BatchDev& B, int slot, int kcl, int total, int ndof_max, cudaStream_t st) {
+template <typename S, typename C, int KCT>
+int launch_one(const BatchDev& B, int slot, int items, int ndof_max, cudaStream_t st) {
   int ring_off, nstage, ch, smem;
-  if (kcl == 0) {
-    if (smem_layout<S, C>(ndof_max, 1, &ring_off, &nstage, &ch, &smem)) return (int)cudaErrorInvalidValue;
-    auto fn = k_local<S, C, 1>;
-    if (int e = ensure_smem(fn, smem)) return e;
-    fn<<<total, NTH, smem, st>>>(B, slot, ring_off, nstage, ch);
-  } else {
-    if (smem_layout<S, C>(ndof_max, KC, &ring_off, &nstage, &ch, &smem)) return (int)cudaErrorInvalidValue;
-    auto fn = k_local<S, C, KC>;
-    if (int e = ensure_smem(fn, smem)) return e;
-    fn<<<total, NTH, smem, st>>>(B, slot, ring_off, nstage, ch);
-  }
+  if (smem_layout<S, C>(ndof_max, KCT, &ring_off, &nstage, &ch, &smem)) return (int)cudaErrorInvalidValue;
+  auto fn = k_local<S, C, KCT>;
+  if (int e = ensure_smem(fn)) return e;
+  fn<<<2 * items, NTH, smem, st>>>(B, slot, ring_off, nstage, ch);   // one CTA pair per item
   return (int)cudaGetLastError();
+}
+
+template <typename S, typename C>
+int launch_local_t(const BatchDev& B, int slot, int kcl, int items, int ndof_max, cudaStream_t st) {
+  return kcl == 0 ? launch_one<S, C, 1>(B, slot, items, ndof_max, st) : launch_one<S, C, KC>(B, slot, items, ndof_max, st);
 }
 
 }  // namespace

@@ -276,18 +276,22 @@ __global__ void __launch_bounds__(256) k_dinv(EnvDev E, const S* __restrict__ L,
   }
 }
 
-// stream tile p = (src[p] >= 0 ? factor tile src[p] : inverse-block tile -src[p]-1), transposed if asked
+// stream tile p = (src[p] >= 0 ? factor tile src[p] : inverse-block tile -src[p]-1), transposed if asked.
+// The stream is stored as two arrays of half tiles: lines 0-15 of every tile, then lines 16-31 (a line
+// is a row of the stored tile: a column of the factor tile when transposed), so that each CTA of a pair
+// reads its half of a run of tiles with one contiguous copy.
 template <typename S>
 __global__ void k_stream_gather(const S* __restrict__ L, const S* __restrict__ X, const long long* __restrict__ src,
                                 S* __restrict__ dst, long long n, int transpose) {
+  constexpr int HT = TT / 2;
   __shared__ S buf[T][T + 1];
   for (long long p = blockIdx.x; p < n; p += gridDim.x) {
     const long long v = src[p];
     const S* a = v >= 0 ? L + v * TT : X + (-v - 1) * TT;
-    S* d = dst + p * TT;
     for (int u = threadIdx.x; u < TT; u += blockDim.x) buf[u / T][u % T] = a[u];
     __syncthreads();
-    for (int u = threadIdx.x; u < TT; u += blockDim.x) d[u] = transpose ? buf[u % T][u / T] : buf[u / T][u % T];
+    for (int u = threadIdx.x; u < TT; u += blockDim.x)
+      dst[(long long)(u / HT) * n * HT + p * HT + (u % HT)] = transpose ? buf[u % T][u / T] : buf[u / T][u % T];
     __syncthreads();
   }
 }

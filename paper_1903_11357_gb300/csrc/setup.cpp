@@ -296,6 +296,7 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
   D.trow_ptr = env0.trow_ptr.as<long long>(); D.stream_ptr = env0.stream_ptr.as<long long>();
   D.sub_sr = env0.sub_sr.as<int>(); D.sr_ilast = env0.sr_ilast.as<int>();
   D.Lr = Lr0.ptr; D.Lc = Lc0.ptr; D.scale = scale0.as<double>();
+  D.stream_total = (long long)P.env0.fwd_src.size();
   D.r = ident.as<double>(); D.z = A0inv.as<double>();
   D.done = (int*)misc.ptr;
   D.part_rz = (double*)((char*)misc.ptr + rz_off);
