@@ -178,8 +178,9 @@ typedef struct {
   int precision;          /* dgasm_precision of the local factors */
   int64_t local_dofs;     /* sum of the subdomain dof counts (= ndof) */
   int64_t local_tiles;    /* 32x32 tiles in the envelopes of all local factors (one copy) */
-  int64_t stream_tiles;   /* 32x32 tiles read by one sweep of the local solves (envelope tiles outside the
-                             diagonal super-row blocks plus the inverted super-row blocks) */
+  int64_t stream_tiles;   /* 32x32 tiles read by one local solve, forward and backward sweep together:
+                             envelope tiles outside the diagonal super-row blocks, the inverted super-row
+                             blocks, and the few zero tiles that keep backward runs contiguous */
   int64_t factor_flops;   /* flops of the tile Cholesky of the local factors (tile-level count) */
   int64_t nnzb;           /* blocks of the block-sparse matrix */
   double plan_ms;         /* host part of dgasm_setup: partition, ordering, envelopes, task lists */
@@ -229,11 +230,12 @@ int dgasm_solve_batch(int nprob, const dgasm_prec_t* pcs, const int* nrhs, const
 int dgasm_lanczos(int k, const double* alpha, const double* beta, double* lambda_min, double* lambda_max);
 
 /* ---- Kernel timing (CUDA events on the launching streams) --------------------------------------
- * When enabled, every launch of the kinds below made by dgasm_setup / dgasm_solve is bracketed by
- * CUDA events (inside the captured graphs as event nodes) and its device time is accumulated.
+ * Every launch of an enabled kind made by dgasm_setup / dgasm_solve is bracketed by CUDA events
+ * (inside the captured graphs as event nodes) and its device time is accumulated.
  * Kinds: 0 SpMV, 1 x/r update + restriction, 2 local solves, 3 coarse solve, 4 p update,
- * 5 Cholesky diagonal tiles, 6 Cholesky panels, 7 Cholesky trailing updates.  Process-wide. */
-int dgasm_profile_enable(int on);
+ * 5 Cholesky diagonal tiles, 6 Cholesky panels, 7 Cholesky trailing updates.  Process-wide.
+ * mask: bit k enables kind k (0xFF: all kinds, 0: off).  Timing fewer kinds adds fewer event nodes. */
+int dgasm_profile_enable(int mask);
 /* Accumulated time (ms) and launch count of one kind since the last reset (reset = 1 clears). */
 int dgasm_profile_read(int kind, double* total_ms, int64_t* launches, int reset);
 

@@ -61,10 +61,12 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.rtol = rtol;
   D.rowptr = pc.rowptr.as<int>(); D.col = pc.col.as<int>(); D.vals = pc.vals.as<double>(); D.perm = pc.perm.as<int>();
   D.sub_e0 = pc.sub_e0.as<int>(); D.sub_trow = pc.env.sub_trow.as<int>(); D.trow_F = pc.env.trow_F.as<int>();
-  D.trow_ptr = pc.env.trow_ptr.as<long long>(); D.stream_ptr = pc.env.stream_ptr.as<long long>();
-  D.sub_sr = pc.env.sub_sr.as<int>(); D.sr_ilast = pc.env.sr_ilast.as<int>();
+  D.trow_ptr = pc.env.trow_ptr.as<long long>(); D.fwd_ptr = pc.env.fwd_ptr.as<long long>();
+  D.bwd_ptr = pc.env.bwd_ptr.as<long long>();
+  D.sub_sr = pc.env.sub_sr.as<int>(); D.fwd_run = pc.env.fwd_run.as<int>(); D.bwd_run = pc.env.bwd_run.as<int>();
   D.Lr = pc.Lr.ptr; D.Lc = pc.Lc.ptr; D.scale = pc.scale.as<double>();
-  D.stream_total = (long long)pc.P.env.fwd_src.size();
+  D.fwd_total = (long long)pc.P.env.fwd_src.size();
+  D.bwd_total = (long long)pc.P.env.bwd_src.size();
   D.grp_ptr = pc.grp_ptr.as<int>(); D.grp_elems = pc.grp_elems.as<int>(); D.agg_int = pc.agg_int.as<int>();
   D.r0t = pc.r0t.as<double>(); D.A0inv = pc.A0inv.as<double>();
   D.b_user = b_user; D.x_user = x_user;

@@ -11,6 +11,8 @@ namespace dgasm {
 constexpr int NTHREADS = 256;  // threads per CTA of the vector kernels
 constexpr int KMAX = 8;        // right-hand sides per problem
 constexpr int KC = 4;          // right-hand sides per local-solve CTA
+constexpr int SUPER_ROW = 8;   // tile rows per super-row of the local triangular solves
+constexpr long long ZERO_TILE = -(1LL << 62);   // solve-stream entry: a tile of zeros
 
 enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
 constexpr int K_SPMV_P = K_NKINDS + 8;   // per-degree SpMV prefix slots p = 1..8
@@ -37,12 +39,14 @@ struct ProbDev {
   const int* sub_trow;
   const int* trow_F;
   const long long* trow_ptr;
-  const long long* stream_ptr;  // [nsub+1] offsets of each subdomain's solve streams
+  const long long* fwd_ptr;     // [nsub+1] each subdomain's range in the forward stream
+  const long long* bwd_ptr;     // [nsub+1] and in the backward stream
+  long long fwd_total, bwd_total;  // tiles in each stream (all subdomains)
   const int* sub_sr;            // [nsub+1] first global super-row of each subdomain
-  const int* sr_ilast;          // per global super-row: last tile row coupled to its columns
-  long long stream_total;  // tiles in each of the two streams (all subdomains)
-  const void* Lr;     // backward stream: row-major tiles in consumption order, as [2][stream_total][16 x 32]
-  const void* Lc;     // forward stream: column-major tiles in consumption order, same split layout
+  const int* fwd_run;           // [global super-row][SUPER_ROW][2]: coupling runs (first operand block, tiles)
+  const int* bwd_run;
+  const void* Lr;     // backward stream: row-major tiles in consumption order, as [2][bwd_total][16 x 32]
+  const void* Lc;     // forward stream: column-major tiles in consumption order, as [2][fwd_total][16 x 32]
   const double* scale;
   // groups and coarse space
   const int* grp_ptr;

@@ -2,28 +2,31 @@
 // Cholesky factor A~_i = L L^T (A~_i = D^{-1/2} A_i D^{-1/2}): forward substitution with L, backward
 // substitution with L^T.
 //
-// The rows are processed in super-rows of SR = 4 tile rows (128 rows).  The setup stores, in the order the
+// The rows are processed in super-rows of SR = 8 tile rows (256 rows).  The setup stores, in the order the
 // sweeps consume them, the factor tiles that couple different super-rows and the explicit inverse X_q of
 // each super-row's lower-triangular diagonal block, so a super-row costs tile GEMVs, one reduction, a
 // product with X_q (or X_q^T) and one more reduction:
 //   forward   y_q = X_q (r_q - sum_{J before q} L_qJ y_J)
 //   backward  x_q = X_q^T (y_q - sum_{I after q} L_Iq^T x_I).
+// The streams are cut into runs: consecutive tiles that add into one output block with consecutive
+// operand blocks (the plan gives each coupling run's first operand block and length), so a warp keeps
+// one pair of accumulators per run and walks the tiles of a run with plain pointer steps.
 //
 // A cluster of two CTAs (two SMs) works on one (subdomain, right-hand-side chunk).  Each stream is stored
 // as two arrays of half tiles, lines 0-15 and lines 16-31 of every 32 x 32 tile (a line is a column of the
 // column-major forward tiles, a row of the row-major backward tiles); CTA rank r streams half r.  In each
 // CTA warp 8 is a producer: one elected lane copies runs of half tiles from HBM into a ring of shared-memory
 // slots with bulk asynchronous copies (cp.async.bulk, 32 KB per slot, completion counted on an mbarrier per
-// slot).  Warps 0..7 consume: warp w of rank r owns lines 16r + 2w and 16r + 2w + 1 of every tile (lane =
-// the other tile index), so the FP64 work is spread evenly over both SMs' sub-partitions and a warp only
-// ever needs its own entries of each solution block.
+// slot).  Warps 0..7 consume: warp w of rank r owns lines 16r + 2w and 16r + 2w + 1 of every tile (stored
+// interleaved, one vector load per tile; lane = the other tile index), so the FP64 work is spread evenly
+// over both SMs' sub-partitions and a warp only ever needs its own entries of each solution block.
 //
 // Reductions.  The warps' partial sums of a block entry are added in a fixed tree inside each CTA; the
 // entries the peer owns are sent to it with st.async, which counts its bytes on the peer's exchange
 // mbarrier, and each entry's total is (rank 0 sum) + (rank 1 sum).  The result therefore does not depend
 // on timing, on the batch a subdomain is launched in or on which SMs run it.  Every wait is bounded; on
 // timeout the kernel records an error in the batch error word, stops waiting, and before returning waits
-// (again bounded) for its own copies and the peer's stores still in flight.
+// (again bounded) for its own copies still in flight.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,7 +43,7 @@ namespace {
 constexpr int T = 32;
 constexpr int TT = T * T;
 constexpr int HT = TT / 2;             // half tile: 16 lines of 32
-constexpr int SR = 4;                  // tile rows per super-row (matches the plan)
+constexpr int SR = SUPER_ROW;          // tile rows per super-row (the plan's)
 constexpr int NCW = 8;                 // consumer warps
 constexpr int NCT = NCW * 32;          // consumer threads
 constexpr int NTH = NCT + 32;          // + producer warp
@@ -171,8 +174,33 @@ __device__ __forceinline__ int find_prob(const int* __restrict__ prefix, int npr
 
 template <typename C> __device__ __forceinline__ C shfl_xor_c(C v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 
-template <typename S, typename C> __device__ __forceinline__ C cvt(S v) { return (C)v; }
-template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
+// the two entries of a warp's line pair, stored next to each other in the solve streams
+template <typename S> struct Pair;
+template <> struct Pair<double> { using V = double2; };
+template <> struct Pair<float> { using V = float2; };
+template <> struct Pair<__nv_bfloat16> { using V = __nv_bfloat162; };
+
+template <typename C>
+__device__ __forceinline__ void ld_pair(const double2* p, C& a, C& b) {
+  const double2 v = *p;
+  a = (C)v.x;
+  b = (C)v.y;
+}
+template <typename C>
+__device__ __forceinline__ void ld_pair(const float2* p, C& a, C& b) {
+  const float2 v = *p;
+  a = (C)v.x;
+  b = (C)v.y;
+}
+template <typename C>
+__device__ __forceinline__ void ld_pair(const __nv_bfloat162* p, C& a, C& b) {
+  const float2 v = __bfloat1622float2(*p);
+  a = (C)v.x;
+  b = (C)v.y;
+}
+// an operand pair (two consecutive entries, 2-element aligned)
+__device__ __forceinline__ double2 ld_pair2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ float2 ld_pair2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
 // Sum over the eight warps' partials of entry (ii, j, c) of `buf` ([NCW][SR][KCT][T]) by the four lanes
 // q = 0..3 of a lane quad: lane q adds warps 2q and 2q+1, then two butterfly steps; every lane of the quad
@@ -189,9 +217,10 @@ __device__ __forceinline__ C quad_sum(const C* buf, int ii, int j, int c, int q)
 template <typename S, typename C, int KCT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     k_local(BatchDev B, int slot, int ring_off, int nstage, int ch) {
-  constexpr int NCH = KCT == 1 ? 2 : 1;   // independent accumulation chains per coupling accumulator
-  constexpr int DCH = KCT == 1 ? 2 : 1;   // and per diagonal-block accumulator
+  using VS = typename Pair<S>::V;
   constexpr int NX = SR * 16 * KCT;       // entries exchanged per reduction (each direction)
+  constexpr int NRP = NX / (NCT / 4);     // rounds of the peer's sums, a lane quad per entry
+  constexpr int NRO = SR * LW * KCT / 8;  // rounds of a warp's own entries, eight quads per round
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[NCW + 1][KCT];
   __shared__ double peer_rz[KCT];
@@ -218,17 +247,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   const int e0 = P.sub_e0[s];
   const int n = (P.sub_e0[s + 1] - e0) * P.np;
   const long long d0 = (long long)e0 * P.np;
-  const int nbt = (n + T - 1) / T, npad = nbt * T;
+  const int nbt = (n + T - 1) / T, npadh = nbt * 16;
   const int nsr = (nbt + SR - 1) / SR;
-  const int tr0 = P.sub_trow[s];
-  const long long f0 = P.stream_ptr[s];
-  const long long nstream = P.stream_ptr[s + 1] - f0;
-  C* y = reinterpret_cast<C*>(smem);                  // [KCT][npad], own lines used
-  C* part = y + KCT * npad;                            // [NCW][SR][KCT][T]
+  const int sr0 = P.sub_sr[s];
+  const long long ff0 = P.fwd_ptr[s], nfwd = P.fwd_ptr[s + 1] - ff0;
+  const long long bb0 = P.bwd_ptr[s], nbwd = P.bwd_ptr[s + 1] - bb0;
+  C* y = reinterpret_cast<C*>(smem);                  // [KCT][nbt][16]: own lines of every block
+  C* part = y + KCT * npadh;                           // [NCW][SR][KCT][T]
   C* dpart = part + NCW * SR * KCT * T;                // [NCW][SR][KCT][T]
-  C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR][LW][KCT]
-  C* xbuf = tvs + NCW * SR * LW * KCT;                 // [2][SR][KCT][16]: the peer's sums of own entries
-  int* Fs = reinterpret_cast<int*>(xbuf + 2 * NX);     // tile-row F values
+  C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR][KCT][LW]
+  C* xbuf = tvs + NCW * SR * KCT * LW;                 // [2][SR][KCT][16]: the peer's sums of own entries
   S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][ch][HT]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * ch * HT);
   unsigned long long* empty = full + nstage;
@@ -247,20 +275,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   cluster_sync();   // the peer's barriers exist before any store reaches them
 
   if (w == NCW) {
-    // ---- producer: half `rank` of the forward stream, then of the backward stream, nstream tiles each,
-    // in runs of ch tiles (one bulk copy per run)
+    // ---- producer: half `rank` of the subdomain's forward stream, then of its backward stream, in runs
+    // of ch tiles (one bulk copy per run)
     if (lane == 0) {
-      const long long tot = P.stream_total;
-      const S* Lc = reinterpret_cast<const S*>(P.Lc) + (rank * tot + f0) * HT;
-      const S* Lr = reinterpret_cast<const S*>(P.Lr) + (rank * tot + f0) * HT;
+      const S* Lc = reinterpret_cast<const S*>(P.Lc) + (rank * P.fwd_total + ff0) * HT;
+      const S* Lr = reinterpret_cast<const S*>(P.Lr) + (rank * P.bwd_total + bb0) * HT;
       int sl = 0;
       unsigned round = 0;   // how many times the ring has wrapped
       long long issued = 0;
       bool ok = true;
       for (int pass = 0; pass < 2 && ok; ++pass) {
         const S* base = pass == 0 ? Lc : Lr;
-        for (long long t = 0; t < nstream; t += ch) {
-          const int len = (int)min((long long)ch, nstream - t);
+        const long long len_pass = pass == 0 ? nfwd : nbwd;
+        for (long long t = 0; t < len_pass; t += ch) {
+          const int len = (int)min((long long)ch, len_pass - t);
           if (round > 0 && !mbar_wait(empty + sl, (round - 1) & 1, &abort_flag, B.err)) { ok = false; break; }
           const unsigned bytes = (unsigned)(len * HT * sizeof(S));
           mbar_expect_tx(full + sl, bytes);
@@ -279,34 +307,77 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     // ---- consumers: warp w owns the lines l0, l0 + 1 of every tile
     const int lw = LW * w;               // line within this CTA's half
     const int l0 = 16 * (int)rank + lw;  // line within the tile
-    for (int i = tid; i < nbt; i += NCT) Fs[i] = P.trow_F[tr0 + i];
-    for (int idx = tid; idx < KCT * nbt * 16; idx += NCT) {
-      const int j = idx / (nbt * 16), m = idx - j * nbt * 16;
+    for (int idx = tid; idx < KCT * npadh; idx += NCT) {
+      const int j = idx / npadh, m = idx - j * npadh;
       const int i = (m >> 4) * T + 16 * (int)rank + (m & 15);
       C v = (C)0;
       if (i < n && act[j]) v = (C)(P.scale[d0 + i] * P.r[(long long)(k0 + j) * P.ndof + d0 + i]);
-      y[j * npad + i] = v;
+      y[idx] = v;
     }
     consumer_sync();
-    // stream cursor: ring slot, its phase parity, position in the run, run length
-    int cs = 0, cpos = 0;
+    // stream cursor: ring slot, its phase parity, position in the run of ch tiles, run length, tiles of
+    // the current stream taken and its length
+    int cs = 0, cpos = 0, clen = 0;
     unsigned cph = 0;
-    long long taken = 0;
-    int clen = (int)min((long long)ch, nstream);
-    auto acquire = [&]() -> const S* {
-      if (cpos == 0 && !mbar_wait(full + cs, cph, &abort_flag, B.err)) return nullptr;
-      return ring + ((size_t)cs * ch + cpos) * HT + lw * T + lane;
+    long long taken = 0, plen = 0;
+    auto start_pass = [&](long long len) {
+      plen = len;
+      taken = 0;
+      clen = (int)min((long long)ch, len);
     };
-    auto release = [&]() {
-      ++taken;
-      if (++cpos == clen) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty + cs);
-        cpos = 0;
-        if (++cs == nstage) { cs = 0; cph ^= 1u; }
-        if (taken == nstream) taken = 0;   // the backward stream starts with a fresh run
-        clen = (int)min((long long)ch, nstream - taken);
+    // One run: cnt consecutive stream tiles into one output block of this warp's lanes,
+    //   res[j] = sum_k (line pair of tile k) . (operand pair k of right-hand side j),
+    // operand pair k of rhs j at v + k * vstride + j * jstride.  Tiles alternate between two
+    // accumulators (restarting at each run of ch tiles, so the grouping depends only on the plan).
+    // After a timed-out wait the data are stale; the error word is set and the result is discarded.
+    auto run = [&](int cnt, const C* v, int vstride, int jstride, C (&res)[KCT]) {
+      C a0[KCT], a1[KCT];
+#pragma unroll
+      for (int j = 0; j < KCT; ++j) a0[j] = a1[j] = (C)0;
+      int k = 0;
+      while (k < cnt) {
+        if (cpos == 0) mbar_wait(full + cs, cph, &abort_flag, B.err);
+        const int m = min(cnt - k, clen - cpos);
+        const VS* tp = reinterpret_cast<const VS*>(ring + ((size_t)cs * ch + cpos) * HT) + w * T + lane;
+        const C* vp = v + (size_t)k * vstride;
+        int t = 0;
+        for (; t + 1 < m; t += 2) {
+          C x0, x1, z0, z1;
+          ld_pair(tp + t * (HT / 2), x0, x1);
+          ld_pair(tp + (t + 1) * (HT / 2), z0, z1);
+#pragma unroll
+          for (int j = 0; j < KCT; ++j) {
+            const auto o0 = ld_pair2(vp + t * vstride + j * jstride);
+            const auto o1 = ld_pair2(vp + (t + 1) * vstride + j * jstride);
+            a0[j] = fma(x0, o0.x, a0[j]);
+            a1[j] = fma(z0, o1.x, a1[j]);
+            a0[j] = fma(x1, o0.y, a0[j]);
+            a1[j] = fma(z1, o1.y, a1[j]);
+          }
+        }
+        if (t < m) {
+          C x0, x1;
+          ld_pair(tp + t * (HT / 2), x0, x1);
+#pragma unroll
+          for (int j = 0; j < KCT; ++j) {
+            const auto o0 = ld_pair2(vp + t * vstride + j * jstride);
+            a0[j] = fma(x0, o0.x, a0[j]);
+            a0[j] = fma(x1, o0.y, a0[j]);
+          }
+        }
+        k += m;
+        cpos += m;
+        taken += m;
+        if (cpos == clen) {   // this run of ch tiles is used up: hand the slot back
+          __syncwarp();
+          if (lane == 0) mbar_arrive(empty + cs);
+          cpos = 0;
+          if (++cs == nstage) { cs = 0; cph ^= 1u; }
+          clen = (int)min((long long)ch, plen - taken);
+        }
       }
+#pragma unroll
+      for (int j = 0; j < KCT; ++j) res[j] = a0[j] + a1[j];
     };
     // Reduction number xcount of the partials in buf (written, followed by consumer_sync): send the sums
     // of the peer's entries, sum this warp's own entries, wait for the peer's sums, and hand each own
@@ -316,7 +387,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     // arms a barrier for reduction m + 2 only after the wait of reduction m.
     unsigned xcount = 0;
     const int q4 = lane & 3;
-    C* tw = tvs + w * SR * LW * KCT;
+    C* tw = tvs + w * SR * KCT * LW;   // this warp's own entries of t (the block product's input)
     auto reduce = [&](const C* buf, auto&& use) {
       const unsigned xb = xcount & 1u, xph = (xcount >> 1) & 1u;
       ++xcount;
@@ -324,15 +395,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       const unsigned pbar = mapa(&xbar[xb], peer);
       const unsigned pbuf = mapa(xbuf + xb * NX, peer);
 #pragma unroll
-      for (int rr = 0; rr < KCT; ++rr) {   // NX / (NCT / 4) = KCT rounds
+      for (int rr = 0; rr < NRP; ++rr) {
         const int e = rr * (NCT / 4) + (tid >> 2);
         const int ii = e / (16 * KCT), j = (e / 16) % KCT, cl = e % 16;
         const C v = quad_sum<C, KCT>(buf, ii, j, 16 * (int)peer + cl, q4);
         if (q4 == 0) st_async(pbuf + (unsigned)(((ii * KCT + j) * 16 + cl) * sizeof(C)), v, pbar);
       }
-      C mine[KCT];
+      C mine[NRO];
 #pragma unroll
-      for (int rr = 0; rr < KCT; ++rr) {   // SR * LW * KCT own entries per warp, 8 per round
+      for (int rr = 0; rr < NRO; ++rr) {
         const int e = rr * 8 + (lane >> 2);
         const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
         mine[rr] = quad_sum<C, KCT>(buf, ii, j, l0 + u, q4);
@@ -340,7 +411,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       xbar_wait(&xbar[xb], xph, &abort_flag, &xdead, B.err);
       if (q4 == 0) {
 #pragma unroll
-        for (int rr = 0; rr < KCT; ++rr) {
+        for (int rr = 0; rr < NRO; ++rr) {
           const int e = rr * 8 + (lane >> 2);
           const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
           use(ii, j, u, mine[rr] + xbuf[xb * NX + (ii * KCT + j) * 16 + lw + u]);
@@ -348,127 +419,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       }
       __syncwarp();
     };
-    // one super-row (tile rows I0 .. I0+ntr-1): acc holds the coupling sums; t = y_q - (sum of all
-    // partials), y_q = X_q t (forward) or X_q^T t (backward)
-    auto finish_super = [&](int I0, int ntr, C (*acc)[KCT][NCH], bool fwd) {
+    // One super-row of a sweep: coupling runs, reduction to t = y_q - sum, block-inverse runs on t,
+    // reduction to the new y_q.  runs: the plan's (first operand block, tiles) per output block.
+    auto super_row = [&](int q, const int* runs, bool fwd) {
+      const int I0 = q * SR, ntr = min(SR, nbt - I0);
+      for (int o = 0; o < SR; ++o) {
+        C res[KCT];
+        if (o < ntr) {
+          const int op0 = __ldg(runs + 2 * o), cnt = __ldg(runs + 2 * o + 1);
+          run(cnt, y + op0 * 16 + lw, 16, npadh, res);
+        } else {
 #pragma unroll
-      for (int ii = 0; ii < SR; ++ii)
-#pragma unroll
-        for (int j = 0; j < KCT; ++j) {
-          C v = (C)0;
-#pragma unroll
-          for (int h = 0; h < NCH; ++h) v += acc[ii][j][h];
-          part[((w * SR + ii) * KCT + j) * T + lane] = ii < ntr ? v : (C)0;
+          for (int j = 0; j < KCT; ++j) res[j] = (C)0;
         }
+#pragma unroll
+        for (int j = 0; j < KCT; ++j) part[((w * SR + o) * KCT + j) * T + lane] = res[j];
+      }
       consumer_sync();
       reduce(part, [&](int ii, int j, int u, C tot) {
-        tw[(ii * LW + u) * KCT + j] = ii < ntr ? y[j * npad + (I0 + ii) * T + l0 + u] - tot : (C)0;
+        tw[(ii * KCT + j) * LW + u] = ii < ntr ? y[j * npadh + (I0 + ii) * 16 + lw + u] - tot : (C)0;
       });
-      C o[SR][KCT][DCH];
+      // forward: output block o = sum_{j<=o} X(o, j) t_j; backward: output block o = sum_{i>=o} X(i, o)^T t_i
+      for (int o = 0; o < SR; ++o) {
+        C res[KCT];
+        if (o < ntr) {
+          if (fwd) run(o + 1, tw, KCT * LW, LW, res);
+          else run(ntr - o, tw + o * KCT * LW, KCT * LW, LW, res);
+        } else {
 #pragma unroll
-      for (int ii = 0; ii < SR; ++ii)
-#pragma unroll
-        for (int j = 0; j < KCT; ++j)
-#pragma unroll
-          for (int h = 0; h < DCH; ++h) o[ii][j][h] = (C)0;
-#pragma unroll
-      for (int i = 0; i < SR; ++i) {
-        if (i >= ntr) break;
-#pragma unroll
-        for (int jj = 0; jj <= i; ++jj) {
-          const S* tile = acquire();
-          if (tile) {
-            C tv[LW];
-#pragma unroll
-            for (int u = 0; u < LW; ++u) tv[u] = cvt<S, C>(tile[u * T]);
-            // forward: X_(i,jj) times block jj into output block i; backward: X_(i,jj)^T times block i
-            // into output block jj
-            const int src = fwd ? jj : i;
-#pragma unroll
-            for (int j = 0; j < KCT; ++j) {
-              C& x = fwd ? o[i][j][jj % DCH] : o[jj][j][i % DCH];
-#pragma unroll
-              for (int u = 0; u < LW; ++u) x = fma(tv[u], tw[(src * LW + u) * KCT + j], x);
-            }
-          }
-          release();
+          for (int j = 0; j < KCT; ++j) res[j] = (C)0;
         }
+#pragma unroll
+        for (int j = 0; j < KCT; ++j) dpart[((w * SR + o) * KCT + j) * T + lane] = res[j];
       }
-#pragma unroll
-      for (int ii = 0; ii < SR; ++ii)
-#pragma unroll
-        for (int j = 0; j < KCT; ++j) {
-          C v = o[ii][j][0];
-#pragma unroll
-          for (int h = 1; h < DCH; ++h) v += o[ii][j][h];
-          dpart[((w * SR + ii) * KCT + j) * T + lane] = v;
-        }
       consumer_sync();
       reduce(dpart, [&](int ii, int j, int u, C tot) {
-        if (ii < ntr) y[j * npad + (I0 + ii) * T + l0 + u] = tot;
+        if (ii < ntr) y[j * npadh + (I0 + ii) * 16 + lw + u] = tot;
       });
     };
-    C acc[SR][KCT][NCH];
-    auto zero_acc = [&]() {
-#pragma unroll
-      for (int ii = 0; ii < SR; ++ii)
-#pragma unroll
-        for (int j = 0; j < KCT; ++j)
-#pragma unroll
-          for (int h = 0; h < NCH; ++h) acc[ii][j][h] = (C)0;
-    };
-    // one coupling tile: a[j][0] += sum_u tile line (l0+u) * v[j][l0+u], then the chains rotate so the
-    // next tile accumulates into the next chain (static register indices throughout)
-    auto couple = [&](const S* tile, const C* v, C (&a)[KCT][NCH]) {
-      C tv[LW];
-#pragma unroll
-      for (int u = 0; u < LW; ++u) tv[u] = cvt<S, C>(tile[u * T]);
-#pragma unroll
-      for (int j = 0; j < KCT; ++j) {
-        const C* vj = v + j * npad;
-        C x = a[j][0];
-#pragma unroll
-        for (int u = 0; u < LW; ++u) x = fma(tv[u], vj[u], x);
-#pragma unroll
-        for (int h = 0; h + 1 < NCH; ++h) a[j][h] = a[j][h + 1];
-        a[j][NCH - 1] = x;
-      }
-    };
-    // forward substitution, super-row by super-row
-    for (int q = 0; q < nsr; ++q) {
-      const int I0 = q * SR, ntr = min(SR, nbt - I0);
-      zero_acc();
-#pragma unroll
-      for (int ii = 0; ii < SR; ++ii) {
-        if (ii >= ntr) break;
-        for (int J = Fs[I0 + ii]; J < I0; ++J) {
-          const S* tile = acquire();
-          if (tile) couple(tile, y + J * T + l0, acc[ii]);
-          release();
-        }
-      }
-      finish_super(I0, ntr, acc, true);
-    }
-    // backward substitution with L^T, super-row by super-row from the last: the tile rows I after the
-    // super-row that couple to its columns, each with its tiles (I, J), J ascending
-    for (int q = nsr - 1; q >= 0; --q) {
-      const int I0 = q * SR, ntr = min(SR, nbt - I0), I1 = I0 + ntr;
-      const int Ilast = P.sr_ilast[P.sub_sr[s] + q];
-      zero_acc();
-      for (int I = I1; I <= Ilast; ++I) {
-        const int FI = Fs[I];
-        if (FI > I1 - 1) continue;
-        const int jstart = FI > I0 ? FI - I0 : 0;
-#pragma unroll
-        for (int jj = 0; jj < SR; ++jj) {
-          if (jj < jstart || jj >= ntr) continue;
-          const S* tile = acquire();
-          if (tile) couple(tile, y + I * T + l0, acc[jj]);
-          release();
-        }
-      }
-      finish_super(I0, ntr, acc, false);
-    }
+    start_pass(nfwd);
+    for (int q = 0; q < nsr; ++q) super_row(q, P.fwd_run + (size_t)(sr0 + q) * SR * 2, true);
+    start_pass(nbwd);
+    for (int q = nsr - 1; q >= 0; --q) super_row(q, P.bwd_run + (size_t)(sr0 + q) * SR * 2, false);
   }
   __syncthreads();
   // z_i = D^{-1/2} y on own entries, partial (r, z) of this CTA; rank 1 hands its sums to rank 0, which
@@ -485,7 +477,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       for (int j = 0; j < KCT; ++j) {
         if (!act[j]) continue;
         const long long o = (long long)(k0 + j) * P.ndof + d0 + i;
-        const double zv = sc * (double)y[j * npad + i];
+        const double zv = sc * (double)y[j * npadh + m];
         P.z[o] = zv;
         prz[j] = fma(P.r[o], zv, prz[j]);
       }
@@ -515,8 +507,7 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int*
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int npad = ((ndof_max + T - 1) / T) * T;
-  const int head = (int)sizeof(C) * (kct * npad + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 2 * SR * kct * 16) +
-                   4 * (npad / T + 4);
+  const int head = (int)sizeof(C) * (kct * npad / 2 + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 2 * SR * kct * 16);
   const int off = (head + 127) & ~127;
   const int budget = optin - 2048 - off;   // static shared memory and slack
   const int hb = (int)(HT * sizeof(S));

@@ -227,59 +227,62 @@ __global__ void __launch_bounds__(256) k_dinv(EnvDev E, const S* __restrict__ L,
   __shared__ C a[T][T + 1];
   __shared__ C b[T][T + 1];
   __shared__ C w[T][T + 1];
-  const int q = blockIdx.x;
+  const int q = blockIdx.x, j = blockIdx.y;   // super-row, tile column of its inverse block
   const int s = task[3 * q], I0 = task[3 * q + 1], ntr = task[3 * q + 2];
+  if (j >= ntr) return;
   const long long xb = dinv_ptr[q];
-  auto xt = [&](int i, int j) { return X + (xb + i * (i + 1) / 2 + j) * TT; };
+  auto xt = [&](int i, int jj) { return X + (xb + i * (i + 1) / 2 + jj) * TT; };
   const int tid = threadIdx.x, c = tid % T, r0 = tid / T;
-  for (int i = 0; i < ntr; ++i) {
-    const S* src = L + tile_index(E, s, I0 + i, I0 + i) * TT;
-    S* dst = xt(i, i);
+  {
+    // X_jj = inv(L_jj), which the diagonal factor tile already holds
+    const S* src = L + tile_index(E, s, I0 + j, I0 + j) * TT;
+    S* dst = xt(j, j);
     for (int t = tid; t < TT; t += blockDim.x) dst[t] = src[t];
   }
   __syncthreads();
-  for (int i = 1; i < ntr; ++i) {
+  // X_ij = -inv(L_ii) sum_{k=j}^{i-1} L_ik X_kj, i = j+1 .. ntr-1: column j depends only on itself
+  for (int i = j + 1; i < ntr; ++i) {
     const int Fi = E.trow_F[E.sub_trow[s] + I0 + i];
-    for (int j = 0; j < i; ++j) {
-      C acc[4] = {0, 0, 0, 0};
-      for (int kk = j; kk < i; ++kk) {
-        if (I0 + kk < Fi) continue;
-        const S* A = L + tile_index(E, s, I0 + i, I0 + kk) * TT;
-        const S* B = xt(kk, j);
-        for (int t = tid; t < TT; t += blockDim.x) {
-          a[t / T][t % T] = (C)A[t];
-          b[t / T][t % T] = (C)B[t];
-        }
-        __syncthreads();
-        for (int m = 0; m < T; ++m) {
-          const C bv = b[m][c];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] += a[r0 + 8 * u][m] * bv;
-        }
-        __syncthreads();
+    C acc[4] = {0, 0, 0, 0};
+    for (int kk = j; kk < i; ++kk) {
+      if (I0 + kk < Fi) continue;
+      const S* A = L + tile_index(E, s, I0 + i, I0 + kk) * TT;
+      const S* B = xt(kk, j);
+      for (int t = tid; t < TT; t += blockDim.x) {
+        a[t / T][t % T] = (C)A[t];
+        b[t / T][t % T] = (C)B[t];
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) w[r0 + 8 * u][c] = acc[u];
-      const S* D = xt(i, i);
-      for (int t = tid; t < TT; t += blockDim.x) a[t / T][t % T] = (C)D[t];
       __syncthreads();
-      S* dst = xt(i, j);
+      for (int m = 0; m < T; ++m) {
+        const C bv = b[m][c];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = r0 + 8 * u;
-        C v = (C)0;
-        for (int m = 0; m <= r; ++m) v += a[r][m] * w[m][c];
-        dst[r * T + c] = (S)(-v);
+        for (int u = 0; u < 4; ++u) acc[u] += a[r0 + 8 * u][m] * bv;
       }
       __syncthreads();
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[r0 + 8 * u][c] = acc[u];
+    const S* D = L + tile_index(E, s, I0 + i, I0 + i) * TT;
+    for (int t = tid; t < TT; t += blockDim.x) a[t / T][t % T] = (C)D[t];
+    __syncthreads();
+    S* dst = xt(i, j);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + 8 * u;
+      C v = (C)0;
+      for (int m = 0; m <= r; ++m) v += a[r][m] * w[m][c];
+      dst[r * T + c] = (S)(-v);
+    }
+    __syncthreads();
   }
 }
 
-// stream tile p = (src[p] >= 0 ? factor tile src[p] : inverse-block tile -src[p]-1), transposed if asked.
-// The stream is stored as two arrays of half tiles: lines 0-15 of every tile, then lines 16-31 (a line
-// is a row of the stored tile: a column of the factor tile when transposed), so that each CTA of a pair
-// reads its half of a run of tiles with one contiguous copy.
+// stream tile p = factor tile src[p] (src[p] >= 0), a zero tile (ZERO_TILE) or inverse-block tile
+// -src[p]-1, transposed if asked.  A line is a row of the stored tile (a column of the factor tile when
+// transposed).  The stream is stored as two arrays of half tiles, lines 0-15 of every tile then lines
+// 16-31, so that each CTA of a pair reads its half of a run of tiles with one contiguous copy; inside a
+// half tile, lines 2w and 2w+1 are interleaved ([8][32][2]: pair w, position k, line), so that the warp
+// that owns the pair reads both of its entries with one vector load.
 template <typename S>
 __global__ void k_stream_gather(const S* __restrict__ L, const S* __restrict__ X, const long long* __restrict__ src,
                                 S* __restrict__ dst, long long n, int transpose) {
@@ -287,11 +290,18 @@ __global__ void k_stream_gather(const S* __restrict__ L, const S* __restrict__ X
   __shared__ S buf[T][T + 1];
   for (long long p = blockIdx.x; p < n; p += gridDim.x) {
     const long long v = src[p];
-    const S* a = v >= 0 ? L + v * TT : X + (-v - 1) * TT;
-    for (int u = threadIdx.x; u < TT; u += blockDim.x) buf[u / T][u % T] = a[u];
+    if (v == ZERO_TILE) {
+      for (int u = threadIdx.x; u < TT; u += blockDim.x) buf[u / T][u % T] = (S)0;
+    } else {
+      const S* a = v >= 0 ? L + v * TT : X + (-v - 1) * TT;
+      for (int u = threadIdx.x; u < TT; u += blockDim.x) buf[u / T][u % T] = a[u];
+    }
     __syncthreads();
-    for (int u = threadIdx.x; u < TT; u += blockDim.x)
-      dst[(long long)(u / HT) * n * HT + p * HT + (u % HT)] = transpose ? buf[u % T][u / T] : buf[u / T][u % T];
+    for (int u = threadIdx.x; u < TT; u += blockDim.x) {
+      const int line = u / T, k = u % T;
+      const int h = line / 16, w = (line % 16) / 2, b = line % 2;
+      dst[(long long)h * n * HT + p * HT + (w * T + k) * 2 + b] = transpose ? buf[k][line] : buf[line][k];
+    }
     __syncthreads();
   }
 }
@@ -555,8 +565,9 @@ int launch_gather_tiles(int prec, const void* src, const long long* idx, void* d
 int launch_dinv(int prec, const EnvDev& E, const void* L, const int* task, const long long* dinv_ptr, void* X, int nsr,
                 void* st) {
   if (nsr <= 0) return 0;
-  if (prec == 0) k_dinv<double><<<nsr, 256, 0, (cudaStream_t)st>>>(E, (const double*)L, task, dinv_ptr, (double*)X);
-  else k_dinv<float><<<nsr, 256, 0, (cudaStream_t)st>>>(E, (const float*)L, task, dinv_ptr, (float*)X);
+  const dim3 grid(nsr, SUPER_ROW);
+  if (prec == 0) k_dinv<double><<<grid, 256, 0, (cudaStream_t)st>>>(E, (const double*)L, task, dinv_ptr, (double*)X);
+  else k_dinv<float><<<grid, 256, 0, (cudaStream_t)st>>>(E, (const float*)L, task, dinv_ptr, (float*)X);
   return (int)cudaGetLastError();
 }
 

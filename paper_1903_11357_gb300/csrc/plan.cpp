@@ -39,14 +39,16 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
     }
     sub_trow[s + 1] = sub_trow[s] + nbt;
   }
-  // super-rows, their inverse blocks and the two solve streams
+  // super-rows, their inverse blocks, the two solve streams and their runs
   sub_sr.assign(nsub + 1, 0);
   dinv_ptr.assign(1, 0);
   dinv_task.clear();
-  stream_ptr.assign(nsub + 1, 0);
+  fwd_ptr.assign(nsub + 1, 0);
+  bwd_ptr.assign(nsub + 1, 0);
   fwd_src.clear();
   bwd_src.clear();
-  sr_ilast.clear();
+  fwd_run.clear();
+  bwd_run.clear();
   fwd_src.reserve((size_t)ntiles + (size_t)ntiles / 2);
   bwd_src.reserve((size_t)ntiles + (size_t)ntiles / 2);
   for (int s = 0; s < nsub; ++s) {
@@ -54,7 +56,8 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
     const int nsr = (nbt + SR - 1) / SR;
     const int q0 = sub_sr[s];
     sub_sr[s + 1] = q0 + nsr;
-    sr_ilast.resize(q0 + nsr, 0);
+    fwd_run.resize((size_t)(q0 + nsr) * SR * 2, 0);
+    bwd_run.resize((size_t)(q0 + nsr) * SR * 2, 0);
     for (int q = 0; q < nsr; ++q) {
       const int I0 = q * SR, ntr = std::min(SR, nbt - I0);
       dinv_task.push_back(s);
@@ -62,24 +65,40 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col) {
       dinv_task.push_back(ntr);
       dinv_ptr.push_back(dinv_ptr.back() + ntr * (ntr + 1) / 2);
     }
+    // inverse-block tile (i, j), j <= i, of super-row q
+    auto xtile = [&](int q, int i, int j) { return -(dinv_ptr[q0 + q] + i * (i + 1) / 2 + j + 1); };
     for (int q = 0; q < nsr; ++q) {
       const int I0 = q * SR, ntr = std::min(SR, nbt - I0);
-      for (int I = I0; I < I0 + ntr; ++I)
-        for (int J = Fs[s][I]; J < I0; ++J) fwd_src.push_back(trow_ptr[tr0 + I] + (J - Fs[s][I]));
-      for (int t = 0; t < ntr * (ntr + 1) / 2; ++t) fwd_src.push_back(-(dinv_ptr[q0 + q] + t + 1));
+      for (int o = 0; o < ntr; ++o) {   // run o: tile row I0+o left of the super-row, J ascending
+        const int I = I0 + o, F = std::min(Fs[s][I], I0);
+        for (int J = F; J < I0; ++J) fwd_src.push_back(trow_ptr[tr0 + I] + (J - Fs[s][I]));
+        fwd_run[((size_t)(q0 + q) * SR + o) * 2] = F;
+        fwd_run[((size_t)(q0 + q) * SR + o) * 2 + 1] = I0 - F;
+      }
+      for (int o = 0; o < ntr; ++o)
+        for (int j = 0; j <= o; ++j) fwd_src.push_back(xtile(q, o, j));
     }
     for (int q = nsr - 1; q >= 0; --q) {
       const int I0 = q * SR, ntr = std::min(SR, nbt - I0), I1 = I0 + ntr;
-      int last = I1 - 1;   // last tile row coupled to this super-row's columns
-      for (int I = I1; I < nbt; ++I) {
-        if (Fs[s][I] > I1 - 1) continue;
-        last = I;
-        for (int J = std::max(Fs[s][I], I0); J < I1; ++J) bwd_src.push_back(trow_ptr[tr0 + I] + (J - Fs[s][I]));
+      for (int o = 0; o < ntr; ++o) {   // run o: column J = I0+o below the super-row, I ascending
+        const int J = I0 + o;
+        int first = -1, last = -1;
+        for (int I = I1; I < nbt; ++I)
+          if (Fs[s][I] <= J) {
+            if (first < 0) first = I;
+            last = I;
+          }
+        if (first >= 0)
+          for (int I = first; I <= last; ++I)
+            bwd_src.push_back(Fs[s][I] <= J ? trow_ptr[tr0 + I] + (J - Fs[s][I]) : ZERO_TILE);
+        bwd_run[((size_t)(q0 + q) * SR + o) * 2] = first >= 0 ? first : I1;
+        bwd_run[((size_t)(q0 + q) * SR + o) * 2 + 1] = first >= 0 ? last - first + 1 : 0;
       }
-      sr_ilast[q0 + q] = last;
-      for (int t = 0; t < ntr * (ntr + 1) / 2; ++t) bwd_src.push_back(-(dinv_ptr[q0 + q] + t + 1));
+      for (int o = 0; o < ntr; ++o)
+        for (int i = o; i < ntr; ++i) bwd_src.push_back(xtile(q, i, o));
     }
-    stream_ptr[s + 1] = (long long)fwd_src.size();
+    fwd_ptr[s + 1] = (long long)fwd_src.size();
+    bwd_ptr[s + 1] = (long long)bwd_src.size();
   }
   ndinv = dinv_ptr.back();
   diag_off.assign(max_nbt + 1, 0);

@@ -5,11 +5,12 @@
 #include <vector>
 
 #include "common.h"
+#include "engine.h"
 
 namespace dgasm {
 
 constexpr int TILE = 32;  // tile edge of the local Cholesky factors
-constexpr int SR = 4;     // tile rows per super-row of the triangular solves
+constexpr int SR = SUPER_ROW;   // tile rows per super-row of the triangular solves
 
 void rcb_parts(const MeshData& m, std::vector<int> elems, int k, std::vector<int>& part_of, int first_part);
 int compute_partition(const MeshData& m, int nsub, int ncoarse, std::vector<int>& sub, std::vector<int>* agg);
@@ -29,16 +30,20 @@ struct Envelope {
   std::vector<int> sub_sr;               // [nsub+1] first global super-row of each subdomain
   std::vector<long long> dinv_ptr;       // [nsr+1] first tile of each super-row's inverse block
   long long ndinv = 0;
-  // Streams in the order the sweeps consume them (equal lengths per subdomain):
-  //   forward, super-row q ascending: for its tile rows I, tiles (I, J) with F(I) <= J < first row of q;
-  //            then X_q;
-  //   backward, super-row q descending: for each tile row I after q (ascending, up to sr_ilast[q]),
-  //            the tiles (I, J) of the columns J of q with F(I) <= J, J ascending; then X_q.
-  // Entry >= 0 is a factor tile index, entry < 0 is -(inverse-block tile index + 1).
-  std::vector<long long> stream_ptr;     // [nsub+1]
+  // Streams in the order the sweeps consume them, made of runs: a run is a sequence of tiles that all
+  // add into one output block, with consecutive operand blocks.  Per super-row q, runs o = 0..ntr-1:
+  //   forward:  coupling run o = tiles (I0+o, J), J = F .. I0-1 (operand y_J), then
+  //             inverse run o = X_q tiles (o, j), j = 0..o (operand t_j);
+  //   backward (super-rows descending): coupling run o = tiles (I, I0+o), I = first .. last tile row
+  //             below the super-row with F(I) <= I0+o (operand x_I; a zero tile where a row in between
+  //             does not reach column I0+o), then inverse run o = X_q tiles (i, o), i = o..ntr-1.
+  // Entry >= 0 is a factor tile index, ZERO_TILE a tile of zeros, other entries < 0 are
+  // -(inverse-block tile index + 1).
+  std::vector<long long> fwd_ptr, bwd_ptr;   // [nsub+1] each subdomain's range in each stream
   std::vector<long long> fwd_src, bwd_src;
   std::vector<int> dinv_task;            // per super-row: (subdomain, first tile row, tile rows)
-  std::vector<int> sr_ilast;             // per super-row: last tile row coupled to its columns
+  // coupling runs: [global super-row][SR][2] = (first operand block, tiles)
+  std::vector<int> fwd_run, bwd_run;
   int max_nbt = 0;
   // Cholesky tasks, grouped by step K: diag (s, K), panel (s, I), update (s, I, J), I >= J
   std::vector<int> diag_off, panel_off, upd_off;  // [max_nbt + 1]

@@ -16,6 +16,7 @@ long long g_n[PK_NKINDS] = {0};
 }  // namespace
 
 bool profiling() { return g_on.load() != 0; }
+bool profiling(int kind) { return (g_on.load() >> kind) & 1; }
 
 void prof_add(int kind, double ms, long long launches) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -39,6 +40,7 @@ void EventPairs::reserve(size_t n) {
 }
 
 int EventPairs::begin(int k, cudaStream_t s) {
+  if (!profiling(k)) return -1;
   if (used == a.size()) {
     cudaEvent_t x, y;
     if (cudaEventCreate(&x) != cudaSuccess) return -1;
@@ -73,8 +75,8 @@ void EventPairs::accumulate() {
 
 }  // namespace dgasm
 
-extern "C" int dgasm_profile_enable(int on) {
-  dgasm::g_on.store(on ? 1 : 0);
+extern "C" int dgasm_profile_enable(int mask) {
+  dgasm::g_on.store(mask & ((1 << dgasm::PK_NKINDS) - 1));
   return DGASM_OK;
 }
 

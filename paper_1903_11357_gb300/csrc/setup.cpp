@@ -36,11 +36,13 @@ int upload_env(const Envelope& E, EnvBufs& D) {
   DG_TRY(upload(D.upd_task, E.upd_task));
   DG_TRY(upload(D.bwd_src, E.bwd_src));
   DG_TRY(upload(D.fwd_src, E.fwd_src));
-  DG_TRY(upload(D.stream_ptr, E.stream_ptr));
+  DG_TRY(upload(D.fwd_ptr, E.fwd_ptr));
+  DG_TRY(upload(D.bwd_ptr, E.bwd_ptr));
   DG_TRY(upload(D.dinv_task, E.dinv_task));
   DG_TRY(upload(D.dinv_ptr, E.dinv_ptr));
   DG_TRY(upload(D.sub_sr, E.sub_sr));
-  DG_TRY(upload(D.sr_ilast, E.sr_ilast));
+  DG_TRY(upload(D.fwd_run, E.fwd_run));
+  DG_TRY(upload(D.bwd_run, E.bwd_run));
   D.dev.nsub = E.nsub;
   D.dev.ndof = D.ndof.as<int>();
   D.dev.sub_trow = D.sub_trow.as<int>();
@@ -81,21 +83,21 @@ int build_streams(int fprec, const Envelope& E, EnvBufs& D, DevBuf& Lf, DevBuf& 
                   int* nl) {
   const int fp = fprec == DGASM_FP64 ? 0 : 1;
   const size_t eb = fact_elem_bytes(fprec);
-  const long long ns = (long long)E.fwd_src.size();
+  const long long nf = (long long)E.fwd_src.size(), nb = (long long)E.bwd_src.size();
   const int nsr = (int)E.dinv_ptr.size() - 1;
   DevBuf X, Sf, Sb;
   DG_TRY(X.alloc((size_t)std::max<long long>(E.ndinv, 1) * TILE * TILE * eb));
   DG_CUDA(launch_dinv(fp, D.dev, Lf.ptr, D.dinv_task.as<int>(), D.dinv_ptr.as<long long>(), X.ptr, nsr, st));
-  DG_TRY(Sf.alloc((size_t)ns * TILE * TILE * eb));
-  DG_TRY(Sb.alloc((size_t)ns * TILE * TILE * eb));
-  DG_CUDA(launch_stream_gather(fp, Lf.ptr, X.ptr, D.fwd_src.as<long long>(), Sf.ptr, ns, 1, st));
-  DG_CUDA(launch_stream_gather(fp, Lf.ptr, X.ptr, D.bwd_src.as<long long>(), Sb.ptr, ns, 0, st));
+  DG_TRY(Sf.alloc((size_t)nf * TILE * TILE * eb));
+  DG_TRY(Sb.alloc((size_t)nb * TILE * TILE * eb));
+  DG_CUDA(launch_stream_gather(fp, Lf.ptr, X.ptr, D.fwd_src.as<long long>(), Sf.ptr, nf, 1, st));
+  DG_CUDA(launch_stream_gather(fp, Lf.ptr, X.ptr, D.bwd_src.as<long long>(), Sb.ptr, nb, 0, st));
   *nl += 3;
   if (fprec == DGASM_BF16) {
-    DG_TRY(Lc.alloc((size_t)ns * TILE * TILE * 2));
-    DG_TRY(Lr.alloc((size_t)ns * TILE * TILE * 2));
-    DG_CUDA(launch_to_bf16(Sf.as<float>(), Lc.ptr, ns * TILE * TILE, st));
-    DG_CUDA(launch_to_bf16(Sb.as<float>(), Lr.ptr, ns * TILE * TILE, st));
+    DG_TRY(Lc.alloc((size_t)nf * TILE * TILE * 2));
+    DG_TRY(Lr.alloc((size_t)nb * TILE * TILE * 2));
+    DG_CUDA(launch_to_bf16(Sf.as<float>(), Lc.ptr, nf * TILE * TILE, st));
+    DG_CUDA(launch_to_bf16(Sb.as<float>(), Lr.ptr, nb * TILE * TILE, st));
     *nl += 2;
     DG_CUDA(cudaStreamSynchronize(st));
   } else {
@@ -142,9 +144,9 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
   const Plan& P = pc.P;
   const size_t ndof = (size_t)P.ne * P.np, t = (size_t)P.env.ntiles * TILE * TILE, n0 = pc.n0;
   size_t b = P.col.size() * (size_t)pc.sys->np2s * 8 + ndof * 8 + P.col.size() * 12 + (size_t)P.ne * 20;
-  const size_t ts = (size_t)P.env.fwd_src.size() * TILE * TILE, td = (size_t)P.env.ndinv * TILE * TILE;
-  b += (t + td) * (pc.precision == DGASM_FP64 ? 8 : 4) + ts * (pc.precision == DGASM_FP64 ? 16 : 8) +
-       P.env.fwd_src.size() * 16;
+  const size_t ns = P.env.fwd_src.size() + P.env.bwd_src.size();
+  const size_t ts = ns * TILE * TILE, td = (size_t)P.env.ndinv * TILE * TILE;
+  b += (t + td) * (pc.precision == DGASM_FP64 ? 8 : 4) + ts * (pc.precision == DGASM_FP64 ? 8 : 4) + ns * 8;
   b += (P.env.upd_task.size() + P.env.panel_task.size() + P.env.diag_task.size() + P.env.trow_F.size() * 3) * 4;
   if (n0) b += ndof * P.nq * 8 + n0 * n0 * 8 * 3 + (size_t)P.env0.ntiles * TILE * TILE * 16;
   const int epi = NTHREADS / P.np;
@@ -293,10 +295,12 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
   std::memset(&D, 0, sizeof(D));
   D.np = n0; D.ndof = n0; D.nsub = 1; D.k = n0; D.kc = KC; D.n_rhs_chunks = chunks; D.prec = DGASM_FP64;
   D.sub_e0 = sub_e0c.as<int>(); D.sub_trow = env0.sub_trow.as<int>(); D.trow_F = env0.trow_F.as<int>();
-  D.trow_ptr = env0.trow_ptr.as<long long>(); D.stream_ptr = env0.stream_ptr.as<long long>();
-  D.sub_sr = env0.sub_sr.as<int>(); D.sr_ilast = env0.sr_ilast.as<int>();
+  D.trow_ptr = env0.trow_ptr.as<long long>(); D.fwd_ptr = env0.fwd_ptr.as<long long>();
+  D.bwd_ptr = env0.bwd_ptr.as<long long>();
+  D.sub_sr = env0.sub_sr.as<int>(); D.fwd_run = env0.fwd_run.as<int>(); D.bwd_run = env0.bwd_run.as<int>();
   D.Lr = Lr0.ptr; D.Lc = Lc0.ptr; D.scale = scale0.as<double>();
-  D.stream_total = (long long)P.env0.fwd_src.size();
+  D.fwd_total = (long long)P.env0.fwd_src.size();
+  D.bwd_total = (long long)P.env0.bwd_src.size();
   D.r = ident.as<double>(); D.z = A0inv.as<double>();
   D.done = (int*)misc.ptr;
   D.part_rz = (double*)((char*)misc.ptr + rz_off);
@@ -327,8 +331,8 @@ size_t dgasm_prec_s::footprint() const {
   const EnvBufs* es[2] = {&env, &env0};
   for (const EnvBufs* e : es)
     b += e->ndof.bytes + e->sub_trow.bytes + e->trow_F.bytes + e->trow_ptr.bytes + e->diag_task.bytes +
-         e->panel_task.bytes + e->upd_task.bytes + e->bwd_src.bytes + e->fwd_src.bytes + e->stream_ptr.bytes +
-         e->dinv_task.bytes + e->dinv_ptr.bytes + e->sub_sr.bytes + e->sr_ilast.bytes;
+         e->panel_task.bytes + e->upd_task.bytes + e->bwd_src.bytes + e->fwd_src.bytes + e->fwd_ptr.bytes +
+         e->bwd_ptr.bytes + e->dinv_task.bytes + e->dinv_ptr.bytes + e->sub_sr.bytes + e->fwd_run.bytes + e->bwd_run.bytes;
   return b;
 }
 
@@ -355,7 +359,7 @@ extern "C" int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info) {
   info->precision = pc->precision;
   info->local_dofs = (int64_t)P.ne * P.np;
   info->local_tiles = P.env.ntiles;
-  info->stream_tiles = (int64_t)P.env.fwd_src.size();
+  info->stream_tiles = (int64_t)(P.env.fwd_src.size() + P.env.bwd_src.size());
   int64_t upd = (int64_t)P.env.upd_task.size() / 3, pan = (int64_t)P.env.panel_task.size() / 2, dg = (int64_t)P.env.diag_task.size();
   const int64_t t3 = (int64_t)TILE * TILE * TILE;
   info->factor_flops = upd * 2 * t3 + pan * t3 + dg * (t3 / 3 + t3 / 3);

@@ -327,8 +327,18 @@ def lanczos(alphas, betas):
 PROFILE_KINDS = ["spmv", "update", "local", "coarse", "pupdate", "chol_diag", "chol_panel", "chol_update"]
 
 
-def profile_enable(on=True):
-    check(lib().dgasm_profile_enable(1 if on else 0))
+def profile_enable(on=True, kinds=None):
+    """Time kernel launches with CUDA events: every kind (on=True), none (on=False), or only the
+    named kinds (kinds: iterable of names from PROFILE_KINDS)."""
+    if not on:
+        mask = 0
+    elif kinds is None:
+        mask = 0xFF
+    else:
+        mask = 0
+        for k in kinds:
+            mask |= 1 << PROFILE_KINDS.index(k)
+    check(lib().dgasm_profile_enable(mask))
 
 
 def profile_read(reset=False):
