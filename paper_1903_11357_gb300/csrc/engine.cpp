@@ -63,6 +63,7 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.sub_e0 = pc.sub_e0.as<int>(); D.sub_trow = pc.env.sub_trow.as<int>(); D.trow_F = pc.env.trow_F.as<int>();
   D.trow_ptr = pc.env.trow_ptr.as<long long>(); D.fwd_ptr = pc.env.fwd_ptr.as<long long>();
   D.bwd_ptr = pc.env.bwd_ptr.as<long long>();
+  D.sr = pc.P.env.sr;
   D.sub_sr = pc.env.sub_sr.as<int>(); D.fwd_run = pc.env.fwd_run.as<int>(); D.bwd_run = pc.env.bwd_run.as<int>();
   D.Lr = pc.Lr.ptr; D.Lc = pc.Lc.ptr; D.scale = pc.scale.as<double>();
   D.fwd_total = (long long)pc.P.env.fwd_src.size();

@@ -11,7 +11,11 @@ namespace dgasm {
 constexpr int NTHREADS = 256;  // threads per CTA of the vector kernels
 constexpr int KMAX = 8;        // right-hand sides per problem
 constexpr int KC = 4;          // right-hand sides per local-solve CTA
-constexpr int SUPER_ROW = 8;   // tile rows per super-row of the local triangular solves
+constexpr int SUPER_ROW_MAX = 8;   // tile rows per super-row of the local triangular solves, at most
+// Super-row size by precision of the local factors.  Larger blocks trade more inverse-block tiles for
+// fewer sequential reductions; on the 16384-cell p=3 workload 8 beat 4 for FP64 (328 vs 354 us per local
+// solve) and FP32 (139 vs 158 us), and 16 gained FP32 only 3%.
+constexpr int super_row(int /*prec*/) { return 8; }
 constexpr long long ZERO_TILE = -(1LL << 62);   // solve-stream entry: a tile of zeros
 
 enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
@@ -42,8 +46,9 @@ struct ProbDev {
   const long long* fwd_ptr;     // [nsub+1] each subdomain's range in the forward stream
   const long long* bwd_ptr;     // [nsub+1] and in the backward stream
   long long fwd_total, bwd_total;  // tiles in each stream (all subdomains)
+  int sr;                       // tile rows per super-row of the local factors
   const int* sub_sr;            // [nsub+1] first global super-row of each subdomain
-  const int* fwd_run;           // [global super-row][SUPER_ROW][2]: coupling runs (first operand block, tiles)
+  const int* fwd_run;           // [global super-row][sr][2]: coupling runs (first operand block, tiles)
   const int* bwd_run;
   const void* Lr;     // backward stream: row-major tiles in consumption order, as [2][bwd_total][16 x 32]
   const void* Lc;     // forward stream: column-major tiles in consumption order, as [2][fwd_total][16 x 32]

@@ -2,7 +2,8 @@
 // Cholesky factor A~_i = L L^T (A~_i = D^{-1/2} A_i D^{-1/2}): forward substitution with L, backward
 // substitution with L^T.
 //
-// The rows are processed in super-rows of SR = 8 tile rows (256 rows).  The setup stores, in the order the
+// The rows are processed in super-rows of SR = 8 tile rows (256 rows; the size is a per-precision choice
+// of the plan and of this kernel).  The setup stores, in the order the
 // sweeps consume them, the factor tiles that couple different super-rows and the explicit inverse X_q of
 // each super-row's lower-triangular diagonal block, so a super-row costs tile GEMVs, one reduction, a
 // product with X_q (or X_q^T) and one more reduction:
@@ -21,7 +22,7 @@
 // interleaved, one vector load per tile; lane = the other tile index), so the FP64 work is spread evenly
 // over both SMs' sub-partitions and a warp only ever needs its own entries of each solution block.
 //
-// Reductions.  The warps' partial sums of a block entry are added in a fixed tree inside each CTA; the
+// Reductions.  The warps' partial sums of a block entry are added in a fixed order inside each CTA; the
 // entries the peer owns are sent to it with st.async, which counts its bytes on the peer's exchange
 // mbarrier, and each entry's total is (rank 0 sum) + (rank 1 sum).  The result therefore does not depend
 // on timing, on the batch a subdomain is launched in or on which SMs run it.  Every wait is bounded; on
@@ -43,7 +44,6 @@ namespace {
 constexpr int T = 32;
 constexpr int TT = T * T;
 constexpr int HT = TT / 2;             // half tile: 16 lines of 32
-constexpr int SR = SUPER_ROW;          // tile rows per super-row (the plan's)
 constexpr int NCW = 8;                 // consumer warps
 constexpr int NCT = NCW * 32;          // consumer threads
 constexpr int NTH = NCT + 32;          // + producer warp
@@ -202,25 +202,14 @@ __device__ __forceinline__ void ld_pair(const __nv_bfloat162* p, C& a, C& b) {
 __device__ __forceinline__ double2 ld_pair2(const double* p) { return *reinterpret_cast<const double2*>(p); }
 __device__ __forceinline__ float2 ld_pair2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
-// Sum over the eight warps' partials of entry (ii, j, c) of `buf` ([NCW][SR][KCT][T]) by the four lanes
-// q = 0..3 of a lane quad: lane q adds warps 2q and 2q+1, then two butterfly steps; every lane of the quad
-// ends with the same value, (w0+w1)+(w2+w3) + (w4+w5)+(w6+w7).
-template <typename C, int KCT>
-__device__ __forceinline__ C quad_sum(const C* buf, int ii, int j, int c, int q) {
-  const C* b = buf + ((2 * q * SR + ii) * KCT + j) * T + c;
-  C v = b[0] + b[SR * KCT * T];
-  v += shfl_xor_c(v, 1);
-  v += shfl_xor_c(v, 2);
-  return v;
-}
-
 template <typename S, typename C, int KCT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     k_local(BatchDev B, int slot, int ring_off, int nstage, int ch) {
   using VS = typename Pair<S>::V;
+  constexpr int SR = 8;                   // tile rows per super-row: super_row() of every precision
   constexpr int NX = SR * 16 * KCT;       // entries exchanged per reduction (each direction)
-  constexpr int NRP = NX / (NCT / 4);     // rounds of the peer's sums, a lane quad per entry
-  constexpr int NRO = SR * LW * KCT / 8;  // rounds of a warp's own entries, eight quads per round
+  constexpr int NE = SR * KCT * T;        // entries summed per reduction in each CTA
+  constexpr bool TWO = sizeof(C) == 4;    // two accumulation chains (FP32: cover the FMA latency)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[NCW + 1][KCT];
   __shared__ double peer_rz[KCT];
@@ -243,6 +232,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     any |= act[j];
   }
   if (!any) return;   // both CTAs of the pair read the same flags and leave together
+  if (P.sr != SR) {   // the plan was built for another super-row size: refuse
+    if (threadIdx.x == 0) atomicExch(B.err, 2);
+    return;
+  }
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int e0 = P.sub_e0[s];
   const int n = (P.sub_e0[s + 1] - e0) * P.np;
@@ -257,6 +250,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   C* dpart = part + NCW * SR * KCT * T;                // [NCW][SR][KCT][T]
   C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR][KCT][LW]
   C* xbuf = tvs + NCW * SR * KCT * LW;                 // [2][SR][KCT][16]: the peer's sums of own entries
+  C* cpart = xbuf + 2 * NX;                            // [SR][KCT][16]: this CTA's sums of own entries
   S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][ch][HT]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * ch * HT);
   unsigned long long* empty = full + nstage;
@@ -349,10 +343,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
           for (int j = 0; j < KCT; ++j) {
             const auto o0 = ld_pair2(vp + t * vstride + j * jstride);
             const auto o1 = ld_pair2(vp + (t + 1) * vstride + j * jstride);
+            C& b = TWO ? a1[j] : a0[j];
             a0[j] = fma(x0, o0.x, a0[j]);
-            a1[j] = fma(z0, o1.x, a1[j]);
+            b = fma(z0, o1.x, b);
             a0[j] = fma(x1, o0.y, a0[j]);
-            a1[j] = fma(z1, o1.y, a1[j]);
+            b = fma(z1, o1.y, b);
           }
         }
         if (t < m) {
@@ -377,16 +372,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
         }
       }
 #pragma unroll
-      for (int j = 0; j < KCT; ++j) res[j] = a0[j] + a1[j];
+      for (int j = 0; j < KCT; ++j) res[j] = TWO ? a0[j] + a1[j] : a0[j];
     };
-    // Reduction number xcount of the partials in buf (written, followed by consumer_sync): send the sums
-    // of the peer's entries, sum this warp's own entries, wait for the peer's sums, and hand each own
-    // entry's total to use(ii, j, u, total) on the first lane of its quad.  Reductions alternate between
-    // two exchange buffers and barriers; the peer cannot send reduction m + 2 before it has received
-    // reduction m + 1, which this CTA sends only after it has read the buffer of reduction m, and thread 0
-    // arms a barrier for reduction m + 2 only after the wait of reduction m.
+    // Reduction number xcount of the partials in buf (written, followed by consumer_sync).  Thread t sums
+    // the eight warps' partials of entries t, t + 256, ... in warp order; the sums of the peer's entries go
+    // to the peer (st.async), those of own entries to cpart.  After a consumer_sync and the peer's signal
+    // each warp forms (rank 0 sum) + (rank 1 sum) of its own entries and hands it to use(ii, j, u, total).
+    // Reductions alternate between two exchange buffers and barriers; the peer cannot send reduction m + 2
+    // before it has received reduction m + 1, which this CTA sends only after every warp has read the
+    // buffer of reduction m, and thread 0 arms a barrier for reduction m + 2 only after waiting on m.
     unsigned xcount = 0;
-    const int q4 = lane & 3;
     C* tw = tvs + w * SR * KCT * LW;   // this warp's own entries of t (the block product's input)
     auto reduce = [&](const C* buf, auto&& use) {
       const unsigned xb = xcount & 1u, xph = (xcount >> 1) & 1u;
@@ -394,34 +389,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       if (tid == 0 && !xdead) mbar_expect_tx(&xbar[xb], (unsigned)(NX * sizeof(C)));
       const unsigned pbar = mapa(&xbar[xb], peer);
       const unsigned pbuf = mapa(xbuf + xb * NX, peer);
+      for (int e = tid; e < NE; e += NCT) {
+        const int c = e % T, j = (e / T) % KCT, ii = e / (T * KCT);
+        const C* b = buf + (ii * KCT + j) * T + c;
+        C v = b[0];
 #pragma unroll
-      for (int rr = 0; rr < NRP; ++rr) {
-        const int e = rr * (NCT / 4) + (tid >> 2);
-        const int ii = e / (16 * KCT), j = (e / 16) % KCT, cl = e % 16;
-        const C v = quad_sum<C, KCT>(buf, ii, j, 16 * (int)peer + cl, q4);
-        if (q4 == 0) st_async(pbuf + (unsigned)(((ii * KCT + j) * 16 + cl) * sizeof(C)), v, pbar);
+        for (int ww = 1; ww < NCW; ++ww) v += b[ww * SR * KCT * T];
+        const int slot16 = (ii * KCT + j) * 16 + (c & 15);
+        if ((c >> 4) == (int)rank) cpart[slot16] = v;
+        else st_async(pbuf + (unsigned)(slot16 * sizeof(C)), v, pbar);
       }
-      C mine[NRO];
-#pragma unroll
-      for (int rr = 0; rr < NRO; ++rr) {
-        const int e = rr * 8 + (lane >> 2);
-        const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
-        mine[rr] = quad_sum<C, KCT>(buf, ii, j, l0 + u, q4);
-      }
+      consumer_sync();
       xbar_wait(&xbar[xb], xph, &abort_flag, &xdead, B.err);
-      if (q4 == 0) {
-#pragma unroll
-        for (int rr = 0; rr < NRO; ++rr) {
-          const int e = rr * 8 + (lane >> 2);
-          const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
-          use(ii, j, u, mine[rr] + xbuf[xb * NX + (ii * KCT + j) * 16 + lw + u]);
-        }
+      for (int e = lane; e < SR * LW * KCT; e += 32) {
+        const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
+        const int slot16 = (ii * KCT + j) * 16 + lw + u;
+        use(ii, j, u, cpart[slot16] + xbuf[xb * NX + slot16]);
       }
       __syncwarp();
     };
     // One super-row of a sweep: coupling runs, reduction to t = y_q - sum, block-inverse runs on t,
     // reduction to the new y_q.  runs: the plan's (first operand block, tiles) per output block.
-    auto super_row = [&](int q, const int* runs, bool fwd) {
+    auto sweep_step = [&](int q, const int* runs, bool fwd) {
       const int I0 = q * SR, ntr = min(SR, nbt - I0);
       for (int o = 0; o < SR; ++o) {
         C res[KCT];
@@ -458,9 +447,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       });
     };
     start_pass(nfwd);
-    for (int q = 0; q < nsr; ++q) super_row(q, P.fwd_run + (size_t)(sr0 + q) * SR * 2, true);
+    for (int q = 0; q < nsr; ++q) sweep_step(q, P.fwd_run + (size_t)(sr0 + q) * SR * 2, true);
     start_pass(nbwd);
-    for (int q = nsr - 1; q >= 0; --q) super_row(q, P.bwd_run + (size_t)(sr0 + q) * SR * 2, false);
+    for (int q = nsr - 1; q >= 0; --q) sweep_step(q, P.bwd_run + (size_t)(sr0 + q) * SR * 2, false);
   }
   __syncthreads();
   // z_i = D^{-1/2} y on own entries, partial (r, z) of this CTA; rank 1 hands its sums to rank 0, which
@@ -506,8 +495,9 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int*
   cudaGetDevice(&dev);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  constexpr int SR = 8;
   const int npad = ((ndof_max + T - 1) / T) * T;
-  const int head = (int)sizeof(C) * (kct * npad / 2 + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 2 * SR * kct * 16);
+  const int head = (int)sizeof(C) * (kct * npad / 2 + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 3 * SR * kct * 16);
   const int off = (head + 127) & ~127;
   const int budget = optin - 2048 - off;   // static shared memory and slack
   const int hb = (int)(HT * sizeof(S));

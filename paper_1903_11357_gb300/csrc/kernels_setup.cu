@@ -565,7 +565,7 @@ int launch_gather_tiles(int prec, const void* src, const long long* idx, void* d
 int launch_dinv(int prec, const EnvDev& E, const void* L, const int* task, const long long* dinv_ptr, void* X, int nsr,
                 void* st) {
   if (nsr <= 0) return 0;
-  const dim3 grid(nsr, SUPER_ROW);
+  const dim3 grid(nsr, SUPER_ROW_MAX);
   if (prec == 0) k_dinv<double><<<grid, 256, 0, (cudaStream_t)st>>>(E, (const double*)L, task, dinv_ptr, (double*)X);
   else k_dinv<float><<<grid, 256, 0, (cudaStream_t)st>>>(E, (const float*)L, task, dinv_ptr, (float*)X);
   return (int)cudaGetLastError();

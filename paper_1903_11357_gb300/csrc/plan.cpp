@@ -14,7 +14,9 @@
 
 namespace dgasm {
 
-void Envelope::build(const std::vector<std::vector<int>>& first_col) {
+void Envelope::build(const std::vector<std::vector<int>>& first_col, int sr_) {
+  sr = sr_;
+  const int SR = sr;
   nsub = (int)first_col.size();
   ndof.resize(nsub);
   sub_trow.assign(nsub + 1, 0);
@@ -194,7 +196,8 @@ std::vector<int> rcm_order(const std::vector<int>& elems, const std::vector<int>
 
 }  // namespace
 
-int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const int* sub_in, const int* agg_in, Plan& P) {
+int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const int* sub_in, const int* agg_in, int sr,
+               Plan& P) {
   const MeshData& m = sys.mesh->m;
   const int ne = m.ne, np = sys.np;
   P.ne = ne;
@@ -306,7 +309,7 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
       for (int a = 0; a < np; ++a) fc[s][(size_t)(i - e0) * np + a] = first * np;
     }
   }
-  P.env.build(fc);
+  P.env.build(fc, sr);
   // groups and coarse data
   P.agg_int.assign(ne, -1);
   P.grp_ptr.assign(1, 0);
@@ -334,7 +337,7 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
     }
     int n0 = P.nagg * P.nq;
     std::vector<std::vector<int>> fc0(1, std::vector<int>(n0, 0));
-    P.env0.build(fc0);
+    P.env0.build(fc0, super_row(DGASM_FP64));
   } else {
     const int G = 64;
     for (int i = 0; i < ne; i += G) {

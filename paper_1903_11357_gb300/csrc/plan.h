@@ -10,7 +10,6 @@
 namespace dgasm {
 
 constexpr int TILE = 32;  // tile edge of the local Cholesky factors
-constexpr int SR = SUPER_ROW;   // tile rows per super-row of the triangular solves
 
 void rcb_parts(const MeshData& m, std::vector<int> elems, int k, std::vector<int>& part_of, int first_part);
 int compute_partition(const MeshData& m, int nsub, int ncoarse, std::vector<int>& sub, std::vector<int>* agg);
@@ -24,8 +23,8 @@ struct Envelope {
   std::vector<int> trow_F;             // first tile column of each tile row
   std::vector<long long> trow_ptr;     // tile index of the first tile of each tile row
   long long ntiles = 0;
-  // Super-rows: groups of SR consecutive tile rows.  The triangular solves use, per super-row q, the
-  // explicit inverse X_q of its lower-triangular diagonal block (ntr(ntr+1)/2 tiles, ntr <= SR, row-major
+  // Super-rows: groups of sr consecutive tile rows.  The triangular solves use, per super-row q, the
+  // explicit inverse X_q of its lower-triangular diagonal block (ntr(ntr+1)/2 tiles, ntr <= sr, row-major
   // tile order (i, j), j <= i), and the factor tiles that couple different super-rows.
   std::vector<int> sub_sr;               // [nsub+1] first global super-row of each subdomain
   std::vector<long long> dinv_ptr;       // [nsr+1] first tile of each super-row's inverse block
@@ -42,7 +41,7 @@ struct Envelope {
   std::vector<long long> fwd_ptr, bwd_ptr;   // [nsub+1] each subdomain's range in each stream
   std::vector<long long> fwd_src, bwd_src;
   std::vector<int> dinv_task;            // per super-row: (subdomain, first tile row, tile rows)
-  // coupling runs: [global super-row][SR][2] = (first operand block, tiles)
+  // coupling runs: [global super-row][sr][2] = (first operand block, tiles)
   std::vector<int> fwd_run, bwd_run;
   int max_nbt = 0;
   // Cholesky tasks, grouped by step K: diag (s, K), panel (s, I), update (s, I, J), I >= J
@@ -50,8 +49,9 @@ struct Envelope {
   std::vector<int> diag_task;   // s
   std::vector<int> panel_task;  // pairs (s, I)
   std::vector<int> upd_task;    // triples (s, I, J)
-  // build from the first-column function of each subdomain's dof rows
-  void build(const std::vector<std::vector<int>>& first_col);
+  int sr = 4;                            // tile rows per super-row
+  // build from the first-column function of each subdomain's dof rows, with super-rows of sr_ tile rows
+  void build(const std::vector<std::vector<int>>& first_col, int sr_);
 };
 
 struct Plan {
@@ -71,6 +71,8 @@ struct Plan {
   Envelope env0;                     // coarse factor (one dense block)
 };
 
-int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const int* sub_in, const int* agg_in, Plan& P);
+// sr: tile rows per super-row of the local factors (the coarse factor takes super_row(DGASM_FP64))
+int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const int* sub_in, const int* agg_in, int sr,
+               Plan& P);
 
 }  // namespace dgasm

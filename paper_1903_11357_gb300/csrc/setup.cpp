@@ -132,7 +132,8 @@ int prec_plan(dgasm_system_s* s, const dgasm_setup_opts* o, std::unique_ptr<dgas
   DG_TRY(s->ensure_device());
   DG_TRY(pc->init_streams(o->stream));
   Plan& P = pc->P;
-  DG_TRY(build_plan(*s, o->nsub, o->ncoarse, coarse ? o->p_c : 1, o->sub_of_elem, o->agg_of_elem, P));
+  DG_TRY(build_plan(*s, o->nsub, o->ncoarse, coarse ? o->p_c : 1, o->sub_of_elem, o->agg_of_elem,
+                    super_row(o->precision), P));
   pc->n0 = P.nagg * P.nq;
   pc->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return DGASM_OK;
@@ -297,6 +298,7 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
   D.sub_e0 = sub_e0c.as<int>(); D.sub_trow = env0.sub_trow.as<int>(); D.trow_F = env0.trow_F.as<int>();
   D.trow_ptr = env0.trow_ptr.as<long long>(); D.fwd_ptr = env0.fwd_ptr.as<long long>();
   D.bwd_ptr = env0.bwd_ptr.as<long long>();
+  D.sr = P.env0.sr;
   D.sub_sr = env0.sub_sr.as<int>(); D.fwd_run = env0.fwd_run.as<int>(); D.bwd_run = env0.bwd_run.as<int>();
   D.Lr = Lr0.ptr; D.Lc = Lc0.ptr; D.scale = scale0.as<double>();
   D.fwd_total = (long long)P.env0.fwd_src.size();
