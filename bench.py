@@ -185,6 +185,226 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def _systems(specs, meshes, dg, torch, rhs_seed_offset=1):
+    """Systems of a problem mix: one coefficient per subdomain, log-uniform in [1, 1e3]; N(0,1) rhs."""
+    from synth.coeff import loguniform_per_subdomain
+    out = []
+    for s, m in zip(specs, meshes):
+        sub, _ = dg.Mesh.from_polymesh(m, np.ones(m.n_elem)).partition(s["nsub"], 0)
+        rho = loguniform_per_subdomain(sub, np.random.default_rng(s["coef_seed"]))
+        S = dg.System(dg.Mesh.from_polymesh(m, rho), s["p"], 10.0)
+        b = torch.tensor(np.random.default_rng(s["coef_seed"] + rhs_seed_offset).standard_normal(S.ndof),
+                         dtype=torch.float64, device="cuda")
+        out.append((s, S, b))
+    return out
+
+
+def run_batch(args):
+    """48 independent problems (element counts log-uniform in 1024..16384, p in 1..4, N/256 subdomains,
+    N/64 agglomerates at p_c=1): setup of all 48 preconditioners with FP32 local factors and one batched
+    solve of all of them (FP64 outer PCG, one launch per kernel kind and iteration for the whole batch,
+    CUDA graphs), against the plain FP64 library mode, one problem at a time."""
+    from synth.workloads import build_meshes, problem_specs
+    specs = problem_specs(48, 4)
+    meshes = build_meshes(specs)
+    import torch
+    from paper_1903_11357_gb300 import dgasm as dg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    probs = _systems(specs, meshes, dg, torch)
+    nrhs = len(probs)
+
+    def batched(precision):
+        precs = [dg.Prec(S, s["nsub"], s["ncoarse"], 1, precision=precision, stream=stream) for s, S, _ in probs]
+        xs = [torch.zeros_like(b) for _, _, b in probs]
+        rc, sts = dg.solve_batch(precs, [b for _, _, b in probs], xs, rtol=1e-8, stream=stream)
+        assert rc == 0, rc
+        return precs, xs, sts
+
+    def plain():
+        xs, sts = [], []
+        for s, S, b in probs:
+            P = dg.Prec(S, s["nsub"], s["ncoarse"], 1, precision="fp64", stream=stream)
+            x = torch.zeros_like(b)
+            rc, st = P.solve(b, x, rtol=1e-8, stream=stream)
+            assert rc == 0, rc
+            xs.append(x)
+            sts.append(st[0])
+        return xs, sts
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = None
+        e0.record(stream)
+        for _ in range(steps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0 / steps, out
+
+    sampler = ClockSampler(0)
+    t_mix, (_, x_mix, st_mix) = timed(lambda: batched("fp32"), args.steps, args.warmup)
+    clocks = sampler.stop()
+    t_bf, (_, x_bf, st_bf) = timed(lambda: batched("bf16"), args.steps, 1)
+    t_b64, (_, x_b64, st_b64) = timed(lambda: batched("fp64"), args.steps, 1)
+    t_plain, (x_64, st_64) = timed(plain, args.steps, 1)
+    rel = lambda xa: max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(xa, x_64))
+    it = lambda sts: [int(s["iters"]) for s in sts]
+    out = {
+        "metric": METRIC, "value": nrhs / t_mix, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_mix, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 outer / f32 local", "data": "synthetic",
+        "config": {"workload": "batch of 48 problems: Voronoi meshes (rng 4) with 1024..16384 cells log-uniform, "
+                               "p in {1..4}, N/256 RCB subdomains, N/64 agglomerates at p_c=1, rho per subdomain "
+                               "log-uniform in [1,1e3], rhs N(0,1) per dof, rtol 1e-8",
+                   "total_dofs": int(sum(S.ndof for _, S, _ in probs)),
+                   "step": "setup of 48 preconditioners + one batched solve of all 48"},
+        "fp64_plain": {"solves_per_s": nrhs / t_plain, "ms_per_step": 1000.0 * t_plain,
+                       "what": "FP64 local factors, one problem at a time (setup + solve each)"},
+        "fp64_batched": {"solves_per_s": nrhs / t_b64, "ms_per_step": 1000.0 * t_b64},
+        "bf16_batched": {"solves_per_s": nrhs / t_bf, "ms_per_step": 1000.0 * t_bf,
+                         "max_rel_diff_vs_fp64": rel(x_bf), "iters_sum": sum(it(st_bf))},
+        "speedup_mixed_batched_vs_fp64_plain": t_plain / t_mix,
+        "max_rel_diff_mixed_vs_fp64": rel(x_mix),
+        "max_true_relres_mixed": max(float(s["true_relres"]) for s in st_mix),
+        "iters_sum": {"fp32": sum(it(st_mix)), "fp64": sum(it(st_64))},
+        "iters_fp32_minus_fp64_max": max(a - c for a, c in zip(it(st_mix), it(st_64))),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals of solve requests (problem drawn from a pool of 16 problems shaped like the batch
+    mix, 1..8 N(0,1) right-hand sides each) into the continuous-batching server; latency from arrival to
+    completion, p50 / p99, and right-hand sides completed per second, per arrival rate and precision."""
+    from synth.workloads import build_meshes, problem_specs
+    specs = problem_specs(16, 5)
+    meshes = build_meshes(specs)
+    import torch
+    from paper_1903_11357_gb300 import dgasm as dg
+    torch.cuda.set_device(0)
+    pool = _systems(specs, meshes, dg, torch)
+    rng = np.random.default_rng(5)
+    n_req = max(16, args.requests)
+
+    def make_request():
+        s, S, _ = pool[int(rng.integers(len(pool)))]
+        k = int(rng.integers(1, 9))
+        b = torch.tensor(rng.standard_normal((k, S.ndof)), dtype=torch.float64, device="cuda")
+        return s, S, b, k
+
+    def run(precision, arrivals):
+        srv = dg.Server(hbm_budget=96 << 30, max_slots=24)
+        reqs = [make_request() for _ in arrivals]
+        t0 = time.perf_counter()
+        pending, lat, rhs_done = {}, [], 0
+        i = 0
+        t_last = t0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrivals[i] <= now:
+                s, S, b, k = reqs[i]
+                x = torch.zeros_like(b)
+                t = srv.submit(S, s["nsub"], s["ncoarse"], 1, b if k > 1 else b[0], x if k > 1 else x[0],
+                               precision=precision)
+                pending[t] = (arrivals[i], k, x)
+                i += 1
+            for t in list(pending):
+                rc, st = srv.poll(t)
+                if rc == 1:
+                    continue
+                a, k, _ = pending.pop(t)
+                assert rc == 0, rc
+                t_done = time.perf_counter() - t0
+                lat.append(t_done - a)
+                rhs_done += k
+                t_last = t_done
+            time.sleep(0.0005)
+        stats = srv.stats()
+        srv.close()
+        lat.sort()
+        return {"requests": len(lat), "rhs": rhs_done, "rhs_per_s": rhs_done / max(t_last - arrivals[0], 1e-9),
+                "p50_ms": 1000 * lat[len(lat) // 2], "p99_ms": 1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "mean_ms": 1000 * sum(lat) / len(lat), "rounds": stats["rounds"], "stalls": stats["stalls"]}
+
+    sampler = ClockSampler(0)
+    res = {}
+    for precision in ("fp32", "fp64"):
+        run(precision, [0.0] * 4)   # warm-up
+        sat = run(precision, [0.0] * n_req)   # everything at once: saturation throughput
+        rows = {"saturation_closed_batch": sat}
+        for frac in (0.5, 0.9):
+            lam = frac * sat["rhs_per_s"] / 4.5   # requests/s: 4.5 right-hand sides per request on average
+            gaps = np.random.default_rng(int(frac * 100)).exponential(1.0 / lam, size=n_req)
+            arrivals = list(np.cumsum(gaps) - gaps[0])
+            rows[f"poisson_{frac:.1f}x_saturation"] = dict(run(precision, arrivals), rate_req_per_s=lam)
+        res[precision] = rows
+    clocks = sampler.stop()
+    mixed = res["fp32"]["poisson_0.9x_saturation"]
+    out = {
+        "metric": METRIC, "value": res["fp32"]["saturation_closed_batch"]["rhs_per_s"], "unit": "solves/s",
+        "n_gpus": 1, "steps": n_req, "warmup": 4, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 outer / f32 local (fp64 row: all f64)", "data": "synthetic",
+        "config": {"workload": "serving: pool of 16 problems (rng 5) shaped like the batch mix, 1..8 N(0,1) rhs per "
+                               "request, Poisson arrivals at 0.5x and 0.9x the saturation rate, budget 96 GiB, 24 slots",
+                   "requests_per_rate": n_req},
+        "p50_ms_mixed_0.9x": mixed["p50_ms"], "p99_ms_mixed_0.9x": mixed["p99_ms"],
+        "saturation_speedup_mixed_vs_fp64": res["fp32"]["saturation_closed_batch"]["rhs_per_s"] /
+                                            res["fp64"]["saturation_closed_batch"]["rhs_per_s"],
+        "results": res, "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_sweep(args):
+    """Precision / contrast sweep: the 16384-cell mesh at p = 4 (245760 dofs, 64 subdomains, 256
+    agglomerates), checkerboard contrast 1, 1e2, 1e4, 1e6; local factors in FP64, FP32, TF32, BF16 (FP64
+    outer PCG, residual and coarse solve).  Per case: iterations, true relative residual, relative
+    difference to the FP64 solution of the same case, and time to 1e-8 (setup + solve)."""
+    from synth.coeff import checker_per_subdomain
+    from synth.voronoi import voronoi_mesh
+    import torch
+    from paper_1903_11357_gb300 import dgasm as dg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    m = voronoi_mesh(N_ELEM, SEED)
+    sub, _ = dg.Mesh.from_polymesh(m, np.ones(m.n_elem)).partition(NSUB, 0)
+    rows = []
+    for contrast in (1.0, 1e2, 1e4, 1e6):
+        S = dg.System(dg.Mesh.from_polymesh(m, checker_per_subdomain(m, sub, contrast)), 4, 10.0, f=f_sin)
+        b = torch.tensor(S.rhs(), dtype=torch.float64, device="cuda")
+        ref = None
+        for precision in ("fp64", "fp32", "tf32", "bf16"):
+            for _ in range(2):   # the second solve is timed
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                P = dg.Prec(S, NSUB, NCOARSE, P_C, precision=precision, stream=stream)
+                x = torch.zeros_like(b)
+                rc, st = P.solve(b, x, rtol=1e-8, maxit=20000, stream=stream)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+            if precision == "fp64":
+                ref = x.clone()
+            rows.append({"contrast": contrast, "precision": precision, "rc": rc, "iters": st[0]["iters"],
+                         "true_relres": st[0]["true_relres"], "kappa": st[0]["kappa"],
+                         "rel_diff_vs_fp64": float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref)),
+                         "ms": 1000 * dt})
+            del P
+    t = {r["precision"]: r["ms"] for r in rows if r["contrast"] == 1e4}
+    out = {"metric": METRIC, "value": 1000.0 / t["fp32"], "unit": "solves/s", "n_gpus": 1, "steps": 1,
+           "warmup": 1, "ms_per_step": t["fp32"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 outer / local per row", "data": "synthetic",
+           "config": {"workload": "precision sweep: 16384-cell mesh (seed 2), p=4 (245760 dofs), 64 subdomains, "
+                                  "256 agglomerates p_c=1, checkerboard contrast 1..1e6; value = FP32-local "
+                                  "solves/s at contrast 1e4"},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def profiled_step(dg, step, barrier, precision):
     """One untimed step with every kernel kind bracketed by CUDA events: per-kind device time."""
     barrier()
@@ -213,7 +433,14 @@ def main():
     ap.add_argument("--nsub", type=int, default=NSUB)
     ap.add_argument("--ncoarse", type=int, default=NCOARSE)
     ap.add_argument("--degree", type=int, default=P_DEG)
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "batch", "serve", "sweep"],
+                    help="cfg2: the headline solve (default); batch: 48-problem batch; serve: Poisson "
+                         "arrivals into the server; sweep: precision / contrast sweep at p=4")
+    ap.add_argument("--requests", type=int, default=48, help="requests per arrival rate (serve)")
     args = ap.parse_args()
+    if args.workload != "cfg2":
+        {"batch": run_batch, "serve": run_serve, "sweep": run_sweep}[args.workload](args)
+        return
     if (args.elems, args.nsub, args.ncoarse, args.degree) != (N_ELEM, NSUB, NCOARSE, P_DEG):
         N_ELEM, NSUB, NCOARSE, P_DEG = args.elems, args.nsub, args.ncoarse, args.degree
         WORKLOAD = (f"profiling case: {N_ELEM} Lloyd-Voronoi cells, p={P_DEG}, {NSUB} subdomains, {NCOARSE} "

@@ -190,19 +190,24 @@ typedef struct {
 int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info);
 int dgasm_prec_destroy(dgasm_prec_t pc);
 
-/* ---- ASPCG solve (Sec. 7: PCG with P_ad from x0 = 0, stop when ||r||_2 / ||b||_2 < rtol) --------- */
+/* ---- ASPCG solve (Sec. 7: PCG with P_ad from x0 = 0, stop when ||r||_2 / ||b||_2 < rtol) ---------
+ * The stop test is taken on the recursive residual; the true residual b - A x is then recomputed in
+ * FP64, and where it misses rtol the recursion restarts from it (residual replacement: r = b - A x,
+ * p = B r; no iteration counted), at most 4 times and within maxit, so that a converged right-hand side
+ * meets rtol in both senses. */
 typedef struct {
   double rtol;          /* relative residual tolerance (Sec. 7 uses 1e-8); <= 0 means 1e-8 */
   int maxit;            /* iteration limit; <= 0 means 10000 */
   int fixed_iters;      /* > 0: run exactly this many iterations, no stop test */
-  int x0_given;         /* 1: x holds the initial guess on entry; 0: start from zero (Sec. 7) */
+  int x0_given;         /* 1: x holds the initial guess on entry (device or host, as b); 0: start from
+                           zero (Sec. 7).  Not accepted by dgasm_submit. */
   int host_buffers;     /* 1: b and x are host pointers (copied in and out inside the call) */
   void* stream;         /* cudaStream_t or NULL */
 } dgasm_solve_opts;
 
 typedef struct {
   int iters;            /* PCG iterations (matrix-vector products after the initial residual) */
-  int converged;        /* 1 if ||r_k|| / ||b|| <= rtol held */
+  int converged;        /* 1 if ||r_k|| / ||b|| <= rtol held (and, unless fixed_iters, ||b - A x|| too) */
   double relres;        /* recursive residual ||r_k|| / ||b|| */
   double true_relres;   /* ||b - A x_k|| / ||b||, recomputed in FP64 */
   double lambda_min;    /* Lanczos extreme-eigenvalue estimates of B A from the CG coefficients */
@@ -213,14 +218,14 @@ typedef struct {
 } dgasm_stats;
 
 /* Solves A x = b for nrhs right-hand sides (column-major ndof x nrhs, caller's dof order), device
- * pointers unless opts->host_buffers.  st (nrhs entries) may be NULL.  The Lanczos estimate uses all
- * CG coefficients of the run.  Returns DGASM_ENOCONV if a right-hand side hit maxit (x holds the
+ * pointers unless opts->host_buffers.  st (nrhs entries) may be NULL.  The Lanczos estimate uses the
+ * CG coefficients of the run up to its first convergence (before any residual replacement).  Returns DGASM_ENOCONV if a right-hand side hit maxit (x holds the
  * last iterate), DGASM_ENAN on a NaN/Inf in b or in a Krylov scalar, DGASM_EINVAL, DGASM_ECUDA. */
 int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x, const dgasm_solve_opts* o,
                 dgasm_stats* st);
 
 /* Solves nprob independent problems in one set of batched launches: problem i uses pcs[i] with
- * nrhs[i] right-hand sides b[i] / x[i] (device pointers).  Results are bitwise identical to
+ * nrhs[i] right-hand sides b[i] / x[i] (device pointers; x0_given allowed, host_buffers not).  Results are bitwise identical to
  * dgasm_solve of each problem alone.  st holds sum(nrhs) entries in problem order (may be NULL). */
 int dgasm_solve_batch(int nprob, const dgasm_prec_t* pcs, const int* nrhs, const double* const* b,
                       double* const* x, const dgasm_solve_opts* o, dgasm_stats* st);

@@ -219,9 +219,61 @@ int Engine::precond(int mode, EventPairs* ev) {
   return DGASM_OK;
 }
 
-int Engine::init() {
+int Engine::init(bool x0) {
   init_ev.reset();
-  DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT, km, stream); }));
+  lanczos_len.assign(nprob, std::vector<int>());
+  if (!x0) {
+    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT, km, stream); }));
+  } else {
+    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT_X0, km, stream); }));
+    // a zero right-hand side has the solution 0 whatever the initial guess
+    for (int i = 0; i < nprob; ++i) {
+      const ProbDev& D = hp[i];
+      const int wk = pcs[i]->ws.k;
+      std::vector<double> bn(wk);
+      DG_CUDA(cudaMemcpyAsync(bn.data(), D.bnorm, sizeof(double) * wk, cudaMemcpyDeviceToHost, stream));
+      DG_CUDA(cudaStreamSynchronize(stream));
+      for (int kk = 0; kk < nrhs[i]; ++kk)
+        if (bn[kk] == 0.0) DG_CUDA(cudaMemsetAsync(D.x + (size_t)kk * D.ndof, 0, sizeof(double) * D.ndof, stream));
+    }
+    DG_TRY(spmv(1, &init_ev));
+    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_RESTART, km, stream); }));
+  }
+  DG_TRY(precond(MODE_INIT, &init_ev));
+  return DGASM_OK;
+}
+
+int Engine::true_residual() { return spmv(1, &init_ev); }
+
+int Engine::restart(int* count) {
+  *count = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const ProbDev& D = hp[i];
+    if (D.fixed_iters > 0) continue;
+    const int wk = pcs[i]->ws.k;
+    std::vector<double> sc(5 * (size_t)wk);
+    std::vector<int> iv(3 * (size_t)wk);
+    DG_CUDA(cudaMemcpyAsync(sc.data(), D.bnorm, sizeof(double) * 5 * wk, cudaMemcpyDeviceToHost, stream));
+    DG_CUDA(cudaMemcpyAsync(iv.data(), D.done, sizeof(int) * 3 * wk, cudaMemcpyDeviceToHost, stream));
+    DG_CUDA(cudaStreamSynchronize(stream));
+    bool any = false;
+    for (int kk = 0; kk < nrhs[i]; ++kk) {
+      const double true_rr = sc[4 * (size_t)wk + kk];
+      if (iv[kk] == 1 && true_rr > D.rtol && iv[wk + kk] < D.maxit && std::isfinite(true_rr)) {
+        if (lanczos_len[i].empty()) lanczos_len[i].assign(wk, -1);
+        if (lanczos_len[i][kk] < 0) lanczos_len[i][kk] = iv[wk + kk];
+        iv[kk] = 0;
+        any = true;
+        ++*count;
+      }
+    }
+    if (any) DG_CUDA(cudaMemcpyAsync(D.done, iv.data(), sizeof(int) * wk, cudaMemcpyHostToDevice, stream));
+  }
+  if (*count == 0) return DGASM_OK;
+  h_remaining[0] = *count;
+  h_remaining[1] = 0;
+  DG_CUDA(cudaMemcpyAsync(d_remaining, h_remaining, 2 * sizeof(int), cudaMemcpyHostToDevice, stream));
+  DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_RESTART, km, stream); }));
   DG_TRY(precond(MODE_INIT, &init_ev));
   return DGASM_OK;
 }
@@ -270,7 +322,6 @@ int Engine::iterate(int max_iters, int* ran) {
 }
 
 int Engine::finish() {
-  DG_TRY(spmv(1, &init_ev));
   DG_CUDA(launch_finish(B, tot_spmv, 0, stream));
   ++launches;
   return DGASM_OK;
@@ -326,7 +377,9 @@ int Engine::collect(dgasm_stats* st, double ms, std::vector<int>* rcs) {
       s.solve_ms = ms;
       s.launches = (int)launches;
       s.lambda_min = s.lambda_max = s.kappa = NAN;
-      const int nh = std::min(iters, D.maxit);
+      int nh = std::min(iters, D.maxit);
+      // after a residual replacement the coefficients of the first CG run give the Lanczos estimate
+      if (!lanczos_len.empty() && !lanczos_len[i].empty() && lanczos_len[i][kk] >= 0) nh = std::min(nh, lanczos_len[i][kk]);
       if (nh >= 1) {
         std::vector<double> al(nh), be(std::max(nh - 1, 1));
         DG_CUDA(cudaMemcpy(al.data(), D.alpha_hist + (size_t)kk * D.maxit, sizeof(double) * nh, cudaMemcpyDeviceToHost));
@@ -353,7 +406,10 @@ int Engine::collect(dgasm_stats* st, double ms, std::vector<int>* rcs) {
   return DGASM_OK;
 }
 
-// One complete solve of a batch: init, iterate until done, finish, statistics.
+constexpr int MAX_RESTARTS = 4;
+
+// One complete solve of a batch: init, iterate until done, true residual (and residual replacement where
+// it misses the tolerance), x out, statistics.
 int solve_all(Engine& E, int n, dgasm_prec_s* const* pcs, const int* nrhs, const double* const* b, double* const* x,
               const dgasm_solve_opts* o, cudaStream_t stream, dgasm_stats* st) {
   const int maxit = (o && o->maxit > 0) ? o->maxit : 10000;
@@ -363,9 +419,19 @@ int solve_all(Engine& E, int n, dgasm_prec_s* const* pcs, const int* nrhs, const
   DG_TRY(E.build(n, pcs, nrhs, b, x, os.data(), stream, -1));
   DG_TRY(E.reset_state());
   DG_CUDA(cudaEventRecord(E.ev0, stream));
-  DG_TRY(E.init());
+  DG_TRY(E.init(o && o->x0_given));
   int ran = 0;
   DG_TRY(E.iterate((fixed > 0 ? fixed : maxit) + Engine::CHUNK, &ran));
+  DG_TRY(E.true_residual());
+  // the recursion's residual can drift from b - A x by rounding: continue from the true residual until
+  // both meet rtol (a few restarts at most)
+  for (int round = 0; round < MAX_RESTARTS; ++round) {
+    int nre = 0;
+    DG_TRY(E.restart(&nre));
+    if (nre == 0) break;
+    DG_TRY(E.iterate(maxit + Engine::CHUNK, &ran));
+    DG_TRY(E.true_residual());
+  }
   DG_TRY(E.finish());
   DG_CUDA(cudaEventRecord(E.ev1, stream));
   DG_CUDA(cudaStreamSynchronize(stream));
@@ -384,7 +450,6 @@ extern "C" int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x
                            dgasm_stats* st) {
   clear_error();
   if (!pc || !b || !x) return set_error(DGASM_EINVAL, "dgasm_solve: NULL argument");
-  if (o && o->x0_given) return set_error(DGASM_EINVAL, "dgasm_solve: an initial guess is not supported (x0_given)");
   if (nrhs < 1 || nrhs > KMAX) return set_error(DGASM_EINVAL, "nrhs=%d must lie in [1, %d]", nrhs, KMAX);
   std::lock_guard<std::mutex> lk(pc->mu);
   if (!pc->engine) pc->engine.reset(new (std::nothrow) Engine());
@@ -397,6 +462,7 @@ extern "C" int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x
     double* db = pc->io.as<double>();
     double* dx = db + n;
     DG_CUDA(cudaMemcpyAsync(db, b, n * sizeof(double), cudaMemcpyHostToDevice, stream));
+    if (o->x0_given) DG_CUDA(cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, stream));
     const double* bb[1] = {db};
     double* xx[1] = {dx};
     int rc = solve_all(*pc->engine, 1, arr, &nrhs, bb, xx, o, stream, st);
@@ -414,8 +480,7 @@ extern "C" int dgasm_solve_batch(int nprob, const dgasm_prec_t* pcs, const int* 
                                  double* const* x, const dgasm_solve_opts* o, dgasm_stats* st) {
   clear_error();
   if (nprob < 1 || !pcs || !nrhs || !b || !x) return set_error(DGASM_EINVAL, "dgasm_solve_batch: bad arguments");
-  if (o && (o->x0_given || o->host_buffers))
-    return set_error(DGASM_EINVAL, "dgasm_solve_batch: device buffers and zero initial guesses only");
+  if (o && o->host_buffers) return set_error(DGASM_EINVAL, "dgasm_solve_batch: device buffers only");
   for (int i = 0; i < nprob; ++i) {
     if (!pcs[i] || !b[i] || !x[i]) return set_error(DGASM_EINVAL, "dgasm_solve_batch: NULL entry %d", i);
     for (int j = 0; j < i; ++j)

@@ -87,7 +87,10 @@ struct BatchDev {
 };
 
 // ---- solve kernels (kernels_solve.cu) ----
-enum UpdateMode { MODE_INIT = 0, MODE_ITER = 1 };
+// k_update modes: INIT r = b, x = 0; ITER the CG update and stop test; RESTART r = b - q with q = A x
+// from the SpMV (residual replacement, no iteration counted); INIT_X0 like INIT but x = the caller's
+// initial guess (r = b - A x follows by SpMV + RESTART)
+enum UpdateMode { MODE_INIT = 0, MODE_ITER = 1, MODE_RESTART = 2, MODE_INIT_X0 = 3 };
 // km: 1 when every problem of the batch has one right-hand side, else KMAX
 int launch_spmv(const BatchDev& B, int p, int total, int operand /*0: q = A p, 1: q = A x, true residual*/, int km,
                 void* stream);

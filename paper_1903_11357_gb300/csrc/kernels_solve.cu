@@ -218,10 +218,13 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
       if (!act[kk]) continue;
       const long long o = kk * (long long)P.ndof + d;
       double rv;
-      if (mode == MODE_INIT) {
-        rv = P.b_user[kk * (long long)P.ndof + (long long)P.perm[e] * np + a];
+      if (mode == MODE_INIT || mode == MODE_INIT_X0) {
+        const long long u = kk * (long long)P.ndof + (long long)P.perm[e] * np + a;
+        rv = P.b_user[u];
         P.b[o] = rv;
-        P.x[o] = 0.0;
+        P.x[o] = mode == MODE_INIT ? 0.0 : P.x_user[u];
+      } else if (mode == MODE_RESTART) {
+        rv = P.b[o] - P.q[o];
       } else {
         P.x[o] = fma(alpha[kk], P.p[o], P.x[o]);
         rv = fma(-alpha[kk], P.q[o], P.r[o]);
@@ -279,7 +282,21 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
     if (!act[kk]) return;
     const double s = warp_sum_strided(P.part_rr + kk, P.ngrp, k);
     if ((threadIdx.x & 31) != 0) return;
-    if (mode == MODE_INIT) {
+    if (mode == MODE_RESTART) {
+      // residual replacement: the recursion continues from r = b - A x; no iteration is counted
+      const double rel = sqrt(s) / P.bnorm[kk];
+      P.relres[kk] = rel;
+      if (!finite_d(rel)) {
+        P.status[kk] = DGASM_ENAN;
+        P.done[kk] = 3;
+        atomicSub(P.remaining, 1);
+      } else if (P.fixed_iters == 0 && rel <= P.rtol) {
+        P.done[kk] = 1;
+        atomicSub(P.remaining, 1);
+      }
+      return;
+    }
+    if (mode == MODE_INIT || mode == MODE_INIT_X0) {
       double bn = sqrt(s);
       P.bnorm[kk] = bn;
       P.relres[kk] = bn > 0.0 ? 1.0 : 0.0;

@@ -193,7 +193,8 @@ void dgasm_server_s::run() {
       ++rounds;
     }
     if (fin.empty()) continue;
-    // retire: true residual, caller-order solution, statistics
+    // retire: true residual (requests whose true residual misses rtol restart from it and stay),
+    // caller-order solution, statistics
     std::vector<int> rcs(fin.size(), rc);
     if (rc >= 0) {
       std::vector<dgasm_prec_s*> fp;
@@ -202,16 +203,39 @@ void dgasm_server_s::run() {
       std::vector<double*> fx;
       std::vector<const dgasm_solve_opts*> fo;
       int total = 0;
-      for (Request* r : fin) {
-        fp.push_back(r->pc.get());
-        fn.push_back(r->nrhs);
-        fb.push_back(r->b);
-        fx.push_back(r->x);
-        fo.push_back(&r->o);
-        total += r->nrhs;
+      auto gather = [&]() {
+        fp.clear(); fn.clear(); fb.clear(); fx.clear(); fo.clear();
+        total = 0;
+        for (Request* r : fin) {
+          fp.push_back(r->pc.get());
+          fn.push_back(r->nrhs);
+          fb.push_back(r->b);
+          fx.push_back(r->x);
+          fo.push_back(&r->o);
+          total += r->nrhs;
+        }
+      };
+      gather();
+      int frc = engine_aux->build((int)fin.size(), fp.data(), fn.data(), fb.data(), fx.data(), fo.data(), stream, 0);
+      if (frc >= 0) frc = engine_aux->true_residual();
+      int nre = 0;
+      if (frc >= 0) frc = engine_aux->restart(&nre);
+      if (frc >= 0 && nre > 0) {
+        std::vector<int> d2;
+        frc = engine_aux->read_done(d2, nullptr);
+        if (frc >= 0) {
+          std::vector<Request*> keep;
+          for (size_t i = 0; i < fin.size(); ++i)
+            if (d2[i]) keep.push_back(fin[i]);
+          fin.swap(keep);
+          rcs.assign(fin.size(), rc);
+          active_changed = true;   // restarted requests continue in the next rounds
+          if (fin.empty()) continue;
+          gather();
+          frc = engine_aux->build((int)fin.size(), fp.data(), fn.data(), fb.data(), fx.data(), fo.data(), stream, 0);
+        }
       }
       std::vector<dgasm_stats> st(total);
-      int frc = engine_aux->build((int)fin.size(), fp.data(), fn.data(), fb.data(), fx.data(), fo.data(), stream, 0);
       if (frc >= 0) frc = engine_aux->finish();
       if (frc >= 0 && cudaStreamSynchronize(stream) != cudaSuccess) frc = cuda_error(cudaGetLastError(), "finish");
       if (frc >= 0) {

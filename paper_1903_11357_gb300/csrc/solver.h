@@ -36,6 +36,7 @@ struct Workspace {
 // a captured graph of CHUNK iterations, and the event pairs used when profiling.
 struct Engine {
   static constexpr int CHUNK = 8;
+  std::vector<std::vector<int>> lanczos_len;   // per problem and rhs: iterations of the first CG run
   int nprob = 0;
   std::vector<dgasm_prec_s*> pcs;
   std::vector<int> nrhs;
@@ -64,9 +65,13 @@ struct Engine {
   int build(int n, dgasm_prec_s* const* pcs, const int* nrhs, const double* const* b, double* const* x,
             const dgasm_solve_opts* const* opts, cudaStream_t stream, int remaining);
   int reset_state();                 // clears done flags, counters and iteration counts
-  int init();                        // r = b, z = B r, p = z, gamma = (r, z)
+  int init(bool x0 = false);         // r = b (- A x0), z = B r, p = z, gamma = (r, z)
+  // Residual replacement for right-hand sides whose recursive residual met rtol but whose true residual
+  // (from the last true_residual()) did not: r = b - A x, z = B r, p = z; *count = how many restarted.
+  int restart(int* count);
+  int true_residual();               // q = A x and the true relative residual of every right-hand side
   int iterate(int max_iters, int* ran);  // CHUNK-iteration graphs until all done or max_iters
-  int finish();                      // true residual and x in the caller's order
+  int finish();                      // x in the caller's order
   int apply_out();                   // z = B r into the caller's buffer (preconditioner apply)
   // statistics of every right-hand side (problem order); per-problem return codes in rcs if given
   int collect(dgasm_stats* st, double ms, std::vector<int>* rcs);

@@ -278,10 +278,10 @@ class Prec:
         check(lib().dgasm_prec_footprint(self.h, C.byref(b)))
         return b.value
 
-    def solve(self, b, x, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None, host_buffers=False):
-        """b, x: (k, ndof) or (ndof,) float64 CUDA tensors (numpy arrays if host_buffers).  Returns
-        (return code, [stats dict per right-hand side])."""
-        o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=0,
+    def solve(self, b, x, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None, host_buffers=False, x0_given=False):
+        """b, x: (k, ndof) or (ndof,) float64 CUDA tensors (numpy arrays if host_buffers); with x0_given
+        x holds the initial guess on entry.  Returns (return code, [stats dict per right-hand side])."""
+        o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=1 if x0_given else 0,
                       host_buffers=1 if host_buffers else 0, stream=_stream_ptr(stream))
         if host_buffers:
             k = 1 if b.ndim == 1 else b.shape[0]
@@ -301,13 +301,13 @@ class Prec:
             self.h = None
 
 
-def solve_batch(precs, bs, xs, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None):
+def solve_batch(precs, bs, xs, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None, x0_given=False):
     n = len(precs)
     hs = (C.c_void_p * n)(*[p.h.value for p in precs])
     ks = np.array([1 if b.dim() == 1 else b.shape[0] for b in bs], np.int32)
     bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
     xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
-    o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=0, host_buffers=0,
+    o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=1 if x0_given else 0, host_buffers=0,
                   stream=_stream_ptr(stream))
     st = (Stats * int(ks.sum()))()
     rc = lib().dgasm_solve_batch(n, hs, _ip(ks), bp, xp, C.byref(o), st)

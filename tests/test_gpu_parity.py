@@ -111,9 +111,46 @@ def test_mixed_precision_reaches_tolerance(precision):
     c = build_case(256, 1, 2, 4, 16, 1, 1e4, precision=precision)
     x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
     rc, st = c["P"].solve(dev(c["b"]), x, rtol=1e-8)
-    assert rc == 0 and st[0]["converged"] and st[0]["true_relres"] <= 2e-8
+    assert rc == 0 and st[0]["converged"] and st[0]["true_relres"] <= 1e-8
     xs = np.linalg.solve(c["A"].toarray(), c["b"])
     assert np.linalg.norm(x.cpu().numpy() - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_true_residual_meets_tolerance_high_contrast(precision):
+    # p = 4 and contrast 1e6: the recursive residual drifts from b - A x; the solve restarts from the
+    # true residual until both meet rtol
+    m = mesh(1024, 3)
+    sub, _ = dg.Mesh.from_polymesh(m, np.ones(1024)).partition(16, 0)
+    S = dg.System(dg.Mesh.from_polymesh(m, checker_per_subdomain(m, sub, 1e6)), 4, 10.0, f=f_sin)
+    P = dg.Prec(S, 16, 64, 1, precision=precision)
+    b = dev(S.rhs())
+    x = torch.zeros_like(b)
+    rc, st = P.solve(b, x, rtol=1e-8)
+    assert rc == 0 and st[0]["converged"] and st[0]["true_relres"] <= 1e-8 and st[0]["relres"] <= 1e-8
+    assert 0.0 < st[0]["kappa"] < 1e6
+
+
+def test_initial_guess():
+    c = build_case(256, 1, 2, 4, 16, 1, 1e4)
+    b = dev(c["b"])
+    x = torch.zeros_like(b)
+    rc, st = c["P"].solve(b, x)
+    assert rc == 0
+    # from the converged solution: nothing to do, x comes back unchanged
+    x2 = x.clone()
+    rc, st2 = c["P"].solve(b, x2, x0_given=True)
+    assert rc == 0 and st2[0]["iters"] == 0 and torch.equal(x2, x)
+    # from a perturbed guess: the same solution, fewer iterations than from zero
+    g = torch.Generator(device="cpu").manual_seed(7)
+    x3 = x + 1e-4 * torch.randn(x.shape, generator=g, dtype=torch.float64).cuda()
+    rc, st3 = c["P"].solve(b, x3, x0_given=True)
+    assert rc == 0 and st3[0]["true_relres"] <= 1e-8 and st3[0]["iters"] <= st[0]["iters"]
+    assert float(torch.linalg.norm(x3 - x)) <= 1e-6 * float(torch.linalg.norm(x))
+    # a zero right-hand side gives zero whatever the guess
+    x4 = torch.ones_like(x)
+    rc, st4 = c["P"].solve(torch.zeros_like(b), x4, x0_given=True)
+    assert rc == 0 and float(x4.abs().max()) == 0.0
 
 
 def test_zero_rhs_and_one_subdomain():
