@@ -35,6 +35,19 @@ WORKLOAD = ("16384 Lloyd-relaxed Voronoi cells of (0,1)^2 (seed 2, 20 Lloyd step
             "C_sigma=10, 64 RCB subdomains (~2560 dofs), 256 RCB agglomerates at p_c=1, rho=1e4 on a 4x4 "
             "checkerboard of subdomains; f = 2 pi^2 sin(pi x) sin(pi y); rtol 1e-8 from x0=0")
 FP64_PEAK_FLOPS_PER_CLK = 152 * 2 * 2   # 152 SMs x 2 DFMA/clk (measured issue rate) x 2 flop
+# DRAM bytes (read + write) per stream tile of the FP64 local-solve kernel, from one ncu capture of the
+# 4096-cell case (profiles/local_solve_fp64_4096cells_p3.md); valid only for the kernel source it was taken on
+LOCAL_TRAFFIC = {"sha256": None, "bytes_per_stream_tile": None}
+
+
+def local_traffic(tiles):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1903_11357_gb300", "csrc", "kernels_local.cu")
+    with open(path, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    if LOCAL_TRAFFIC["sha256"] != h or not LOCAL_TRAFFIC["bytes_per_stream_tile"]:
+        return None
+    return LOCAL_TRAFFIC["bytes_per_stream_tile"] * tiles
 
 
 def f_sin(X):
@@ -583,7 +596,7 @@ def main():
         flops, bytes_ = None, None
     roof = {"kernel": dom, "bound": "alu", "achieved": (flops / avg_s / 1e12) if flops else None,
             "peak": fp64_peak, "unit": "TFLOP/s", "frac": (flops / avg_s / 1e12 / fp64_peak) if flops else None,
-            "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
+            "traffic": local_traffic(tiles) if dom == "local" else None, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
             "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
             "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (issue rate measured by an FMA probe)"}
 
