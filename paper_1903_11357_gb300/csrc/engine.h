@@ -132,12 +132,12 @@ int launch_dinv(int prec, const EnvDev& E, const void* L, const int* task, const
 // solve streams from factor tiles (src >= 0) and inverse-block tiles (src < 0)
 int launch_stream_gather(int prec, const void* L, const void* X, const long long* src, void* dst, long long n,
                          int transpose, void* stream);
-int launch_r0t(const int* perm, const double* xy, const int* pptr, const int* pvtx, const double* bbox,
-               const int* agg_int, const double* agg_bbox, int ne, int p, int q, const double* gl_t,
-               const double* gl_w, int mq, double* r0t, void* stream);
+int launch_r0t(const int* perm, const double* bbox, const int* agg_int, const double* agg_bbox, int ne, int p, int q,
+               const double* gl_t, const double* gl_w, int mq, double* r0t, void* st);
+// W: nnzb * nq * nq doubles of scratch
 int launch_galerkin(const int* grp_ptr, const int* grp_elems, const int* agg_int, const int* rowptr,
-                    const int* col, const double* vals, const double* r0t, int nagg, int np, int np2s, int nq,
-                    double* A0, void* stream);
+                    const int* col, const double* vals, const double* r0t, int ne, long long nnzb, int nagg, int np,
+                    int np2s, int nq, double* W, double* A0, void* stream);
 int launch_coarse_extract(const double* A0, int n0, double* scale0, const EnvDev& E0, double* Lr0, void* stream);
 int launch_identity(double* I, int n, void* stream);
 

@@ -312,7 +312,6 @@ __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restri
 }
 
 // ---- coarse transfer R_0^T|_kappa = M_kappa^{-1} N_kappa (Eq. R0T, nested agglomerates) ---------
-constexpr int R0T_WARPS = 4;
 
 __device__ void legendre_dev(int p, double t, double* L, double* dL) {
   L[0] = 1.0; dL[0] = 0.0;
@@ -323,148 +322,99 @@ __device__ void legendre_dev(int p, double t, double* L, double* dL) {
   }
 }
 
-// values of the scaled Legendre basis of degree p on box at (x, y)
-__device__ void basis_dev(int p, const double* box, double x, double y, double* out, int stride) {
-  double wx = box[1] - box[0], wy = box[3] - box[2];
-  double xi = 2.0 * (x - 0.5 * (box[0] + box[1])) / wx;
-  double eta = 2.0 * (y - 0.5 * (box[2] + box[3])) / wy;
-  double Lx[10], dLx[10], Ly[10], dLy[10];
-  legendre_dev(p, xi, Lx, dLx);
-  legendre_dev(p, eta, Ly, dLy);
-  int a = 0;
-  for (int d = 0; d <= p; ++d)
-    for (int i = d; i >= 0; --i, ++a) {
-      int j = d - i;
-      out[a * stride] = sqrt((2.0 * i + 1.0) * (2.0 * j + 1.0) / (wx * wy)) * Lx[i] * Ly[j];
-    }
-}
-
-__global__ void k_r0t(const int* __restrict__ perm, const double* __restrict__ xy, const int* __restrict__ pptr,
-                      const int* __restrict__ pvtx, const double* __restrict__ bbox, const int* __restrict__ agg_int,
+// R_0^T|_kappa = M_kappa^{-1} N_kappa (Eq. R0T) for nested agglomerates: the coarse basis functions are
+// polynomials of total degree q <= p, so (Remark 3.1) M^{-1} N holds the exact coefficients of their
+// restrictions in the element's basis, whatever domain the two mass matrices are integrated on.  On the
+// element's bounding box that basis is orthonormal (M = I), so R0T[a][c] = integral over the box of
+// phi_a psi_c, exact with mq = ceil((p + q + 1) / 2) Gauss points per direction (degree <= p + q in each
+// variable).  One thread per (element, a, c).
+__global__ void k_r0t(const int* __restrict__ perm, const double* __restrict__ bbox, const int* __restrict__ agg_int,
                       const double* __restrict__ agg_bbox, int ne, int p, int q, const double* __restrict__ gl_t,
                       const double* __restrict__ gl_w, int mq, double* __restrict__ r0t) {
-  extern __shared__ double sm[];
   const int np = (p + 1) * (p + 2) / 2, nq = (q + 1) * (q + 2) / 2;
-  const int per_warp = 32 * np + 32 * nq + np * np + np * nq;
-  int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* phi = sm + wid * per_warp;   // [np][32]
-  double* psi = phi + 32 * np;         // [nq][32]
-  double* M = psi + 32 * nq;           // [np][np]
-  double* N = M + np * np;             // [np][nq]
-  int i = blockIdx.x * R0T_WARPS + wid;
-  if (i >= ne) return;
-  int e = perm[i];
-  const double* box = bbox + 4LL * e;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ne * np * nq) return;
+  const int i = (int)(t / (np * nq)), ent = (int)(t % (np * nq)), a = ent / nq, c = ent % nq;
+  const double* box = bbox + 4LL * perm[i];
   const double* cbox = agg_bbox + 4LL * agg_int[i];
-  int b = pptr[e], nv = pptr[e + 1] - b;
-  double cx = 0, cy = 0;
-  for (int k = 0; k < nv; ++k) { cx += xy[2LL * pvtx[b + k]]; cy += xy[2LL * pvtx[b + k] + 1]; }
-  cx /= nv; cy /= nv;
-  for (int t = lane; t < np * np; t += 32) M[t] = 0.0;
-  for (int t = lane; t < np * nq; t += 32) N[t] = 0.0;
-  __syncwarp();
-  int npts = nv * mq * mq;
-  for (int base = 0; base < npts; base += 32) {
-    int pt = base + lane;
-    double wq = 0.0;
-    if (pt < npts) {
-      int tri = pt / (mq * mq), rem = pt % (mq * mq), iu = rem / mq, iv = rem % mq;
-      const double* B = xy + 2LL * pvtx[b + tri];
-      const double* Cv = xy + 2LL * pvtx[b + (tri + 1) % nv];
-      double e1x = B[0] - cx, e1y = B[1] - cy, e2x = Cv[0] - B[0], e2y = Cv[1] - B[1];
-      double u = gl_t[iu], v = gl_t[iv];
-      double x = cx + u * e1x + u * v * e2x, y = cy + u * e1y + u * v * e2y;
-      wq = gl_w[iu] * gl_w[iv] * u * fabs(e1x * e2y - e1y * e2x);
-      basis_dev(p, box, x, y, phi + lane, 32);
-      basis_dev(q, cbox, x, y, psi + lane, 32);
-      for (int a = 0; a < np; ++a) phi[a * 32 + lane] *= sqrt(wq);
-      for (int c = 0; c < nq; ++c) psi[c * 32 + lane] *= sqrt(wq);
-    } else {
-      for (int a = 0; a < np; ++a) phi[a * 32 + lane] = 0.0;
-      for (int c = 0; c < nq; ++c) psi[c * 32 + lane] = 0.0;
-    }
-    __syncwarp();
-    for (int t = lane; t < np * np; t += 32) {
-      int a = t / np, c = t % np;
-      double acc = 0.0;
-      for (int u = 0; u < 32; ++u) acc += phi[a * 32 + u] * phi[c * 32 + u];
-      M[t] += acc;
-    }
-    for (int t = lane; t < np * nq; t += 32) {
-      int a = t / nq, c = t % nq;
-      double acc = 0.0;
-      for (int u = 0; u < 32; ++u) acc += phi[a * 32 + u] * psi[c * 32 + u];
-      N[t] += acc;
-    }
-    __syncwarp();
-  }
-  // Cholesky of M (lane 0), then forward/backward solves, one coarse column per lane
-  if (lane == 0) {
-    for (int j = 0; j < np; ++j) {
-      double d = M[j * np + j];
-      for (int m = 0; m < j; ++m) d -= M[j * np + m] * M[j * np + m];
-      d = sqrt(d);
-      M[j * np + j] = d;
-      for (int r = j + 1; r < np; ++r) {
-        double v = M[r * np + j];
-        for (int m = 0; m < j; ++m) v -= M[r * np + m] * M[j * np + m];
-        M[r * np + j] = v / d;
-      }
+  // (i, j) degrees of basis function a (degree d, i from d down to 0) and of coarse function c
+  auto degrees = [](int idx, int* di, int* dj) {
+    int d = 0;
+    while (idx > d) { idx -= d + 1; ++d; }
+    *di = d - idx;
+    *dj = idx;
+  };
+  int ai, aj, ci, cj;
+  degrees(a, &ai, &aj);
+  degrees(c, &ci, &cj);
+  const double wx = box[1] - box[0], wy = box[3] - box[2];
+  const double cwx = cbox[1] - cbox[0], cwy = cbox[3] - cbox[2];
+  const double na = sqrt((2.0 * ai + 1.0) * (2.0 * aj + 1.0) / (wx * wy));
+  const double nc = sqrt((2.0 * ci + 1.0) * (2.0 * cj + 1.0) / (cwx * cwy));
+  double acc = 0.0;
+  for (int iu = 0; iu < mq; ++iu) {
+    const double x = box[0] + wx * gl_t[iu];
+    double Lx[10], dLx[10], Cx[10], dCx[10];
+    legendre_dev(p, 2.0 * gl_t[iu] - 1.0, Lx, dLx);
+    legendre_dev(q, 2.0 * (x - 0.5 * (cbox[0] + cbox[1])) / cwx, Cx, dCx);
+    for (int iv = 0; iv < mq; ++iv) {
+      const double y = box[2] + wy * gl_t[iv];
+      double Ly[10], dLy[10], Cy[10], dCy[10];
+      legendre_dev(p, 2.0 * gl_t[iv] - 1.0, Ly, dLy);
+      legendre_dev(q, 2.0 * (y - 0.5 * (cbox[2] + cbox[3])) / cwy, Cy, dCy);
+      acc = fma(gl_w[iu] * gl_w[iv], (Lx[ai] * Ly[aj]) * (Cx[ci] * Cy[cj]), acc);
     }
   }
-  __syncwarp();
-  for (int c = lane; c < nq; c += 32) {
-    for (int r = 0; r < np; ++r) {
-      double v = N[r * nq + c];
-      for (int m = 0; m < r; ++m) v -= M[r * np + m] * N[m * nq + c];
-      N[r * nq + c] = v / M[r * np + r];
-    }
-    for (int r = np - 1; r >= 0; --r) {
-      double v = N[r * nq + c];
-      for (int m = r + 1; m < np; ++m) v -= M[m * np + r] * N[m * nq + c];
-      N[r * nq + c] = v / M[r * np + r];
-    }
-  }
-  __syncwarp();
-  for (int t = lane; t < np * nq; t += 32) r0t[(long long)i * np * nq + t] = N[t];
+  r0t[t] = acc * na * nc * wx * wy;
 }
 
-// A_0 = R_0 A R_0^T (Eq. A0): one warp per agglomerate J, blocks visited in a fixed order; only this
-// warp writes the rows of J, so no atomics are needed and the sum order is deterministic
-__global__ void k_galerkin(const int* __restrict__ grp_ptr, const int* __restrict__ grp_elems,
-                           const int* __restrict__ agg_int, const int* __restrict__ rowptr, const int* __restrict__ col,
-                           const double* __restrict__ vals, const double* __restrict__ r0t, int nagg, int np, int np2s,
-                           int nq, double* __restrict__ A0) {
-  extern __shared__ double sm[];
-  int J = blockIdx.x;
-  if (J >= nagg) return;
-  int lane = threadIdx.x;
-  double* Tm = sm;  // [np][nq]
-  const int n0 = nagg * nq;
+// A_0 = R_0 A R_0^T (Eq. A0) in two passes.  Pass 1, one thread per (block k, a, c): the block's
+// contribution W_k = R_e^T B_k R_c (n_q x n_q; e the block's row element, c its column element).
+__global__ void k_galerkin_w(const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const double* __restrict__ vals, const double* __restrict__ r0t, int ne, long long nnzb,
+                             int np, int np2s, int nq, double* __restrict__ W) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzb * nq * nq) return;
+  const long long k = t / (nq * nq);
+  const int a = (int)((t / nq) % nq), cc = (int)(t % nq);
+  int lo = 0, hi = ne;   // row element: rowptr[e] <= k < rowptr[e + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (rowptr[mid] <= k) lo = mid; else hi = mid;
+  }
+  const double* Re = r0t + (long long)lo * np * nq;
+  const double* Rc = r0t + (long long)col[k] * np * nq;
+  const double* Bk = vals + k * np2s;   // column-major: entry (r, m) at m * np + r
+  double acc = 0.0;
+  for (int r = 0; r < np; ++r) {
+    double tr = 0.0;
+    for (int m = 0; m < np; ++m) tr = fma(Bk[m * np + r], Rc[m * nq + cc], tr);
+    acc = fma(Re[r * nq + a], tr, acc);
+  }
+  W[t] = acc;
+}
+
+// Pass 2, one warp per agglomerate J: the blocks of J's elements are added in a fixed order into the
+// warp's shared copy of row block J of A_0, which is then written out (only this warp writes those
+// rows, so no atomics; the sum order is deterministic).
+__global__ void k_galerkin_sum(const int* __restrict__ grp_ptr, const int* __restrict__ grp_elems,
+                               const int* __restrict__ agg_int, const int* __restrict__ rowptr,
+                               const int* __restrict__ col, const double* __restrict__ W, int nagg, int nq,
+                               double* __restrict__ A0) {
+  extern __shared__ double rowJ[];   // [nq][n0]
+  const int J = blockIdx.x, lane = threadIdx.x;
+  const int n0 = nagg * nq, nqq = nq * nq;
+  for (int t = lane; t < nq * n0; t += 32) rowJ[t] = 0.0;
+  __syncwarp();
   for (int g = grp_ptr[J]; g < grp_ptr[J + 1]; ++g) {
-    int e = grp_elems[g];
-    const double* Re = r0t + (long long)e * np * nq;
+    const int e = grp_elems[g];
     for (int k = rowptr[e]; k < rowptr[e + 1]; ++k) {
-      int c = col[k];
-      int Jc = agg_int[c];
-      const double* Rc = r0t + (long long)c * np * nq;
-      const double* Bk = vals + (long long)k * np2s;
+      const int Jc = agg_int[col[k]];
+      for (int t = lane; t < nqq; t += 32) rowJ[(t / nq) * n0 + Jc * nq + t % nq] += W[(long long)k * nqq + t];
       __syncwarp();
-      for (int t = lane; t < np * nq; t += 32) {
-        int r = t / nq, cc = t % nq;
-        double acc = 0.0;
-        for (int m = 0; m < np; ++m) acc += Bk[m * np + r] * Rc[m * nq + cc];
-        Tm[t] = acc;
-      }
-      __syncwarp();
-      for (int t = lane; t < nq * nq; t += 32) {
-        int a = t / nq, cc = t % nq;
-        double acc = 0.0;
-        for (int r = 0; r < np; ++r) acc += Re[r * nq + a] * Tm[r * nq + cc];
-        A0[(long long)(J * nq + a) * n0 + Jc * nq + cc] += acc;
-      }
     }
   }
+  for (int t = lane; t < nq * n0; t += 32) A0[(long long)(J * nq + t / n0) * n0 + t % n0] = rowJ[t];
 }
 
 // symmetrise, scale to unit diagonal and write the lower triangle of A_0 into its (dense) tile envelope
@@ -589,26 +539,25 @@ int launch_to_bf16(const float* src, void* dst, long long n, void* st) {
   return (int)cudaGetLastError();
 }
 
-int launch_r0t(const int* perm, const double* xy, const int* pptr, const int* pvtx, const double* bbox, const int* agg_int,
-               const double* agg_bbox, int ne, int p, int q, const double* gl_t, const double* gl_w, int mq, double* r0t,
-               void* st) {
-  int np = (p + 1) * (p + 2) / 2, nq = (q + 1) * (q + 2) / 2;
-  size_t smem = sizeof(double) * (size_t)R0T_WARPS * (32 * np + 32 * nq + np * np + np * nq);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_r0t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-  }
-  int blocks = (ne + R0T_WARPS - 1) / R0T_WARPS;
-  k_r0t<<<blocks, 32 * R0T_WARPS, smem, (cudaStream_t)st>>>(perm, xy, pptr, pvtx, bbox, agg_int, agg_bbox, ne, p, q, gl_t,
-                                                             gl_w, mq, r0t);
+int launch_r0t(const int* perm, const double* bbox, const int* agg_int, const double* agg_bbox, int ne, int p, int q,
+               const double* gl_t, const double* gl_w, int mq, double* r0t, void* st) {
+  const int np = (p + 1) * (p + 2) / 2, nq = (q + 1) * (q + 2) / 2;
+  const long long n = (long long)ne * np * nq;
+  k_r0t<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)st>>>(perm, bbox, agg_int, agg_bbox, ne, p, q, gl_t, gl_w, mq, r0t);
   return (int)cudaGetLastError();
 }
 
 int launch_galerkin(const int* grp_ptr, const int* grp_elems, const int* agg_int, const int* rowptr, const int* col,
-                    const double* vals, const double* r0t, int nagg, int np, int np2s, int nq, double* A0, void* st) {
-  size_t smem = sizeof(double) * (size_t)np * nq;
-  k_galerkin<<<nagg, 32, smem, (cudaStream_t)st>>>(grp_ptr, grp_elems, agg_int, rowptr, col, vals, r0t, nagg, np, np2s,
-                                                    nq, A0);
+                    const double* vals, const double* r0t, int ne, long long nnzb, int nagg, int np, int np2s, int nq,
+                    double* W, double* A0, void* st) {
+  const long long n = nnzb * nq * nq;
+  k_galerkin_w<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)st>>>(rowptr, col, vals, r0t, ne, nnzb, np, np2s, nq, W);
+  const size_t smem = sizeof(double) * (size_t)nq * nagg * nq;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_galerkin_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  k_galerkin_sum<<<nagg, 32, smem, (cudaStream_t)st>>>(grp_ptr, grp_elems, agg_int, rowptr, col, W, nagg, nq, A0);
   return (int)cudaGetLastError();
 }
 

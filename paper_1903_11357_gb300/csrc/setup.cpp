@@ -149,7 +149,7 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
   const size_t ts = ns * TILE * TILE, td = (size_t)P.env.ndinv * TILE * TILE;
   b += (t + td) * (pc.precision == DGASM_FP64 ? 8 : 4) + ts * (pc.precision == DGASM_FP64 ? 8 : 4) + ns * 8;
   b += (P.env.upd_task.size() + P.env.panel_task.size() + P.env.diag_task.size() + P.env.trow_F.size() * 3) * 4;
-  if (n0) b += ndof * P.nq * 8 + n0 * n0 * 8 * 3 + (size_t)P.env0.ntiles * TILE * TILE * 16;
+  if (n0) b += ndof * P.nq * 8 + n0 * n0 * 8 * 3 + (size_t)P.env0.ntiles * TILE * TILE * 16 + P.col.size() * P.nq * P.nq * 8;
   const int epi = NTHREADS / P.np;
   b += 8 * ((size_t)6 * nrhs * ndof + 2 * nrhs * std::max<size_t>(n0, 1) + 2 * (size_t)nrhs * maxit +
             (size_t)nrhs * ((P.ne + epi - 1) / epi + P.ngrp + P.nsub + n0 / 8 + 1)) + 4096;
@@ -198,7 +198,7 @@ int prec_build(dgasm_prec_s* pc) {
   DG_TRY(build_streams(fprec, P.env, pc->env, Lf, pc->Lc, pc->Lr, st, &nl));
   // coarse space: R_0^T, A_0 = R_0 A R_0^T, FP64 factor and explicit inverse
   if (pc->n0 > 0) {
-    const int n0 = pc->n0, q = P.q, nq = P.nq, mq = s->p + 2;
+    const int n0 = pc->n0, q = P.q, nq = P.nq, mq = (s->p + q + 2) / 2;
     std::vector<double> gt, gw;
     gauss_legendre01(mq, gt, gw);
     DevBuf d_gt, d_gw, d_aggbox;
@@ -206,15 +206,15 @@ int prec_build(dgasm_prec_s* pc) {
     DG_TRY(upload(d_gw, gw));
     DG_TRY(upload(d_aggbox, P.agg_bbox));
     DG_TRY(pc->r0t.alloc(sizeof(double) * (size_t)ne * np * nq));
-    DG_CUDA(launch_r0t(pc->perm.as<int>(), s->d_xy.as<double>(), s->d_pptr.as<int>(), s->d_pvtx.as<int>(),
-                       s->d_bbox.as<double>(), pc->agg_int.as<int>(), d_aggbox.as<double>(), ne, s->p, q,
-                       d_gt.as<double>(), d_gw.as<double>(), mq, pc->r0t.as<double>(), st));
+    DG_CUDA(launch_r0t(pc->perm.as<int>(), s->d_bbox.as<double>(), pc->agg_int.as<int>(), d_aggbox.as<double>(), ne,
+                       s->p, q, d_gt.as<double>(), d_gw.as<double>(), mq, pc->r0t.as<double>(), st));
     DevBuf A0;
     DG_TRY(A0.alloc(sizeof(double) * (size_t)n0 * n0));
-    DG_CUDA(cudaMemsetAsync(A0.ptr, 0, A0.bytes, st));
+    DevBuf W;
+    DG_TRY(W.alloc(sizeof(double) * P.col.size() * (size_t)nq * nq));
     DG_CUDA(launch_galerkin(pc->grp_ptr.as<int>(), pc->grp_elems.as<int>(), pc->agg_int.as<int>(), pc->rowptr.as<int>(),
-                            pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), P.nagg, np, np2s, nq,
-                            A0.as<double>(), st));
+                            pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), ne, (long long)P.col.size(),
+                            P.nagg, np, np2s, nq, W.as<double>(), A0.as<double>(), st));
     DG_TRY(upload_env(P.env0, pc->env0));
     DevBuf scale0, Lr0, Lc0, Lb0;
     DG_TRY(scale0.alloc(sizeof(double) * n0));
