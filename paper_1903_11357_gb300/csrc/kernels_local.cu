@@ -251,6 +251,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR][KCT][LW]
   C* xbuf = tvs + NCW * SR * KCT * LW;                 // [2][SR][KCT][16]: the peer's sums of own entries
   C* cpart = xbuf + 2 * NX;                            // [SR][KCT][16]: this CTA's sums of own entries
+  int* runs_s = reinterpret_cast<int*>(cpart + NX);    // [2][nsr][SR][2]: the subdomain's coupling runs
   S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][ch][HT]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * ch * HT);
   unsigned long long* empty = full + nstage;
@@ -301,6 +302,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     // ---- consumers: warp w owns the lines l0, l0 + 1 of every tile
     const int lw = LW * w;               // line within this CTA's half
     const int l0 = 16 * (int)rank + lw;  // line within the tile
+    for (int t = tid; t < nsr * SR * 2; t += NCT) {
+      runs_s[t] = P.fwd_run[(size_t)sr0 * SR * 2 + t];
+      runs_s[nsr * SR * 2 + t] = P.bwd_run[(size_t)sr0 * SR * 2 + t];
+    }
     for (int idx = tid; idx < KCT * npadh; idx += NCT) {
       const int j = idx / npadh, m = idx - j * npadh;
       const int i = (m >> 4) * T + 16 * (int)rank + (m & 15);
@@ -415,7 +420,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       for (int o = 0; o < SR; ++o) {
         C res[KCT];
         if (o < ntr) {
-          const int op0 = __ldg(runs + 2 * o), cnt = __ldg(runs + 2 * o + 1);
+          const int op0 = runs[2 * o], cnt = runs[2 * o + 1];
           run(cnt, y + op0 * 16 + lw, 16, npadh, res);
         } else {
 #pragma unroll
@@ -447,9 +452,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       });
     };
     start_pass(nfwd);
-    for (int q = 0; q < nsr; ++q) sweep_step(q, P.fwd_run + (size_t)(sr0 + q) * SR * 2, true);
+    for (int q = 0; q < nsr; ++q) sweep_step(q, runs_s + q * SR * 2, true);
     start_pass(nbwd);
-    for (int q = nsr - 1; q >= 0; --q) sweep_step(q, P.bwd_run + (size_t)(sr0 + q) * SR * 2, false);
+    for (int q = nsr - 1; q >= 0; --q) sweep_step(q, runs_s + (nsr + q) * SR * 2, false);
   }
   __syncthreads();
   // z_i = D^{-1/2} y on own entries, partial (r, z) of this CTA; rank 1 hands its sums to rank 0, which
@@ -497,7 +502,9 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int*
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   constexpr int SR = 8;
   const int npad = ((ndof_max + T - 1) / T) * T;
-  const int head = (int)sizeof(C) * (kct * npad / 2 + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 3 * SR * kct * 16);
+  const int nsr_max = (npad / T + SR - 1) / SR;
+  const int head = (int)sizeof(C) * (kct * npad / 2 + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 3 * SR * kct * 16) +
+                   (int)sizeof(int) * 4 * nsr_max * SR;
   const int off = (head + 127) & ~127;
   const int budget = optin - 2048 - off;   // static shared memory and slack
   const int hb = (int)(HT * sizeof(S));
