@@ -202,14 +202,18 @@ __device__ __forceinline__ void ld_pair(const __nv_bfloat162* p, C& a, C& b) {
 __device__ __forceinline__ double2 ld_pair2(const double* p) { return *reinterpret_cast<const double2*>(p); }
 __device__ __forceinline__ float2 ld_pair2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
+// tiles per ring slot: 32 KB of half tiles (the cost of a bulk copy is mostly per operation)
+template <typename S> __host__ __device__ constexpr int slot_tiles() { return (32 * 1024) / (int)(HT * sizeof(S)); }
+
 template <typename S, typename C, int KCT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
-    k_local(BatchDev B, int slot, int ring_off, int nstage, int ch) {
+    k_local(BatchDev B, int slot, int ring_off, int nstage) {
   using VS = typename Pair<S>::V;
   constexpr int SR = 8;                   // tile rows per super-row: super_row() of every precision
   constexpr int NX = SR * 16 * KCT;       // entries exchanged per reduction (each direction)
   constexpr int NE = SR * KCT * T;        // entries summed per reduction in each CTA
   constexpr bool TWO = sizeof(C) == 4;    // two accumulation chains (FP32: cover the FMA latency)
+  constexpr int CH = slot_tiles<S>();     // tiles per ring slot
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[NCW + 1][KCT];
   __shared__ double peer_rz[KCT];
@@ -243,17 +247,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   const int nbt = (n + T - 1) / T, npadh = nbt * 16;
   const int nsr = (nbt + SR - 1) / SR;
   const int sr0 = P.sub_sr[s];
-  const long long ff0 = P.fwd_ptr[s], nfwd = P.fwd_ptr[s + 1] - ff0;
-  const long long bb0 = P.bwd_ptr[s], nbwd = P.bwd_ptr[s + 1] - bb0;
+  const long long ff0 = P.fwd_ptr[s], bb0 = P.bwd_ptr[s];
   C* y = reinterpret_cast<C*>(smem);                  // [KCT][nbt][16]: own lines of every block
-  C* part = y + KCT * npadh;                           // [NCW][SR][KCT][T]
-  C* dpart = part + NCW * SR * KCT * T;                // [NCW][SR][KCT][T]
-  C* tvs = dpart + NCW * SR * KCT * T;                 // [NCW][SR][KCT][LW]
+  // per-warp partial sums [NCW][SR][KCT][T], one buffer for both reductions of a super-row: a reduction
+  // reads it only before its internal barrier, which every warp passes before writing the next partials
+  C* part = y + KCT * npadh;
+  C* dpart = part;
+  C* tvs = part + NCW * SR * KCT * T;                  // [NCW][SR][KCT][LW]
   C* xbuf = tvs + NCW * SR * KCT * LW;                 // [2][SR][KCT][16]: the peer's sums of own entries
   C* cpart = xbuf + 2 * NX;                            // [SR][KCT][16]: this CTA's sums of own entries
   int* runs_s = reinterpret_cast<int*>(cpart + NX);    // [2][nsr][SR][2]: the subdomain's coupling runs
-  S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][ch][HT]
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * ch * HT);
+  S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][CH][HT]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * CH * HT);
   unsigned long long* empty = full + nstage;
   if (tid == 0) {
     abort_flag = 0;
@@ -270,26 +275,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   cluster_sync();   // the peer's barriers exist before any store reaches them
 
   if (w == NCW) {
-    // ---- producer: half `rank` of the subdomain's forward stream, then of its backward stream, in runs
-    // of ch tiles (one bulk copy per run)
+    // ---- producer: half `rank` of the subdomain's forward stream, then of its backward stream.  Each
+    // super-row's coupling section and inverse-block section is copied in runs of up to CH tiles (one
+    // bulk copy per run), every section starting in a fresh slot.
     if (lane == 0) {
-      const S* Lc = reinterpret_cast<const S*>(P.Lc) + (rank * P.fwd_total + ff0) * HT;
-      const S* Lr = reinterpret_cast<const S*>(P.Lr) + (rank * P.bwd_total + bb0) * HT;
       int sl = 0;
       unsigned round = 0;   // how many times the ring has wrapped
       long long issued = 0;
       bool ok = true;
       for (int pass = 0; pass < 2 && ok; ++pass) {
-        const S* base = pass == 0 ? Lc : Lr;
-        const long long len_pass = pass == 0 ? nfwd : nbwd;
-        for (long long t = 0; t < len_pass; t += ch) {
-          const int len = (int)min((long long)ch, len_pass - t);
-          if (round > 0 && !mbar_wait(empty + sl, (round - 1) & 1, &abort_flag, B.err)) { ok = false; break; }
-          const unsigned bytes = (unsigned)(len * HT * sizeof(S));
-          mbar_expect_tx(full + sl, bytes);
-          bulk_g2s(ring + (size_t)sl * ch * HT, base + t * HT, bytes, full + sl);
-          ++issued;
-          if (++sl == nstage) { sl = 0; ++round; }
+        const S* base = pass == 0 ? reinterpret_cast<const S*>(P.Lc) + (rank * P.fwd_total + ff0) * HT
+                                  : reinterpret_cast<const S*>(P.Lr) + (rank * P.bwd_total + bb0) * HT;
+        const int* rt = (pass == 0 ? P.fwd_run : P.bwd_run) + (size_t)sr0 * SR * 2;
+        long long pos = 0;
+        for (int qi = 0; qi < nsr && ok; ++qi) {
+          const int q = pass == 0 ? qi : nsr - 1 - qi;
+          const int ntr = min(SR, nbt - q * SR);
+          int lc = 0;
+          for (int o = 0; o < ntr; ++o) lc += rt[(q * SR + o) * 2 + 1];
+          for (int sec = 0; sec < 2 && ok; ++sec) {
+            const int len_sec = sec == 0 ? lc : ntr * (ntr + 1) / 2;
+            for (int t = 0; t < len_sec; t += CH) {
+              const int len = min(CH, len_sec - t);
+              if (round > 0 && !mbar_wait(empty + sl, (round - 1) & 1, &abort_flag, B.err)) { ok = false; break; }
+              const unsigned bytes = (unsigned)(len * HT * sizeof(S));
+              mbar_expect_tx(full + sl, bytes);
+              bulk_g2s(ring + (size_t)sl * CH * HT, base + (pos + t) * HT, bytes, full + sl);
+              ++issued;
+              if (++sl == nstage) { sl = 0; ++round; }
+            }
+            pos += len_sec;
+          }
         }
       }
       // let every copy issued land (they all have when the consumers finished normally)
@@ -314,40 +330,50 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       y[idx] = v;
     }
     consumer_sync();
-    // stream cursor: ring slot, its phase parity, position in the run of ch tiles, run length, tiles of
-    // the current stream taken and its length
-    int cs = 0, cpos = 0, clen = 0;
+    // Stream cursor: ring slot cs (phase parity cph), this warp's line pair of the current tile in it
+    // (cur), tiles left in the slot's run of tiles (left_in), tiles of the current stream still to come
+    // after this slot (rest).  A slot is waited for when the cursor enters it and handed back to the
+    // producer when the cursor leaves it.
+    int cs = 0, left_in = 0, rest = 0;
     unsigned cph = 0;
-    long long taken = 0, plen = 0;
-    auto start_pass = [&](long long len) {
-      plen = len;
-      taken = 0;
-      clen = (int)min((long long)ch, len);
+    const VS* cur = nullptr;
+    const size_t wofs = (size_t)w * T + lane;   // this warp's pair within a half tile, in pairs
+    auto enter_slot = [&]() {
+      left_in = min(CH, rest);
+      rest -= left_in;
+      cur = reinterpret_cast<const VS*>(ring + (size_t)cs * CH * HT) + wofs;
+      if (left_in > 0 && !mbar_try(full + cs, cph)) mbar_wait(full + cs, cph, &abort_flag, B.err);
+    };
+    auto leave_slot = [&]() {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + cs);
+      if (++cs == nstage) { cs = 0; cph ^= 1u; }
+      enter_slot();
+    };
+    auto start_section = [&](int len) {
+      rest = len;
+      enter_slot();
     };
     // One run: cnt consecutive stream tiles into one output block of this warp's lanes,
     //   res[j] = sum_k (line pair of tile k) . (operand pair k of right-hand side j),
-    // operand pair k of rhs j at v + k * vstride + j * jstride.  Tiles alternate between two
-    // accumulators (restarting at each run of ch tiles, so the grouping depends only on the plan).
-    // After a timed-out wait the data are stale; the error word is set and the result is discarded.
+    // operand pair k of rhs j at v + k * vstride + j * jstride.  FP32 tiles alternate between two
+    // accumulators (restarting in each slot, so the grouping depends only on the plan).  After a
+    // timed-out wait the data are stale; the error word is set and the result is discarded.
     auto run = [&](int cnt, const C* v, int vstride, int jstride, C (&res)[KCT]) {
       C a0[KCT], a1[KCT];
 #pragma unroll
       for (int j = 0; j < KCT; ++j) a0[j] = a1[j] = (C)0;
-      int k = 0;
-      while (k < cnt) {
-        if (cpos == 0) mbar_wait(full + cs, cph, &abort_flag, B.err);
-        const int m = min(cnt - k, clen - cpos);
-        const VS* tp = reinterpret_cast<const VS*>(ring + ((size_t)cs * ch + cpos) * HT) + w * T + lane;
-        const C* vp = v + (size_t)k * vstride;
+      while (cnt > 0) {
+        const int m = min(cnt, left_in);
         int t = 0;
         for (; t + 1 < m; t += 2) {
           C x0, x1, z0, z1;
-          ld_pair(tp + t * (HT / 2), x0, x1);
-          ld_pair(tp + (t + 1) * (HT / 2), z0, z1);
+          ld_pair(cur + t * (HT / 2), x0, x1);
+          ld_pair(cur + (t + 1) * (HT / 2), z0, z1);
 #pragma unroll
           for (int j = 0; j < KCT; ++j) {
-            const auto o0 = ld_pair2(vp + t * vstride + j * jstride);
-            const auto o1 = ld_pair2(vp + (t + 1) * vstride + j * jstride);
+            const auto o0 = ld_pair2(v + t * vstride + j * jstride);
+            const auto o1 = ld_pair2(v + (t + 1) * vstride + j * jstride);
             C& b = TWO ? a1[j] : a0[j];
             a0[j] = fma(x0, o0.x, a0[j]);
             b = fma(z0, o1.x, b);
@@ -357,24 +383,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
         }
         if (t < m) {
           C x0, x1;
-          ld_pair(tp + t * (HT / 2), x0, x1);
+          ld_pair(cur + t * (HT / 2), x0, x1);
 #pragma unroll
           for (int j = 0; j < KCT; ++j) {
-            const auto o0 = ld_pair2(vp + t * vstride + j * jstride);
+            const auto o0 = ld_pair2(v + t * vstride + j * jstride);
             a0[j] = fma(x0, o0.x, a0[j]);
             a0[j] = fma(x1, o0.y, a0[j]);
           }
         }
-        k += m;
-        cpos += m;
-        taken += m;
-        if (cpos == clen) {   // this run of ch tiles is used up: hand the slot back
-          __syncwarp();
-          if (lane == 0) mbar_arrive(empty + cs);
-          cpos = 0;
-          if (++cs == nstage) { cs = 0; cph ^= 1u; }
-          clen = (int)min((long long)ch, plen - taken);
-        }
+        cur += m * (HT / 2);
+        v += m * vstride;
+        cnt -= m;
+        left_in -= m;
+        if (left_in == 0) leave_slot();
       }
 #pragma unroll
       for (int j = 0; j < KCT; ++j) res[j] = TWO ? a0[j] + a1[j] : a0[j];
@@ -415,8 +436,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     };
     // One super-row of a sweep: coupling runs, reduction to t = y_q - sum, block-inverse runs on t,
     // reduction to the new y_q.  runs: the plan's (first operand block, tiles) per output block.
+    // The inverse-block section of a full super-row (ntr = SR): its SR(SR+1)/2 tiles start in a fresh slot,
+    // so every tile sits at a static offset; fully unrolled, one accumulator per output block, a slot handed
+    // back after every CH tiles.  Forward: out_i += X(i, j) t_j, tiles (i, j) row by row; backward:
+    // out_o += X(i, o)^T t_i, tiles (i, o) column by column.
+    auto inverse_block = [&](bool fwd, C (&out)[SR][KCT]) {
+#pragma unroll
+      for (int a = 0; a < SR; ++a)
+#pragma unroll
+        for (int j = 0; j < KCT; ++j) out[a][j] = (C)0;
+      int u = 0;
+      auto tile = [&](int dst, int src) {
+        C x0, x1;
+        ld_pair(cur + u * (HT / 2), x0, x1);
+#pragma unroll
+        for (int j = 0; j < KCT; ++j) {
+          const auto o0 = ld_pair2(tw + (src * KCT + j) * LW);
+          out[dst][j] = fma(x0, o0.x, out[dst][j]);
+          out[dst][j] = fma(x1, o0.y, out[dst][j]);
+        }
+        if (++u == CH) {
+          leave_slot();
+          u = 0;
+        }
+      };
+      if (fwd) {
+#pragma unroll
+        for (int a = 0; a < SR; ++a)
+#pragma unroll
+          for (int b = 0; b <= a; ++b) tile(a, b);
+      } else {
+#pragma unroll
+        for (int a = 0; a < SR; ++a)
+#pragma unroll
+          for (int b = a; b < SR; ++b) tile(a, b);
+      }
+      if (u != 0) leave_slot();
+    };
     auto sweep_step = [&](int q, const int* runs, bool fwd) {
       const int I0 = q * SR, ntr = min(SR, nbt - I0);
+      int lc = 0;
+      for (int o = 0; o < ntr; ++o) lc += runs[2 * o + 1];
+      start_section(lc);
       for (int o = 0; o < SR; ++o) {
         C res[KCT];
         if (o < ntr) {
@@ -433,27 +494,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
       reduce(part, [&](int ii, int j, int u, C tot) {
         tw[(ii * KCT + j) * LW + u] = ii < ntr ? y[j * npadh + (I0 + ii) * 16 + lw + u] - tot : (C)0;
       });
-      // forward: output block o = sum_{j<=o} X(o, j) t_j; backward: output block o = sum_{i>=o} X(i, o)^T t_i
-      for (int o = 0; o < SR; ++o) {
-        C res[KCT];
-        if (o < ntr) {
-          if (fwd) run(o + 1, tw, KCT * LW, LW, res);
-          else run(ntr - o, tw + o * KCT * LW, KCT * LW, LW, res);
-        } else {
+      start_section(ntr * (ntr + 1) / 2);
+      if (ntr == SR) {
+        C out[SR][KCT];
+        inverse_block(fwd, out);
 #pragma unroll
-          for (int j = 0; j < KCT; ++j) res[j] = (C)0;
+        for (int o = 0; o < SR; ++o)
+#pragma unroll
+          for (int j = 0; j < KCT; ++j) dpart[((w * SR + o) * KCT + j) * T + lane] = out[o][j];
+      } else {
+        // a partial last super-row: the same products run by run
+        for (int o = 0; o < SR; ++o) {
+          C res[KCT];
+          if (o < ntr) {
+            if (fwd) run(o + 1, tw, KCT * LW, LW, res);
+            else run(ntr - o, tw + o * KCT * LW, KCT * LW, LW, res);
+          } else {
+#pragma unroll
+            for (int j = 0; j < KCT; ++j) res[j] = (C)0;
+          }
+#pragma unroll
+          for (int j = 0; j < KCT; ++j) dpart[((w * SR + o) * KCT + j) * T + lane] = res[j];
         }
-#pragma unroll
-        for (int j = 0; j < KCT; ++j) dpart[((w * SR + o) * KCT + j) * T + lane] = res[j];
       }
       consumer_sync();
       reduce(dpart, [&](int ii, int j, int u, C tot) {
         if (ii < ntr) y[j * npadh + (I0 + ii) * 16 + lw + u] = tot;
       });
     };
-    start_pass(nfwd);
     for (int q = 0; q < nsr; ++q) sweep_step(q, runs_s + q * SR * 2, true);
-    start_pass(nbwd);
     for (int q = nsr - 1; q >= 0; --q) sweep_step(q, runs_s + (nsr + q) * SR * 2, false);
   }
   __syncthreads();
@@ -492,10 +561,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   if (rank == 0 && tid < kc) P.part_rz[(long long)s * P.k + k0 + tid] = P.done[k0 + tid] == 0 ? csum + peer_rz[tid] : 0.0;
 }
 
-// shared memory: y, partial sums, exchange buffers and F values, then a ring of nstage slots of ch half
-// tiles (32 KB per slot)
+// shared memory: y, partial sums, exchange buffers and run tables, then a ring of nstage slots of 32 KB of
+// half tiles
 template <typename S, typename C>
-int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int* total) {
+int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* total) {
   int dev = 0;
   cudaGetDevice(&dev);
   int optin = 0;
@@ -503,24 +572,17 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* ch, int*
   constexpr int SR = 8;
   const int npad = ((ndof_max + T - 1) / T) * T;
   const int nsr_max = (npad / T + SR - 1) / SR;
-  const int head = (int)sizeof(C) * (kct * npad / 2 + 2 * NCW * SR * kct * T + NCW * SR * LW * kct + 3 * SR * kct * 16) +
+  const int head = (int)sizeof(C) * (kct * npad / 2 + NCW * SR * kct * T + NCW * SR * LW * kct + 3 * SR * kct * 16) +
                    (int)sizeof(int) * 4 * nsr_max * SR;
   const int off = (head + 127) & ~127;
   const int budget = optin - 2048 - off;   // static shared memory and slack
-  const int hb = (int)(HT * sizeof(S));
-  int c = (32 * 1024) / hb;
-  int ns = 0;
-  for (; c >= 1; c /= 2) {
-    ns = budget / (c * hb + 16);
-    if (ns >= 3) break;
-  }
-  if (c < 1) c = 1;
+  const int slot = slot_tiles<S>() * (int)(HT * sizeof(S)) + 16;   // 32 KB of tiles + its barriers
+  int ns = budget / slot;
   if (ns > 32) ns = 32;
-  if (ns < 2) return -1;
+  if (ns < 2) return -1;   // the subdomains are too large for this kernel's shared memory
   *ring_off = off;
   *nstage = ns;
-  *ch = c;
-  *total = off + ns * c * hb + ns * 16;
+  *total = off + ns * slot;
   return 0;
 }
 
@@ -542,11 +604,11 @@ int ensure_smem(K fn) {
 
 template <typename S, typename C, int KCT>
 int launch_one(const BatchDev& B, int slot, int items, int ndof_max, cudaStream_t st) {
-  int ring_off, nstage, ch, smem;
-  if (smem_layout<S, C>(ndof_max, KCT, &ring_off, &nstage, &ch, &smem)) return (int)cudaErrorInvalidValue;
+  int ring_off, nstage, smem;
+  if (smem_layout<S, C>(ndof_max, KCT, &ring_off, &nstage, &smem)) return (int)cudaErrorInvalidValue;
   auto fn = k_local<S, C, KCT>;
   if (int e = ensure_smem(fn)) return e;
-  fn<<<2 * items, NTH, smem, st>>>(B, slot, ring_off, nstage, ch);   // one CTA pair per item
+  fn<<<2 * items, NTH, smem, st>>>(B, slot, ring_off, nstage);   // one CTA pair per item
   return (int)cudaGetLastError();
 }
 
