@@ -26,6 +26,8 @@ int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
   const int n0 = pc.n0;
   const int epi = NTHREADS / P.np;
   n_chunk_items = (P.ne + epi - 1) / epi;
+  const int epis = SPMV_THREADS / P.np;
+  n_spmv_items = (P.ne + epis - 1) / epis;
   n_coarse_items = n0 > 0 ? (n0 + 7) / 8 : 0;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
@@ -34,7 +36,7 @@ int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
   o_scal = take(sizeof(double) * 5 * k);
   o_int = take(sizeof(int) * 3 * k);
   o_hist = take(sizeof(double) * 2 * (size_t)k * maxit);
-  o_ppq = take(sizeof(double) * (size_t)n_chunk_items * k);
+  o_ppq = take(sizeof(double) * (size_t)n_spmv_items * k);
   o_prr = take(sizeof(double) * (size_t)P.ngrp * k);
   o_prz = take(sizeof(double) * (size_t)P.nsub * k);
   o_pc = take(sizeof(double) * (size_t)std::max(n_coarse_items, 1) * k);
@@ -54,6 +56,8 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.nsub = P.nsub; D.ngrp = P.ngrp; D.n0 = pc.n0; D.k = kk; D.prec = pc.precision;
   D.epi = NTHREADS / P.np;
   D.n_chunk_items = n_chunk_items;
+  D.epi_spmv = SPMV_THREADS / P.np;
+  D.n_spmv_items = n_spmv_items;
   D.n_coarse_items = n_coarse_items;
   D.kc = kk > 1 ? KC : 1;
   D.n_rhs_chunks = (kk + D.kc - 1) / D.kc;
@@ -137,7 +141,7 @@ int Engine::build(int n, dgasm_prec_s* const* pcs_, const int* nrhs_, const doub
     const ProbDev& D = hp[i];
     for (int kind = 0; kind < K_NSLOTS; ++kind) P_(kind, i + 1) = P_(kind, i);
     P_(K_SPMV, i + 1) += D.n_chunk_items;
-    P_(K_SPMV_P + pc->sys->p - 1, i + 1) += D.n_chunk_items;
+    P_(K_SPMV_P + pc->sys->p - 1, i + 1) += D.n_spmv_items;
     P_(K_GRP, i + 1) += D.ngrp;
     P_(K_COARSE, i + 1) += D.nq > 0 ? D.n_coarse_items : 0;
     const int slot = 2 * D.prec + (D.kc > 1 ? 1 : 0);

@@ -9,6 +9,7 @@
 namespace dgasm {
 
 constexpr int NTHREADS = 256;  // threads per CTA of the vector kernels
+constexpr int SPMV_THREADS = 128;   // threads per CTA of the SpMV (finer items balance the SMs better)
 constexpr int KMAX = 8;        // right-hand sides per problem
 constexpr int KC = 4;          // right-hand sides per local-solve CTA
 constexpr int SUPER_ROW_MAX = 8;   // tile rows per super-row of the local triangular solves, at most
@@ -27,7 +28,9 @@ enum Counter { C_SPMV = 0, C_GRP = 1, C_PUPD = 2, C_NCOUNTERS = 4 };
 struct ProbDev {
   int ne, np, np2s, nq, ndof, nsub, ngrp, n0, k, prec;
   int epi;            // elements per element-chunk item
-  int n_chunk_items;  // element-chunk items (SpMV, p update)
+  int n_chunk_items;  // element-chunk items (p update, output)
+  int epi_spmv;       // elements per SpMV item
+  int n_spmv_items;   // SpMV items
   int n_coarse_items; // coarse GEMV items (8 rows each)
   int kc;             // right-hand sides per local-solve item
   int n_rhs_chunks;   // ceil(k / kc)
@@ -70,7 +73,7 @@ struct ProbDev {
   int *done, *iters, *status;
   double *alpha_hist, *beta_hist;  // [k][maxit]
   // deterministic partial sums
-  double *part_pq;    // [n_chunk_items][k]
+  double *part_pq;    // [n_spmv_items][k]
   double *part_rr;    // [ngrp][k]
   double *part_rz;    // [nsub][k]
   double *part_c;     // [n_coarse_items][k]

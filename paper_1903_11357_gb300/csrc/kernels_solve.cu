@@ -36,8 +36,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // deterministic CTA sum of k values per thread; result in out[0..k) (shared), all threads synced
-template <int KM>
-__device__ void block_sum_k(const double* v, int k, double* red /*[NW][KMAX]*/, double* out) {
+template <int KM, int NWB = NW>
+__device__ void block_sum_k(const double* v, int k, double* red /*[NWB][KMAX]*/, double* out) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int kk = 0; kk < KM; ++kk) {
@@ -49,7 +49,7 @@ __device__ void block_sum_k(const double* v, int k, double* red /*[NW][KMAX]*/, 
   __syncthreads();
   if (threadIdx.x < k) {
     double s = 0.0;
-    for (int ww = 0; ww < NW; ++ww) s += red[ww * KMAX + threadIdx.x];
+    for (int ww = 0; ww < NWB; ++ww) s += red[ww * KMAX + threadIdx.x];
     out[threadIdx.x] = s;
   }
   __syncthreads();
@@ -85,8 +85,8 @@ __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 // block width NP known at compile time (fully unrolled, two accumulator chains per right-hand side)
 template <int NP, int KM>
 __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operand, const bool* act, double* part) {
-  const int e_begin = item * P.epi;
-  const int nel = min(P.epi, P.ne - e_begin);
+  const int e_begin = item * P.epi_spmv;
+  const int nel = min(P.epi_spmv, P.ne - e_begin);
   const int t = threadIdx.x;
   if (t >= nel * NP) return;
   const int e = e_begin + t / NP, r = t % NP;
@@ -110,6 +110,7 @@ __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operan
       for (int c = 0; c < NP; ++c) acc[kk][c & 1] = fma(a[c], xk[c], acc[kk][c & 1]);
     }
   }
+
   const long long d = (long long)e * NP + r;
 #pragma unroll
   for (int kk = 0; kk < KM; ++kk) {
@@ -127,8 +128,9 @@ __device__ __forceinline__ void spmv_rows(const ProbDev& P, int item, int operan
 
 // ---- SpMV: q = A p (operand 0, with partial (p, q)) or q = A x and (b - A x)^2 (operand 1) ------
 template <int NP, int KM>
-__global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand, int slot) {
-  __shared__ double red[NW * KMAX];
+__global__ void __launch_bounds__(SPMV_THREADS) k_spmv(BatchDev B, int operand, int slot) {
+  constexpr int SW = SPMV_THREADS / 32;
+  __shared__ double red[SW * KMAX];
   __shared__ double tot[KMAX];
   __shared__ int lastf;
   const int pi = find_prob(B.prefix[slot], B.nprob, blockIdx.x);
@@ -146,17 +148,16 @@ __global__ void __launch_bounds__(NTHREADS) k_spmv(BatchDev B, int operand, int 
 #pragma unroll
   for (int kk = 0; kk < KM; ++kk) part[kk] = 0.0;
   if (any) spmv_rows<NP, KM>(P, item, operand, act, part);
-  block_sum_k<KM>(part, k, red, tot);
+  block_sum_k<KM, SW>(part, k, red, tot);
   if (threadIdx.x < k) P.part_pq[(long long)item * k + threadIdx.x] = tot[threadIdx.x];
-  if (!last_block(&P.counters[C_SPMV], P.n_chunk_items, &lastf)) return;
-  if ((threadIdx.x >> 5) < k) {
-    const int kk = threadIdx.x >> 5;
-    if (!act[kk]) return;
-    const double s = warp_sum_strided(P.part_pq + kk, P.n_chunk_items, k);
-    if ((threadIdx.x & 31) != 0) return;
+  if (!last_block(&P.counters[C_SPMV], P.n_spmv_items, &lastf)) return;
+  for (int kk = threadIdx.x >> 5; kk < k; kk += SW) {
+    if (!act[kk]) continue;
+    const double s = warp_sum_strided(P.part_pq + kk, P.n_spmv_items, k);
+    if ((threadIdx.x & 31) != 0) continue;
     if (operand == 1) {
       P.true_rr[kk] = P.bnorm[kk] > 0.0 ? sqrt(s) / P.bnorm[kk] : 0.0;
-      return;
+      continue;
     }
     double alpha = P.gamma[kk] / s;
     if (!(s > 0.0) || !finite_d(alpha)) {
@@ -492,14 +493,14 @@ template <int KM>
 int launch_spmv_k(const BatchDev& B, int p, int total, int operand, cudaStream_t s) {
   const int slot = K_SPMV_P + p - 1;
   switch (p) {
-    case 1: k_spmv<3, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 2: k_spmv<6, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 3: k_spmv<10, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 4: k_spmv<15, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 5: k_spmv<21, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 6: k_spmv<28, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    case 7: k_spmv<36, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
-    default: k_spmv<45, KM><<<total, NTHREADS, 0, s>>>(B, operand, slot); break;
+    case 1: k_spmv<3, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
+    case 2: k_spmv<6, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
+    case 3: k_spmv<10, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
+    case 4: k_spmv<15, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
+    case 5: k_spmv<21, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
+    case 6: k_spmv<28, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
+    case 7: k_spmv<36, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
+    default: k_spmv<45, KM><<<total, SPMV_THREADS, 0, s>>>(B, operand, slot); break;
   }
   return (int)cudaGetLastError();
 }

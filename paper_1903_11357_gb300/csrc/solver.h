@@ -25,7 +25,7 @@ struct EnvBufs {
 struct Workspace {
   DevBuf buf;
   int k = 0, maxit = 0;
-  int n_chunk_items = 0, n_coarse_items = 0;
+  int n_chunk_items = 0, n_spmv_items = 0, n_coarse_items = 0;
   size_t o_vec = 0, o_coarse = 0, o_scal = 0, o_int = 0, o_hist = 0, o_ppq = 0, o_prr = 0, o_prz = 0, o_pc = 0, o_cnt = 0;
   int ensure(const dgasm_prec_s& pc, int k, int maxit);
   void fill(const dgasm_prec_s& pc, ProbDev& D, int k, const double* b_user, double* x_user, int maxit, int fixed,
