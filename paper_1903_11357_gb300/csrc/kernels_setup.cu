@@ -16,9 +16,9 @@ constexpr int TT = T * T;
 template <typename S> struct Compute { using type = float; };
 template <> struct Compute<double> { using type = double; };
 
-template <typename C> __device__ __forceinline__ C csqrt(C x);
-template <> __device__ __forceinline__ double csqrt<double>(double x) { return sqrt(x); }
-template <> __device__ __forceinline__ float csqrt<float>(float x) { return sqrtf(x); }
+template <typename C> __device__ __forceinline__ C crsqrt(C x);
+template <> __device__ __forceinline__ double crsqrt<double>(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float crsqrt<float>(float x) { return rsqrtf(x); }
 
 __device__ __forceinline__ long long tile_index(const EnvDev& E, int s, int I, int J) {
   int tr = E.sub_trow[s] + I;
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, 
   using C = typename Compute<S>::type;
   __shared__ C a[T][T + 1];
   __shared__ C inv[T][T + 1];
+  __shared__ C rdj;
   __shared__ int bad;
   int s = tasks[blockIdx.x];
   long long ti = tile_index(E, s, K, K);
@@ -101,38 +102,37 @@ __global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, 
   for (int t = tid; t < TT; t += blockDim.x) {
     int r = t / T, c = t % T;
     a[r][c] = (r >= c) ? (C)tile[t] : (C)0;
+    inv[r][c] = (r == c) ? (C)1 : (C)0;
   }
   __syncthreads();
-  __shared__ C rdiag[T];   // 1 / L_jj
+  // Right-looking Cholesky of the tile, and in the same sweep the inverse X = inv(L) by forward
+  // elimination of L X = I: once column j of L is known, row j of X is final and the rows below it take
+  // their update from it.  Each step is parallel over the entries it touches (one warp per tile is
+  // slower: the FP64 pipe spends its slots on the lanes a triangular step leaves idle).
   for (int j = 0; j < T; ++j) {
     if (tid == 0) {
       C d = a[j][j];
       if (!(d > (C)0)) { if (bad < 0) bad = j; d = (C)1; }
-      d = csqrt<C>(d);
-      a[j][j] = d;
-      rdiag[j] = (C)1 / d;
+      const C rd = crsqrt<C>(d);
+      a[j][j] = d * rd;   // sqrt(d)
+      rdj = rd;
     }
     __syncthreads();
-    if (tid > j && tid < T) a[tid][j] *= rdiag[j];
+    const C rd = rdj;
+    // column j of L and row j of X (X_jc, c <= j)
+    if (tid < T) {
+      if (tid > j) a[tid][j] *= rd;
+      if (tid <= j) inv[j][tid] *= rd;
+    }
     __syncthreads();
+    // trailing update of A (c > j, r >= c) and of the rows of X below j (r > j, c <= j)
     for (int t = tid; t < TT; t += blockDim.x) {
-      int r = t / T, c = t % T;
+      const int r = t / T, c = t % T;
       if (c > j && r >= c) a[r][c] -= a[r][j] * a[c][j];
+      else if (r > j && c <= j) inv[r][c] -= a[r][j] * inv[j][c];
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular factor, one column per thread
-  if (tid < T) {
-    int c = tid;
-    for (int r = 0; r < c; ++r) inv[r][c] = (C)0;
-    inv[c][c] = rdiag[c];
-    for (int r = c + 1; r < T; ++r) {
-      C acc = (C)0;
-      for (int m = c; m < r; ++m) acc += a[r][m] * inv[m][c];
-      inv[r][c] = -acc * rdiag[r];
-    }
-  }
-  __syncthreads();
   for (int t = tid; t < TT; t += blockDim.x) tile[t] = (S)inv[t / T][t % T];
   if (tid == 0 && bad >= 0) {
     // record the first failure: subdomain and pivot row
