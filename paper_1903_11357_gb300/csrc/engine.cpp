@@ -68,6 +68,8 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.trow_ptr = pc.env.trow_ptr.as<long long>(); D.fwd_ptr = pc.env.fwd_ptr.as<long long>();
   D.bwd_ptr = pc.env.bwd_ptr.as<long long>();
   D.sr = pc.P.env.sr;
+  D.dinv = pc.blocks ? pc.dinv.as<double>() : nullptr;
+  D.n_rz = pc.blocks ? n_chunk_items : P.nsub;
   D.sub_sr = pc.env.sub_sr.as<int>(); D.fwd_run = pc.env.fwd_run.as<int>(); D.bwd_run = pc.env.bwd_run.as<int>();
   D.Lr = pc.Lr.ptr; D.Lc = pc.Lc.ptr; D.scale = pc.scale.as<double>();
   D.fwd_total = (long long)pc.P.env.fwd_src.size();
@@ -144,11 +146,15 @@ int Engine::build(int n, dgasm_prec_s* const* pcs_, const int* nrhs_, const doub
     P_(K_SPMV_P + pc->sys->p - 1, i + 1) += D.n_spmv_items;
     P_(K_GRP, i + 1) += D.ngrp;
     P_(K_COARSE, i + 1) += D.nq > 0 ? D.n_coarse_items : 0;
-    const int slot = 2 * D.prec + (D.kc > 1 ? 1 : 0);
-    P_(K_NKINDS + slot, i + 1) += D.nsub * D.n_rhs_chunks;
-    int maxn = 0;
-    for (int sdx = 0; sdx < pc->P.nsub; ++sdx) maxn = std::max(maxn, pc->P.env.ndof[sdx]);
-    max_smem[slot] = std::max(max_smem[slot], local_smem_bytes(D.prec, maxn, D.kc));
+    if (pc->blocks) {
+      P_(K_BJAC, i + 1) += D.n_chunk_items;
+    } else {
+      const int slot = 2 * D.prec + (D.kc > 1 ? 1 : 0);
+      P_(K_NKINDS + slot, i + 1) += D.nsub * D.n_rhs_chunks;
+      int maxn = 0;
+      for (int sdx = 0; sdx < pc->P.nsub; ++sdx) maxn = std::max(maxn, pc->P.env.ndof[sdx]);
+      max_smem[slot] = std::max(max_smem[slot], local_smem_bytes(D.prec, maxn, D.kc));
+    }
   }
   tot_spmv = P_(K_SPMV, n);
   tot_grp = P_(K_GRP, n);
@@ -218,6 +224,9 @@ int Engine::precond(int mode, EventPairs* ev) {
       DG_CUDA(timed_launch(PK_LOCAL, stream, ev, launches,
                            [&] { return launch_local(B, K_NKINDS + slot, tot, max_smem[slot], stream); }));
   }
+  const int tot_bjac = pre[K_BJAC * (n + 1) + n];
+  if (tot_bjac)
+    DG_CUDA(timed_launch(PK_LOCAL, stream, ev, launches, [&] { return launch_bjac(B, tot_bjac, km, stream); }));
   DG_CUDA(cudaStreamWaitEvent(stream, ev_join, 0));
   DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, km, stream); }));
   return DGASM_OK;

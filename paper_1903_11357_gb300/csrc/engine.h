@@ -21,7 +21,8 @@ constexpr long long ZERO_TILE = -(1LL << 62);   // solve-stream entry: a tile of
 
 enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
 constexpr int K_SPMV_P = K_NKINDS + 8;   // per-degree SpMV prefix slots p = 1..8
-constexpr int K_NSLOTS = K_SPMV_P + 8;
+constexpr int K_BJAC = K_SPMV_P + 8;     // element-block local solves (subdomains = elements)
+constexpr int K_NSLOTS = K_BJAC + 1;
 enum Counter { C_SPMV = 0, C_GRP = 1, C_PUPD = 2, C_NCOUNTERS = 4 };
 
 // One problem (one preconditioner with k right-hand sides) of a batch.
@@ -50,6 +51,8 @@ struct ProbDev {
   const long long* bwd_ptr;     // [nsub+1] and in the backward stream
   long long fwd_total, bwd_total;  // tiles in each stream (all subdomains)
   int sr;                       // tile rows per super-row of the local factors
+  const double* dinv;           // subdomains = elements: [ne][np][np] inverses of the diagonal blocks, row-major
+  int n_rz;                     // partial sums of (r, z): nsub (envelope solves) or n_chunk_items (blocks)
   const int* sub_sr;            // [nsub+1] first global super-row of each subdomain
   const int* fwd_run;           // [global super-row][sr][2]: coupling runs (first operand block, tiles)
   const int* bwd_run;
@@ -100,6 +103,8 @@ int launch_spmv(const BatchDev& B, int p, int total, int operand /*0: q = A p, 1
 int launch_update(const BatchDev& B, int total, int mode, int km, void* stream);
 int launch_local(const BatchDev& B, int slot, int total, int smem_bytes, void* stream);
 int launch_coarse(const BatchDev& B, int total, int km, void* stream);
+// element-block local solves z_e = inv(A_ee) r_e with the partial (r, z) per chunk item
+int launch_bjac(const BatchDev& B, int total, int km, void* stream);
 int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* stream);
 int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);
 // dynamic shared memory of a local-solve launch over subdomains of at most ndof_max dofs
@@ -135,6 +140,9 @@ int launch_dinv(int prec, const EnvDev& E, const void* L, const int* task, const
 // solve streams from factor tiles (src >= 0) and inverse-block tiles (src < 0)
 int launch_stream_gather(int prec, const void* L, const void* X, const long long* src, void* dst, long long n,
                          int transpose, void* stream);
+// subdomains = elements: inverses of the diagonal blocks [ne][np][np] (err as the Cholesky kernels)
+int launch_bjac_inverse(const int* rowptr, const int* col, const double* vals, int ne, int np, int np2s, double* dinv,
+                        int* err, void* stream);
 int launch_r0t(const int* perm, const double* bbox, const int* agg_int, const double* agg_bbox, int ne, int p, int q,
                const double* gl_t, const double* gl_w, int mq, double* r0t, void* st);
 // W: nnzb * nq * nq doubles of scratch

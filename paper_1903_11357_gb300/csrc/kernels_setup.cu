@@ -322,6 +322,56 @@ __device__ void legendre_dev(int p, double t, double* L, double* dL) {
   }
 }
 
+// Subdomains = elements (Sec. 7's setting): the inverse of each diagonal block A_ee, one warp per element,
+// by Gauss-Jordan elimination without pivoting (A_ee is SPD, so every pivot is positive; a non-positive
+// pivot is recorded like a failed Cholesky).  Output row-major [ne][np][np].
+constexpr int BJAC_WARPS = 4;
+__global__ void k_bjac_inverse(const int* __restrict__ rowptr, const int* __restrict__ col,
+                               const double* __restrict__ vals, int ne, int np, int np2s, double* __restrict__ dinv,
+                               int* __restrict__ err) {
+  extern __shared__ double bsm[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * BJAC_WARPS + wid;
+  if (e >= ne) return;
+  const int ld = np + 1;
+  double* A = bsm + (size_t)wid * (np * ld + np);   // [np][np + 1]
+  double* f = A + np * ld;                          // [np]: column k before its elimination step
+  // the diagonal block: the entry of row e whose column is e
+  int kd = -1;
+  for (int k = rowptr[e] + lane; k < rowptr[e + 1]; k += 32)
+    if (col[k] == e) kd = k;
+  for (int o = 16; o > 0; o >>= 1) kd = max(kd, __shfl_xor_sync(0xffffffffu, kd, o));
+  const double* Bk = vals + (long long)kd * np2s;   // column-major: entry (r, c) at c * np + r
+  for (int t = lane; t < np * np; t += 32) A[(t % np) * ld + t / np] = Bk[t];
+  __syncwarp();
+  int bad = -1;
+  for (int k = 0; k < np; ++k) {
+    double p = A[k * ld + k];
+    if (!(p > 0.0)) {
+      if (bad < 0) bad = k;
+      p = 1.0;
+    }
+    const double rp = 1.0 / p;
+    for (int i = lane; i < np; i += 32) f[i] = A[i * ld + k];
+    __syncwarp();
+    for (int j = lane; j < np; j += 32) A[k * ld + j] = (j == k ? 1.0 : A[k * ld + j]) * rp;
+    __syncwarp();
+    for (int t = lane; t < np * np; t += 32) {
+      const int i = t / np, j = t % np;
+      if (i == k) continue;
+      A[i * ld + j] = (j == k ? 0.0 : A[i * ld + j]) - f[i] * A[k * ld + j];
+    }
+    __syncwarp();
+  }
+  double* out = dinv + (long long)e * np * np;
+  for (int t = lane; t < np * np; t += 32) out[t] = A[(t / np) * ld + t % np];
+  if (lane == 0 && (bad >= 0 || kd < 0)) {
+    atomicCAS(&err[0], 0, 1);
+    atomicCAS(&err[1], -1, e);
+    atomicCAS(&err[2], -1, bad >= 0 ? bad : 0);
+  }
+}
+
 // R_0^T|_kappa = M_kappa^{-1} N_kappa (Eq. R0T) for nested agglomerates: the coarse basis functions are
 // polynomials of total degree q <= p, so (Remark 3.1) M^{-1} N holds the exact coefficients of their
 // restrictions in the element's basis, whatever domain the two mass matrices are integrated on.  On the
@@ -536,6 +586,18 @@ int launch_stream_gather(int prec, const void* L, const void* X, const long long
 
 int launch_to_bf16(const float* src, void* dst, long long n, void* st) {
   k_to_bf16<<<grid_for(n, 256), 256, 0, (cudaStream_t)st>>>(src, (__nv_bfloat16*)dst, n);
+  return (int)cudaGetLastError();
+}
+
+int launch_bjac_inverse(const int* rowptr, const int* col, const double* vals, int ne, int np, int np2s, double* dinv,
+                        int* err, void* st) {
+  const size_t smem = sizeof(double) * (size_t)BJAC_WARPS * (np * (np + 1) + np);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bjac_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  k_bjac_inverse<<<(ne + BJAC_WARPS - 1) / BJAC_WARPS, 32 * BJAC_WARPS, smem, (cudaStream_t)st>>>(rowptr, col, vals, ne, np, np2s,
+                                                                                              dinv, err);
   return (int)cudaGetLastError();
 }
 

@@ -380,6 +380,46 @@ __global__ void __launch_bounds__(NTHREADS) k_coarse(BatchDev B) {
   }
 }
 
+// ---- element-block local solves (subdomains = elements, Sec. 7's setting): z_e = inv(A_ee) r_e with
+// the inverses precomputed at setup; one thread per (element, row), partial (r, z) per chunk item --------
+template <int KM>
+__global__ void __launch_bounds__(NTHREADS) k_bjac(BatchDev B) {
+  __shared__ double red[NW * KMAX];
+  __shared__ double tot[KMAX];
+  const int pi = find_prob(B.prefix[K_BJAC], B.nprob, blockIdx.x);
+  const ProbDev& P = B.probs[pi];
+  const int item = blockIdx.x - B.prefix[K_BJAC][pi];
+  const int k = P.k, np = P.np;
+  bool act[KM];
+  bool any = false;
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk) {
+    act[kk] = kk < k && P.done[kk] == 0;
+    any |= act[kk];
+  }
+  double prz[KM];
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk) prz[kk] = 0.0;
+  const int e_begin = item * P.epi;
+  const int nel = min(P.epi, P.ne - e_begin);
+  const int t = threadIdx.x;
+  if (any && t < nel * np) {
+    const int e = e_begin + t / np, a = t % np;
+    const double* Dr = P.dinv + ((long long)e * np + a) * np;   // row a of inv(A_ee)
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) {
+      if (!act[kk]) continue;
+      const double* rv = P.r + kk * (long long)P.ndof + (long long)e * np;
+      double z = 0.0;
+      for (int c = 0; c < np; ++c) z = fma(Dr[c], rv[c], z);
+      P.z[kk * (long long)P.ndof + (long long)e * np + a] = z;
+      prz[kk] = rv[a] * z;
+    }
+  }
+  block_sum_k<KM>(prz, k, red, tot);
+  if (threadIdx.x < k) P.part_rz[(long long)item * k + threadIdx.x] = P.done[threadIdx.x] == 0 ? tot[threadIdx.x] : 0.0;
+}
+
 // ---- p = z + R_0^T z_0 + beta p, beta = (r, z)_new / (r, z)_old ----------------------------------
 template <int KM>
 __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
@@ -401,7 +441,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
     const int kk = threadIdx.x >> 5;
     double g = 0.0;
     if (act[kk]) {
-      g = warp_sum_strided(P.part_rz + kk, P.nsub, k);
+      g = warp_sum_strided(P.part_rz + kk, P.n_rz, k);
       if (nq > 0) g += warp_sum_strided(P.part_c + kk, P.n_coarse_items, k);
     }
     if ((threadIdx.x & 31) == 0) {
@@ -521,6 +561,12 @@ int launch_update(const BatchDev& B, int total, int mode, int km, void* st) {
 int launch_coarse(const BatchDev& B, int total, int km, void* st) {
   if (km == 1) k_coarse<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
   else k_coarse<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
+  return (int)cudaGetLastError();
+}
+
+int launch_bjac(const BatchDev& B, int total, int km, void* st) {
+  if (km == 1) k_bjac<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
+  else k_bjac<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
   return (int)cudaGetLastError();
 }
 

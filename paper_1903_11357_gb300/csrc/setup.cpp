@@ -184,18 +184,27 @@ int prec_build(dgasm_prec_s* pc) {
   DG_TRY(pc->scale.alloc(sizeof(double) * (size_t)ne * np));
   DG_CUDA(launch_scale(pc->rowptr.as<int>(), pc->col.as<int>(), pc->vals.as<double>(), ne, np, np2s, pc->scale.as<double>(), st));
   // local factors
-  const int fprec = pc->precision;
-  const size_t ftiles = (size_t)P.env.ntiles * TILE * TILE;
-  DevBuf Lf;  // factorisation pool (row-major)
-  DG_TRY(Lf.alloc(ftiles * fact_elem_bytes(fprec)));
-  DG_CUDA(cudaMemsetAsync(Lf.ptr, 0, Lf.bytes, st));
-  DG_CUDA(launch_extract_rows(fprec == DGASM_FP64 ? 0 : 1, pc->env.dev, pc->sub_e0.as<int>(), pc->rowptr.as<int>(),
-                              pc->col.as<int>(), pc->vals.as<double>(), np, np2s, pc->scale.as<double>(), Lf.ptr,
-                              P.nsub, ne, st));
-  nl += 1;
-  DG_TRY(factor_env(fprec, P.env, pc->env, Lf.ptr, pc->err.as<int>(), st, ev, &nl));
-  // super-row inverse blocks, then the forward (column-major) and backward (row-major) solve streams
-  DG_TRY(build_streams(fprec, P.env, pc->env, Lf, pc->Lc, pc->Lr, st, &nl));
+  pc->blocks = P.nsub == P.ne;
+  if (pc->blocks) {
+    // every subdomain is one element: explicit FP64 inverses of the diagonal blocks
+    DG_TRY(pc->dinv.alloc(sizeof(double) * (size_t)ne * np * np));
+    DG_CUDA(launch_bjac_inverse(pc->rowptr.as<int>(), pc->col.as<int>(), pc->vals.as<double>(), ne, np, np2s,
+                                pc->dinv.as<double>(), pc->err.as<int>(), st));
+    nl += 1;
+  } else {
+    const int fprec = pc->precision;
+    const size_t ftiles = (size_t)P.env.ntiles * TILE * TILE;
+    DevBuf Lf;  // factorisation pool (row-major)
+    DG_TRY(Lf.alloc(ftiles * fact_elem_bytes(fprec)));
+    DG_CUDA(cudaMemsetAsync(Lf.ptr, 0, Lf.bytes, st));
+    DG_CUDA(launch_extract_rows(fprec == DGASM_FP64 ? 0 : 1, pc->env.dev, pc->sub_e0.as<int>(), pc->rowptr.as<int>(),
+                                pc->col.as<int>(), pc->vals.as<double>(), np, np2s, pc->scale.as<double>(), Lf.ptr,
+                                P.nsub, ne, st));
+    nl += 1;
+    DG_TRY(factor_env(fprec, P.env, pc->env, Lf.ptr, pc->err.as<int>(), st, ev, &nl));
+    // super-row inverse blocks, then the forward (column-major) and backward (row-major) solve streams
+    DG_TRY(build_streams(fprec, P.env, pc->env, Lf, pc->Lc, pc->Lr, st, &nl));
+  }
   // coarse space: R_0^T, A_0 = R_0 A R_0^T, FP64 factor and explicit inverse
   if (pc->n0 > 0) {
     const int n0 = pc->n0, q = P.q, nq = P.nq, mq = (s->p + q + 2) / 2;
@@ -329,7 +338,7 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
 
 size_t dgasm_prec_s::footprint() const {
   size_t b = perm.bytes + rowptr.bytes + col.bytes + vals.bytes + sub_e0.bytes + scale.bytes + Lr.bytes + Lc.bytes +
-             grp_ptr.bytes + grp_elems.bytes + agg_int.bytes + r0t.bytes + A0inv.bytes + err.bytes;
+             grp_ptr.bytes + grp_elems.bytes + agg_int.bytes + r0t.bytes + A0inv.bytes + err.bytes + dinv.bytes;
   const EnvBufs* es[2] = {&env, &env0};
   for (const EnvBufs* e : es)
     b += e->ndof.bytes + e->sub_trow.bytes + e->trow_F.bytes + e->trow_ptr.bytes + e->diag_task.bytes +
@@ -361,7 +370,7 @@ extern "C" int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info) {
   info->precision = pc->precision;
   info->local_dofs = (int64_t)P.ne * P.np;
   info->local_tiles = P.env.ntiles;
-  info->stream_tiles = (int64_t)(P.env.fwd_src.size() + P.env.bwd_src.size());
+  info->stream_tiles = pc->blocks ? 0 : (int64_t)(P.env.fwd_src.size() + P.env.bwd_src.size());
   int64_t upd = (int64_t)P.env.upd_task.size() / 3, pan = (int64_t)P.env.panel_task.size() / 2, dg = (int64_t)P.env.diag_task.size();
   const int64_t t3 = (int64_t)TILE * TILE * TILE;
   info->factor_flops = upd * 2 * t3 + pan * t3 + dg * (t3 / 3 + t3 / 3);

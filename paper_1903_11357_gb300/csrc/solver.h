@@ -101,6 +101,8 @@ struct dgasm_prec_s {
   cudaStream_t stream = nullptr, own_stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   dgasm::DevBuf perm, rowptr, col, vals, src_blk, sub_e0, scale, Lr, Lc, grp_ptr, grp_elems, agg_int, r0t, A0inv, err, io;
+  bool blocks = false;      // every subdomain is one element: local solves with explicit block inverses
+  dgasm::DevBuf dinv;       // [ne][np][np] FP64, internal element order
   dgasm::EnvBufs env, env0;
   dgasm::Workspace ws;
   dgasm::EventPairs setup_ev;

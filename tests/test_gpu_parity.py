@@ -62,6 +62,40 @@ def test_preconditioner_apply_matches_oracle(n, p, nsub, ncoarse, q):
     assert np.linalg.norm(z.cpu().numpy() - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("n,p,ncoarse,q", [(256, 2, 16, 1), (200, 3, 8, 2), (120, 1, 0, 1)])
+def test_element_blocks_apply_matches_oracle(n, p, ncoarse, q):
+    """Subdomains = elements (the setting of the paper's experiments): explicit inverses of the
+    diagonal blocks instead of envelope factors."""
+    c = build_case(n, 5, p, n, ncoarse, q)
+    assert c["P"].info()["stream_tiles"] == 0
+    r = np.random.default_rng(2).standard_normal(c["A"].shape[0])
+    z = torch.zeros_like(dev(r))
+    c["P"].apply(dev(r), z)
+    torch.cuda.synchronize()
+    ref = c["O"].apply(r)
+    assert np.linalg.norm(z.cpu().numpy() - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_element_blocks_solve_parity():
+    c = build_case(256, 1, 2, 256, 16)
+    ref = pcg.pcg(c["A"], c["b"], c["O"].apply, rtol=1e-8)
+    x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
+    rc, st = c["P"].solve(dev(c["b"]), x, rtol=1e-8)
+    assert rc == 0 and st[0]["converged"] and abs(st[0]["iters"] - ref.iters) <= 1
+    assert st[0]["true_relres"] <= 1e-8
+    rc, st2 = c["P"].solve(dev(c["b"]), x, fixed_iters=ref.iters)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    assert st[0]["kappa"] == pytest.approx(pcg.condition_estimate(ref), rel=0.05)
+    # two right-hand sides through the same block inverses
+    B = np.random.default_rng(3).standard_normal((2, len(c["b"])))
+    X = torch.zeros(2, len(c["b"]), dtype=torch.float64, device="cuda")
+    rc, stm = c["P"].solve(dev(B), X, rtol=1e-8)
+    assert rc == 0
+    for j in range(2):
+        xs = np.linalg.solve(c["A"].toarray(), B[j])
+        assert np.linalg.norm(X[j].cpu().numpy() - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
 def test_partition_used_matches_oracle():
     c = build_case(256, 1, 2, 4, 16)
     sub, agg = c["P"].partition()
@@ -163,7 +197,9 @@ def test_zero_rhs_and_one_subdomain():
 
 
 def test_batch_equals_alone():
-    cases = [build_case(256, 1, 2, 4, 16), build_case(300, 2, 3, 4, 8), build_case(200, 3, 1, 2, 8)]
+    # the third problem runs with subdomains = elements (block inverses) next to two envelope problems
+    cases = [build_case(256, 1, 2, 4, 16), build_case(300, 2, 3, 4, 8), build_case(200, 3, 1, 2, 8),
+             build_case(180, 4, 2, 180, 12)]
     xs_alone = []
     for c in cases:
         x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
