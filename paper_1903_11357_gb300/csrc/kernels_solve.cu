@@ -19,6 +19,10 @@ namespace {
 constexpr int T = 32;
 constexpr int TT = T * T;
 constexpr int NW = NTHREADS / 32;
+// the x / r update runs one CTA per element group (an agglomerate, about 64 elements); 512 threads per CTA
+// measured slower than 256 (the kernel's time is its serial tail, not the pass over the group)
+constexpr int UPD_THREADS = 256;
+constexpr int UPD_NW = UPD_THREADS / 32;
 
 __device__ __forceinline__ int find_prob(const int* __restrict__ prefix, int nprob, int item) {
   int lo = 0, hi = nprob;  // prefix[lo] <= item < prefix[hi]
@@ -172,9 +176,9 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv(BatchDev B, int operand, 
 
 // ---- x/r update (or initial residual) with partial ||r||^2 and the coarse restriction ----------
 template <int KM>
-__global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
-  __shared__ double red4[NW][KMAX][4];
-  __shared__ double red[NW * KMAX];
+__global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
+  __shared__ double red4[UPD_NW][KMAX][4];
+  __shared__ double red[UPD_NW * KMAX];
   __shared__ double tot[KMAX];
   __shared__ int lastf;
   const int pi = find_prob(B.prefix[K_GRP], B.nprob, blockIdx.x);
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
   }
   const bool fused_r0 = nq == NQ1;
   const bool restrict_ = nq > 0;
-  for (int base = 0; base < nd && any; base += NTHREADS) {
+  for (int base = 0; base < nd && any; base += UPD_THREADS) {
     const int t = base + threadIdx.x;
     if (t >= nd) break;
     const int e = P.grp_elems[g0 + t / np], a = t % np;
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
     if (threadIdx.x < k * nv) {
       const int kk = threadIdx.x / nv, c = threadIdx.x % nv;
       double v = 0.0;
-      for (int ww = 0; ww < NW; ++ww) v += red4[ww][kk][c];
+      for (int ww = 0; ww < UPD_NW; ++ww) v += red4[ww][kk][c];
       if (c == 0) P.part_rr[(long long)g * k + kk] = v;
       else if (act[kk]) P.r0[(long long)kk * P.n0 + g * nq + c - 1] = v;
     }
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
       double v[KM];
 #pragma unroll
       for (int kk = 0; kk < KM; ++kk) v[kk] = 0.0;
-      for (int base = 0; base < nd; base += NTHREADS) {
+      for (int base = 0; base < nd; base += UPD_THREADS) {
         const int t = base + threadIdx.x;
         if (t >= nd) break;
         const int e = P.grp_elems[g0 + t / np], a = t % np;
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(NTHREADS) k_update(BatchDev B, int mode) {
         for (int kk = 0; kk < KM; ++kk)
           if (act[kk]) v[kk] = fma(wv, P.r[kk * (long long)P.ndof + (long long)e * np + a], v[kk]);
       }
-      block_sum_k<KM>(v, k, red, tot);
+      block_sum_k<KM, UPD_NW>(v, k, red, tot);
       if (threadIdx.x < k && act[threadIdx.x]) P.r0[(long long)threadIdx.x * P.n0 + g * nq + c] = tot[threadIdx.x];
     }
   }
@@ -553,8 +557,8 @@ int launch_spmv(const BatchDev& B, int p, int total, int operand, int km, void* 
 }
 
 int launch_update(const BatchDev& B, int total, int mode, int km, void* st) {
-  if (km == 1) k_update<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
-  else k_update<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
+  if (km == 1) k_update<1><<<total, UPD_THREADS, 0, (cudaStream_t)st>>>(B, mode);
+  else k_update<KMAX><<<total, UPD_THREADS, 0, (cudaStream_t)st>>>(B, mode);
   return (int)cudaGetLastError();
 }
 
