@@ -234,7 +234,7 @@ int Engine::precond(int mode, EventPairs* ev) {
 
 int Engine::init(bool x0) {
   init_ev.reset();
-  lanczos_len.assign(nprob, std::vector<int>());
+  for (int i = 0; i < nprob; ++i) pcs[i]->ws.lanczos_len.assign(pcs[i]->ws.k, -1);
   if (!x0) {
     DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT, km, stream); }));
   } else {
@@ -273,8 +273,9 @@ int Engine::restart(int* count) {
     for (int kk = 0; kk < nrhs[i]; ++kk) {
       const double true_rr = sc[4 * (size_t)wk + kk];
       if (iv[kk] == 1 && true_rr > D.rtol && iv[wk + kk] < D.maxit && std::isfinite(true_rr)) {
-        if (lanczos_len[i].empty()) lanczos_len[i].assign(wk, -1);
-        if (lanczos_len[i][kk] < 0) lanczos_len[i][kk] = iv[wk + kk];
+        std::vector<int>& ll = pcs[i]->ws.lanczos_len;
+        if ((int)ll.size() < wk) ll.resize(wk, -1);
+        if (ll[kk] < 0) ll[kk] = iv[wk + kk];
         iv[kk] = 0;
         any = true;
         ++*count;
@@ -392,7 +393,8 @@ int Engine::collect(dgasm_stats* st, double ms, std::vector<int>* rcs) {
       s.lambda_min = s.lambda_max = s.kappa = NAN;
       int nh = std::min(iters, D.maxit);
       // after a residual replacement the coefficients of the first CG run give the Lanczos estimate
-      if (!lanczos_len.empty() && !lanczos_len[i].empty() && lanczos_len[i][kk] >= 0) nh = std::min(nh, lanczos_len[i][kk]);
+      const std::vector<int>& ll = pcs[i]->ws.lanczos_len;
+      if (kk < (int)ll.size() && ll[kk] >= 0) nh = std::min(nh, ll[kk]);
       if (nh >= 1) {
         std::vector<double> al(nh), be(std::max(nh - 1, 1));
         DG_CUDA(cudaMemcpy(al.data(), D.alpha_hist + (size_t)kk * D.maxit, sizeof(double) * nh, cudaMemcpyDeviceToHost));

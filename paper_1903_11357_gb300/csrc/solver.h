@@ -26,6 +26,9 @@ struct Workspace {
   DevBuf buf;
   int k = 0, maxit = 0;
   int n_chunk_items = 0, n_spmv_items = 0, n_coarse_items = 0;
+  // per right-hand side: iterations of the first CG run when a residual replacement restarted it (-1:
+  // none); kept with the problem, so it survives the engine being rebuilt for other batches
+  std::vector<int> lanczos_len;
   size_t o_vec = 0, o_coarse = 0, o_scal = 0, o_int = 0, o_hist = 0, o_ppq = 0, o_prr = 0, o_prz = 0, o_pc = 0, o_cnt = 0;
   int ensure(const dgasm_prec_s& pc, int k, int maxit);
   void fill(const dgasm_prec_s& pc, ProbDev& D, int k, const double* b_user, double* x_user, int maxit, int fixed,
@@ -36,7 +39,6 @@ struct Workspace {
 // a captured graph of CHUNK iterations, and the event pairs used when profiling.
 struct Engine {
   static constexpr int CHUNK = 8;
-  std::vector<std::vector<int>> lanczos_len;   // per problem and rhs: iterations of the first CG run
   int nprob = 0;
   std::vector<dgasm_prec_s*> pcs;
   std::vector<int> nrhs;

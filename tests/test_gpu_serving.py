@@ -89,3 +89,27 @@ def test_cancel_queued_request():
     for t in ts[:-1]:
         assert sv.wait(t, 60000)[0] == 0
     sv.close()
+
+
+def test_restarts_from_the_true_residual_in_the_mix():
+    """A tight tolerance makes the recursive residual run ahead of b - A x, so requests restart from the
+    true residual (residual replacement) while others come and go; each result still equals the solve
+    alone and meets the tolerance in both senses."""
+    cases = [(300, 21, 3, 4, 16, 1), (400, 22, 2, 4, 16, 2), (250, 23, 3, 2, 8, 1), (350, 24, 2, 4, 8, 3)]
+    systems = [make_system(n, s, p) for (n, s, p, *_) in cases]
+    bs = [rhs(S, c[5], 30 + i) for i, (S, c) in enumerate(zip(systems, cases))]
+    refs = []
+    for S, c, b in zip(systems, cases, bs):
+        P = dg.Prec(S, c[3], c[4], 1)
+        x = torch.zeros_like(b)
+        rc, st = P.solve(b, x, rtol=1e-12)
+        assert rc == 0 and all(s["true_relres"] <= 1e-12 for s in st)
+        refs.append(x)
+    sv = dg.Server(hbm_budget=8 << 30, max_slots=2)
+    xs = [torch.zeros_like(b) for b in bs]
+    tickets = [sv.submit(S, c[3], c[4], 1, b, x, rtol=1e-12) for S, c, b, x in zip(systems, cases, bs, xs)]
+    for t, x, ref in zip(tickets, xs, refs):
+        rc, st = sv.wait(t, 60000)
+        assert rc == 0 and all(s["converged"] and s["true_relres"] <= 1e-12 for s in st)
+        assert torch.equal(x, ref)
+    sv.close()
