@@ -479,6 +479,18 @@ def run_paper(args):
     print(json.dumps(out), flush=True)
 
 
+def slowest_rank_seconds(elapsed, world, device="cpu"):
+    """Replicas: every rank solves its own copy of the workload; the job's time is the slowest rank's
+    (max over ranks, the same on every rank), and the whole-job value is world * steps / that time."""
+    if world <= 1:
+        return float(elapsed)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def profiled_step(dg, step, barrier, precision):
     """One untimed step with every kernel kind bracketed by CUDA events: per-kind device time."""
     barrier()
@@ -585,10 +597,7 @@ def main():
     prof = dg.profile_read(reset=True)
     clocks = sampler.stop()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
-    t = torch.tensor([elapsed], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = slowest_rank_seconds(elapsed, world, device="cuda")
     lat = sorted(a.elapsed_time(bq) for a, bq, _ in per_step)
     info = keep[0][0].info()
     sts = [s for _, _, s in per_step]
