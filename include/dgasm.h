@@ -144,6 +144,15 @@ int dgasm_system_destroy(dgasm_system_t s);
  * Asynchronous on the stream; y is bitwise identical to dgasm_system_spmv's. */
 int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, double* y, double* xAx, void* stream);
 
+/* ---- Failure detection self-test (no counterpart in the paper) --------------------------------------
+ * Every wait inside the library's kernels (ring slots, the CTA pair's exchange) is bounded: past its limit
+ * it sets the batch error word, stops waiting and lets the kernel return, and the host reports
+ * DGASM_ECUDA ("a bounded wait ... gave up") with the context still usable.  This call runs that path on
+ * purpose: one CTA waits on an mbarrier nothing arrives on, with a limit of limit_ms milliseconds (0 < limit_ms
+ * <= 1000).  *gave_up = 1 when the wait expired and reported it (the expected outcome); *elapsed_ms is the
+ * kernel's device time.  Returns DGASM_EINVAL for a limit out of range, DGASM_ECUDA on a CUDA error. */
+int dgasm_selftest_bounded_wait(double limit_ms, int* gave_up, double* elapsed_ms);
+
 /* ---- Two-level Schwarz preconditioner (Sec. 3: local solvers, coarse solver, Eq. R0T, Eq. A0) --- */
 typedef struct {
   int nsub;                 /* number of subdomains (1..ne); ignored if sub_of_elem is given */

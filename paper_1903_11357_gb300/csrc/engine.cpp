@@ -545,3 +545,35 @@ extern "C" int dgasm_system_spmv(dgasm_system_t s, const double* x, double* y, v
   DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   return DGASM_OK;
 }
+
+extern "C" int dgasm_selftest_bounded_wait(double limit_ms, int* gave_up, double* elapsed_ms) {
+  using namespace dgasm;
+  clear_error();
+  if (!gave_up || !(limit_ms > 0.0) || limit_ms > 1000.0)
+    return set_error(DGASM_EINVAL, "dgasm_selftest_bounded_wait: need gave_up and 0 < limit_ms <= 1000");
+  int dev = 0, khz = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  const long long limit = (long long)(limit_ms * (double)khz);   // cycles at the reported SM clock
+  DevBuf err;
+  DG_TRY(err.alloc(2 * sizeof(int)));
+  DG_CUDA(cudaMemset(err.ptr, 0, 2 * sizeof(int)));
+  cudaEvent_t a, b;
+  DG_CUDA(cudaEventCreate(&a));
+  DG_CUDA(cudaEventCreate(&b));
+  cudaEventRecord(a, nullptr);
+  int rc = launch_wait_selftest(err.as<int>(), limit, nullptr);
+  cudaEventRecord(b, nullptr);
+  cudaError_t se = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (rc == 0 && se == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return cuda_error(rc, "bounded-wait self-test launch");
+  if (se != cudaSuccess) return cuda_error((int)se, "bounded-wait self-test");
+  int h[2] = {0, 0};
+  DG_CUDA(cudaMemcpy(h, err.ptr, sizeof(h), cudaMemcpyDeviceToHost));
+  *gave_up = (h[0] == 1 && h[1] == 1) ? 1 : 0;
+  if (elapsed_ms) *elapsed_ms = ms;
+  return DGASM_OK;
+}

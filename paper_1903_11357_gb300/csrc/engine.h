@@ -104,6 +104,9 @@ int launch_update(const BatchDev& B, int total, int mode, int km, void* stream);
 int launch_local(const BatchDev& B, int slot, int total, int smem_bytes, void* stream);
 int launch_coarse(const BatchDev& B, int total, int km, void* stream);
 // element-block local solves z_e = inv(A_ee) r_e with the partial (r, z) per chunk item
+// one CTA waits on an mbarrier nothing arrives on, bounded by `limit` cycles: err[0] = 1 (the wait gave
+// up and set the error word), err[1] = 1 (the wait returned false)
+int launch_wait_selftest(int* err, long long limit, void* stream);
 int launch_bjac(const BatchDev& B, int total, int km, void* stream);
 int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* stream);
 int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);

@@ -68,14 +68,15 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned parit
   return ok != 0;
 }
 
-// bounded wait; returns false (and raises the abort flag and the error word) on timeout
-__device__ bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort_flag, int* err) {
+// bounded wait; returns false (and raises the abort flag and the error word) after `limit` cycles
+__device__ bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort_flag, int* err,
+                          long long limit = WAIT_CYCLES) {
   if (*abort_flag) return false;
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicExch(err, 1);
       return false;
@@ -617,11 +618,34 @@ int launch_local_t(const BatchDev& B, int slot, int kcl, int items, int ndof_max
   return kcl == 0 ? launch_one<S, C, 1>(B, slot, items, ndof_max, st) : launch_one<S, C, KC>(B, slot, items, ndof_max, st);
 }
 
+// Self-test of the bounded wait every ring and exchange wait of k_local goes through: one CTA waits on an
+// mbarrier that nothing arrives on, with a limit of `limit` cycles; the wait gives up, sets the error word
+// and the kernel returns normally (no trap, no fault, the context stays usable).
+__global__ void k_wait_selftest(int* err, long long limit) {
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(&bar, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = mbar_wait(&bar, 0, &abort_flag, err, limit);
+    err[1] = ok ? 0 : 1;
+    mbar_arrive(&bar);   // complete the phase so the barrier is left consistent
+  }
+}
+
 }  // namespace
 
 // the launch is sized inside launch_local from ndof_max; this returns ndof_max itself so that callers
 // can keep one number per launch slot
 int local_smem_bytes(int /*prec*/, int ndof_max, int /*kc*/) { return ndof_max; }
+
+int launch_wait_selftest(int* err, long long limit, void* stream) {
+  k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(err, limit);
+  return (int)cudaGetLastError();
+}
 
 // slot = K_NKINDS + 2 * prec + (kc > 1); `param` is the largest subdomain dof count of the launch
 int launch_local(const BatchDev& B, int slot, int total, int param, void* stream) {

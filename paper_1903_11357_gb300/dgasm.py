@@ -96,6 +96,7 @@ def lib():
             "dgasm_set_allocator": [vp, vp, vp],
             "dgasm_prec_info": [vp, C.c_void_p],
             "dgasm_profile_enable": [C.c_int],
+            "dgasm_selftest_bounded_wait": [C.c_double, C.POINTER(C.c_int), dp],
             "dgasm_profile_read": [C.c_int, dp, i64p, C.c_int],
             "dgasm_server_create": [C.c_size_t, C.c_int, vp, C.POINTER(vp)],
             "dgasm_submit": [vp, vp, C.POINTER(SetupOpts), C.c_int, vp, vp, C.POINTER(SolveOpts),
@@ -322,6 +323,15 @@ def lanczos(alphas, betas):
     lo, hi = C.c_double(), C.c_double()
     check(lib().dgasm_lanczos(len(a), _dp(a), _dp(b), C.byref(lo), C.byref(hi)))
     return lo.value, hi.value
+
+
+def selftest_bounded_wait(limit_ms=5.0):
+    """Runs the kernels' bounded-wait failure path on purpose (a wait nothing satisfies); returns
+    (gave_up, device ms)."""
+    g = C.c_int()
+    ms = C.c_double()
+    check(lib().dgasm_selftest_bounded_wait(float(limit_ms), C.byref(g), C.byref(ms)))
+    return bool(g.value), ms.value
 
 
 PROFILE_KINDS = ["spmv", "update", "local", "coarse", "pupdate", "chol_diag", "chol_panel", "chol_update"]
