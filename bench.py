@@ -37,8 +37,8 @@ WORKLOAD = ("16384 Lloyd-relaxed Voronoi cells of (0,1)^2 (seed 2, 20 Lloyd step
 FP64_PEAK_FLOPS_PER_CLK = 152 * 2 * 2   # 152 SMs x 2 DFMA/clk (measured issue rate) x 2 flop
 # DRAM bytes (read + write) per stream tile of the FP64 local-solve kernel, from one ncu capture of the
 # 4096-cell case (profiles/local_solve_fp64_4096cells_p3.md); valid only for the kernel source it was taken on
-LOCAL_TRAFFIC = {"sha256": "e3e39d0474eb462e58afa0e6c4c62e89ad6c040ffb09697a9827e727c8e78369",
-                 "bytes_per_stream_tile": 8478}
+LOCAL_TRAFFIC = {"sha256": "dd12d7c7069094093c9801a4ad85cb01dfb5fe167d8c84b1fbf30787c96a9b65",
+                 "bytes_per_stream_tile": 8453}
 
 
 def local_traffic(tiles):
