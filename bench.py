@@ -618,28 +618,31 @@ def main():
     barrier()
     e2e_t = time.perf_counter() - t0
 
-    mixed = None
-    if not args.no_mixed:
+    def run_mixed(precision, label):
+        """The same workload with lower-precision local factors (FP64 outer PCG, residual and coarse solve)."""
         barrier()
         mx = []
         for _ in range(args.warmup):
-            step("fp32")
-        breakdown32 = profiled_step(dg, step, barrier, "fp32")
+            step(precision)
+        breakdown_m = profiled_step(dg, step, barrier, precision)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            rc, st32, P32, x32 = step("fp32", keep=mx)
+            rc, stm, Pm, xm = step(precision, keep=mx)
         e1.record(stream)
         barrier()
-        t32 = e0.elapsed_time(e1) / 1000.0
-        err = float(torch.linalg.norm(x32 - x_fp64) / torch.linalg.norm(x_fp64))
-        mixed = {"precision": "fp32 local factors, fp64 outer", "solves_per_s": args.steps / t32,
-                 "ms_per_step": 1000.0 * t32 / args.steps, "iters": st32["iters"], "true_relres": st32["true_relres"],
-                 "rel_diff_vs_fp64": err, "speedup_vs_fp64": (args.steps / t32) / (args.steps / elapsed),
-                 "kernels_one_step": breakdown32}
-        del mx
+        tm = e0.elapsed_time(e1) / 1000.0
+        err = float(torch.linalg.norm(xm - x_fp64) / torch.linalg.norm(x_fp64))
+        return {"precision": label, "solves_per_s": args.steps / tm, "ms_per_step": 1000.0 * tm / args.steps,
+                "iters": stm["iters"], "true_relres": stm["true_relres"], "rel_diff_vs_fp64": err,
+                "speedup_vs_fp64": (args.steps / tm) / (args.steps / elapsed), "kernels_one_step": breakdown_m}
+
+    mixed = mixed_tf32 = None
+    if not args.no_mixed:
+        mixed = run_mixed("fp32", "fp32 local factors, fp64 outer")
+        mixed_tf32 = run_mixed("tf32", "fp32 local factors with tensor-core (split TF32) trailing updates, fp64 outer")
 
     if rank != 0:
         if world > 1:
@@ -688,6 +691,7 @@ def main():
         "e2e": {"value": world * args.steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": ndof * 8,
                 "d2h_bytes_per_step": ndof * 8},
         "mixed_fp32": mixed,
+        "mixed_tf32": mixed_tf32,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

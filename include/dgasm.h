@@ -153,6 +153,16 @@ int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, double* y, 
  * kernel's device time.  Returns DGASM_EINVAL for a limit out of range, DGASM_ECUDA on a CUDA error. */
 int dgasm_selftest_bounded_wait(double limit_ms, int* gave_up, double* elapsed_ms);
 
+/* ---- Tensor-core trailing update self-test ------------------------------------------------------------
+ * The TF32 precision mode runs the trailing updates of the local tile Cholesky (Sec. 3, local solvers:
+ * C_IJ -= L_IK L_JK^T) on the tensor cores with split TF32 operands.  This call runs that kernel once on a
+ * caller-supplied dense lower tile matrix of n + 1 tile rows (1 <= n <= 64): `tiles` (host, FP32) holds the
+ * (n+1)(n+2)/2 tiles row by row, tile (I, J), J <= I, at index I(I+1)/2 + J, each 32 x 32 row-major; the call
+ * applies step K = 0, C_IJ -= L_I0 L_J0^T for 1 <= J <= I <= n, and writes the whole matrix to `out` (host,
+ * same layout; tile row 0 is unchanged).  Synchronous.  DGASM_EINVAL for bad arguments, DGASM_ETIMEOUT if
+ * the kernel's bounded wait on the MMA completion gave up, DGASM_ECUDA on a CUDA error. */
+int dgasm_selftest_tc_update(int n, const float* tiles, float* out);
+
 /* ---- Two-level Schwarz preconditioner (Sec. 3: local solvers, coarse solver, Eq. R0T, Eq. A0) --- */
 typedef struct {
   int nsub;                 /* number of subdomains (1..ne); ignored if sub_of_elem is given */

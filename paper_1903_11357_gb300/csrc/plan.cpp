@@ -109,6 +109,8 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col, int sr_) {
   diag_task.clear();
   panel_task.clear();
   upd_task.clear();
+  tc_off.assign(max_nbt + 1, 0);
+  tc_task.clear();
   diag_task.reserve((size_t)nsub * max_nbt);
   panel_task.reserve((size_t)ntiles * 2);
   upd_task.reserve((size_t)ntiles * 3 * 8);
@@ -121,7 +123,17 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col, int sr_) {
       S.clear();
       for (int I = K + 1; I < nbt; ++I)
         if (Fs[s][I] <= K) S.push_back(I);
+      const int pstart = (int)(panel_task.size() / 2), n = (int)S.size();
       for (int I : S) { panel_task.push_back(s); panel_task.push_back(I); }
+      for (int mb = 0; 4 * mb < n; ++mb) {
+        const int bmax = std::min(n, 4 * mb + 4);   // column tiles J <= the block's last row tile
+        for (int nb = 0; 8 * nb < bmax; ++nb) {
+          tc_task.push_back(pstart);
+          tc_task.push_back(n);
+          tc_task.push_back(mb);
+          tc_task.push_back(nb);
+        }
+      }
       for (size_t a = 0; a < S.size(); ++a)
         for (size_t b = 0; b <= a; ++b) {
           upd_task.push_back(s);
@@ -132,6 +144,7 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col, int sr_) {
     diag_off[K + 1] = (int)diag_task.size();
     panel_off[K + 1] = (int)(panel_task.size() / 2);
     upd_off[K + 1] = (int)(upd_task.size() / 3);
+    tc_off[K + 1] = (int)(tc_task.size() / 4);
   }
 }
 

@@ -49,6 +49,11 @@ struct Envelope {
   std::vector<int> diag_task;   // s
   std::vector<int> panel_task;  // pairs (s, I)
   std::vector<int> upd_task;    // triples (s, I, J)
+  // the same updates grouped for the tensor-core kernel: per (s, K) the panel P = [L_IK], I in S(s, K)
+  // (n tiles, panel_task entries pstart .. pstart+n-1) and C_IJ -= (P P^T)_IJ, I >= J, cut into blocks of
+  // 4 row tiles (mb) x 8 column tiles (nb): quadruples (pstart, n, mb, nb)
+  std::vector<int> tc_off;      // [max_nbt + 1]
+  std::vector<int> tc_task;
   int sr = 4;                            // tile rows per super-row
   // build from the first-column function of each subdomain's dof rows, with super-rows of sr_ tile rows
   void build(const std::vector<std::vector<int>>& first_col, int sr_);

@@ -34,6 +34,7 @@ int upload_env(const Envelope& E, EnvBufs& D) {
   DG_TRY(upload(D.diag_task, E.diag_task));
   DG_TRY(upload(D.panel_task, E.panel_task));
   DG_TRY(upload(D.upd_task, E.upd_task));
+  DG_TRY(upload(D.tc_task, E.tc_task));
   DG_TRY(upload(D.bwd_src, E.bwd_src));
   DG_TRY(upload(D.fwd_src, E.fwd_src));
   DG_TRY(upload(D.fwd_ptr, E.fwd_ptr));
@@ -68,7 +69,11 @@ int factor_env(int prec, const Envelope& E, EnvBufs& D, void* Lr, int* err, cuda
     if (ev) ev->end(id, st);
     if (rc) return cuda_error(rc, "tile Cholesky panel step");
     id = ev && nu ? ev->begin(PK_CHOL_UPDATE, st) : -1;
-    rc = launch_chol_update(fp, D.dev, Lr, K, D.upd_task.as<int>() + 3 * (size_t)E.upd_off[K], nu, st);
+    if (prec == DGASM_TF32)   // tensor cores (split TF32 products, FP32 accumulation)
+      rc = launch_chol_update_tc(D.dev, (float*)Lr, K, D.panel_task.as<int>(), D.tc_task.as<int>() + 4 * (size_t)E.tc_off[K],
+                                 E.tc_off[K + 1] - E.tc_off[K], err, st);
+    else
+      rc = launch_chol_update(fp, D.dev, Lr, K, D.upd_task.as<int>() + 3 * (size_t)E.upd_off[K], nu, st);
     if (ev) ev->end(id, st);
     if (rc) return cuda_error(rc, "tile Cholesky update step");
     *launches += (nd > 0) + (npn > 0) + (nu > 0);
@@ -148,7 +153,8 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
   const size_t ns = P.env.fwd_src.size() + P.env.bwd_src.size();
   const size_t ts = ns * TILE * TILE, td = (size_t)P.env.ndinv * TILE * TILE;
   b += (t + td) * (pc.precision == DGASM_FP64 ? 8 : 4) + ts * (pc.precision == DGASM_FP64 ? 8 : 4) + ns * 8;
-  b += (P.env.upd_task.size() + P.env.panel_task.size() + P.env.diag_task.size() + P.env.trow_F.size() * 3) * 4;
+  b += (P.env.upd_task.size() + P.env.tc_task.size() + P.env.panel_task.size() + P.env.diag_task.size() +
+        P.env.trow_F.size() * 3) * 4;
   if (n0) b += ndof * P.nq * 8 + n0 * n0 * 8 * 3 + (size_t)P.env0.ntiles * TILE * TILE * 16 + P.col.size() * P.nq * P.nq * 8;
   const int epi = NTHREADS / P.np;
   b += 8 * ((size_t)6 * nrhs * ndof + 2 * nrhs * std::max<size_t>(n0, 1) + 2 * (size_t)nrhs * maxit +
@@ -245,6 +251,7 @@ int prec_build(dgasm_prec_s* pc) {
   DG_CUDA(cudaStreamSynchronize(st));
   if (herr[0]) return set_error(DGASM_ENOTSPD, "non-positive pivot in the Cholesky factor of subdomain %d at row %d", herr[1], herr[2]);
   if (herr[4]) return set_error(DGASM_ENOTSPD, "non-positive pivot in the Cholesky factor of the coarse operator A_0");
+  if (herr[3]) return set_error(DGASM_ETIMEOUT, "a tensor-core trailing update did not complete within its wait limit");
   if (ev) ev->accumulate();
   pc->setup_launches = nl;
   pc->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - pc->t_start).count();
@@ -342,7 +349,7 @@ size_t dgasm_prec_s::footprint() const {
   const EnvBufs* es[2] = {&env, &env0};
   for (const EnvBufs* e : es)
     b += e->ndof.bytes + e->sub_trow.bytes + e->trow_F.bytes + e->trow_ptr.bytes + e->diag_task.bytes +
-         e->panel_task.bytes + e->upd_task.bytes + e->bwd_src.bytes + e->fwd_src.bytes + e->fwd_ptr.bytes +
+         e->panel_task.bytes + e->upd_task.bytes + e->tc_task.bytes + e->bwd_src.bytes + e->fwd_src.bytes + e->fwd_ptr.bytes +
          e->bwd_ptr.bytes + e->dinv_task.bytes + e->dinv_ptr.bytes + e->sub_sr.bytes + e->fwd_run.bytes + e->bwd_run.bytes;
   return b;
 }
@@ -383,6 +390,35 @@ extern "C" int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info) {
 
 extern "C" int dgasm_prec_destroy(dgasm_prec_t pc) {
   delete pc;
+  return DGASM_OK;
+}
+
+// One trailing-update step on the tensor cores for a dense lower tile matrix (Sec. 3, local solvers: the
+// update C_IJ -= L_I0 L_J0^T of step 0 of the tile Cholesky), for tests of the tcgen05 kernel.
+extern "C" int dgasm_selftest_tc_update(int n, const float* tiles, float* out) {
+  using namespace dgasm;
+  clear_error();
+  if (n < 1 || n > 64 || !tiles || !out) return set_error(DGASM_EINVAL, "dgasm_selftest_tc_update: need 1 <= n <= 64 and buffers");
+  // one subdomain of n + 1 tile rows, every row reaching column 0: the envelope is the full lower triangle
+  std::vector<std::vector<int>> first_col(1, std::vector<int>((size_t)(n + 1) * TILE, 0));
+  Envelope E;
+  E.build(first_col, 8);
+  EnvBufs D;
+  DG_TRY(upload_env(E, D));
+  const size_t bytes = (size_t)E.ntiles * TILE * TILE * sizeof(float);
+  DevBuf L, err;
+  DG_TRY(L.alloc(bytes));
+  DG_TRY(err.alloc(4 * sizeof(int)));
+  DG_CUDA(cudaMemcpy(L.ptr, tiles, bytes, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemset(err.ptr, 0, 4 * sizeof(int)));
+  int rc = launch_chol_update_tc(D.dev, L.as<float>(), 0, D.panel_task.as<int>(), D.tc_task.as<int>() + 4 * (size_t)E.tc_off[0],
+                                 E.tc_off[1] - E.tc_off[0], err.as<int>(), nullptr);
+  if (rc) return cuda_error(rc, "tensor-core update self-test launch");
+  DG_CUDA(cudaDeviceSynchronize());
+  int h[4];
+  DG_CUDA(cudaMemcpy(h, err.ptr, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[3]) return set_error(DGASM_ETIMEOUT, "a tensor-core trailing update did not complete within its wait limit");
+  DG_CUDA(cudaMemcpy(out, L.ptr, bytes, cudaMemcpyDeviceToHost));
   return DGASM_OK;
 }
 

@@ -16,8 +16,8 @@
 namespace dgasm {
 
 struct EnvBufs {
-  DevBuf ndof, sub_trow, trow_F, trow_ptr, diag_task, panel_task, upd_task, bwd_src, fwd_src, fwd_ptr, bwd_ptr, dinv_task,
-      dinv_ptr, sub_sr, fwd_run, bwd_run;
+  DevBuf ndof, sub_trow, trow_F, trow_ptr, diag_task, panel_task, upd_task, tc_task, bwd_src, fwd_src, fwd_ptr, bwd_ptr,
+      dinv_task, dinv_ptr, sub_sr, fwd_run, bwd_run;
   EnvDev dev{};
 };
 

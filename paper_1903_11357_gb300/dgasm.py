@@ -97,6 +97,7 @@ def lib():
             "dgasm_prec_info": [vp, C.c_void_p],
             "dgasm_profile_enable": [C.c_int],
             "dgasm_selftest_bounded_wait": [C.c_double, C.POINTER(C.c_int), dp],
+            "dgasm_selftest_tc_update": [C.c_int, vp, vp],
             "dgasm_profile_read": [C.c_int, dp, i64p, C.c_int],
             "dgasm_server_create": [C.c_size_t, C.c_int, vp, C.POINTER(vp)],
             "dgasm_submit": [vp, vp, C.POINTER(SetupOpts), C.c_int, vp, vp, C.POINTER(SolveOpts),
@@ -332,6 +333,20 @@ def selftest_bounded_wait(limit_ms=5.0):
     ms = C.c_double()
     check(lib().dgasm_selftest_bounded_wait(float(limit_ms), C.byref(g), C.byref(ms)))
     return bool(g.value), ms.value
+
+
+def selftest_tc_update(tiles):
+    """One tensor-core trailing-update step (C_IJ -= L_I0 L_J0^T, 1 <= J <= I <= n) on a dense lower tile
+    matrix: `tiles` is a float32 array of shape ((n+1)(n+2)/2, 32, 32), tile (I, J) at I(I+1)/2 + J; returns
+    the updated array."""
+    t = np.ascontiguousarray(tiles, dtype=np.float32)
+    m = t.shape[0]
+    n = int(round((-3 + np.sqrt(1 + 8 * m)) / 2))
+    if t.shape[1:] != (32, 32) or (n + 1) * (n + 2) // 2 != m:
+        raise ValueError("tiles must have shape ((n+1)(n+2)/2, 32, 32)")
+    out = np.empty_like(t)
+    check(lib().dgasm_selftest_tc_update(n, t.ctypes.data, out.ctypes.data))
+    return out
 
 
 PROFILE_KINDS = ["spmv", "update", "local", "coarse", "pupdate", "chol_diag", "chol_panel", "chol_update"]
