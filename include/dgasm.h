@@ -172,6 +172,10 @@ typedef struct {
   const int* agg_of_elem;   /* optional host array [ne]: agglomerate of each element */
   int precision;            /* dgasm_precision for the local factors and solves */
   void* stream;             /* cudaStream_t or NULL */
+  dgasm_mesh_t coarse_mesh; /* optional: an independent polygonal mesh of the same domain whose (convex) cells
+                               D_j carry the coarse space V_0 = P_q(D_j) (non-nested coarse space, Example 4);
+                               ncoarse and agg_of_elem are then ignored.  Borrowed for the call (dgasm_setup)
+                               or until the request finishes (dgasm_submit).  NULL = agglomerates. */
 } dgasm_setup_opts;
 
 /* Builds the partition (RCB as dgasm_partition, unless arrays are given), renumbers the elements
@@ -179,13 +183,16 @@ typedef struct {
  * submatrix of A on Omega_i's dofs, Sec. 3), scales it to unit diagonal and factors it by tile
  * Cholesky (FP64/FP32/TF32/BF16 per precision); builds R_0^T|_kappa = M_kappa^{-1} N_kappa (Eq. R0T,
  * exact injection in the nested case, Remark 3.1), A_0 = R_0 A R_0^T (Eq. A0) and its FP64 Cholesky
- * factor and inverse.  All numerical work runs on the device.  Errors: DGASM_EINVAL (bad options or
- * arrays), DGASM_ENOTSPD (the message names the subdomain, or "coarse", and the pivot row),
- * DGASM_ENOMEM, DGASM_ECUDA. */
+ * factor and inverse.  With a coarse_mesh, R_0^T|_kappa = M_kappa^{-1} [int_{kappa cap D_j} phi psi_j^T]_j over
+ * the coarse cells overlapping kappa (pieces by convex clipping, computed on the host like the assembly;
+ * A_0 and everything after it on the device).  Errors: DGASM_EINVAL (bad options or arrays, a fine element
+ * or coarse cell that overlaps nothing), DGASM_ENOTSPD (the message names the subdomain, or "coarse", and
+ * the pivot row), DGASM_ENOMEM, DGASM_ECUDA. */
 int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_prec_t* out);
 /* z = B r for nrhs vectors (device, caller's dof order, column-major ndof x nrhs). */
 int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, double* z, void* stream);
-/* Partition actually used (host arrays [ne]); either pointer may be NULL. */
+/* Partition actually used (host arrays [ne]); either pointer may be NULL; agg_of_elem is not written when
+ * the coarse space lives on a coarse_mesh. */
 int dgasm_prec_partition(dgasm_prec_t pc, int* sub_of_elem, int* agg_of_elem);
 /* Bytes held on the device by the preconditioner (factors, coarse operator, permuted matrix). */
 int dgasm_prec_footprint(dgasm_prec_t pc, int64_t* bytes);

@@ -76,6 +76,11 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.bwd_total = (long long)pc.P.env.bwd_src.size();
   D.grp_ptr = pc.grp_ptr.as<int>(); D.grp_elems = pc.grp_elems.as<int>(); D.agg_int = pc.agg_int.as<int>();
   D.r0t = pc.r0t.as<double>(); D.A0inv = pc.A0inv.as<double>();
+  D.nc = P.nagg;
+  if (P.nonnested && pc.n0 > 0) {
+    D.r0t_ptr = pc.r0t_ptr.as<int>(); D.r0t_col = pc.r0t_col.as<int>(); D.r0t_elem = pc.r0t_elem.as<int>();
+    D.rT_ptr = pc.rT_ptr.as<int>(); D.rT_pair = pc.rT_pair.as<int>();
+  }
   D.b_user = b_user; D.x_user = x_user;
   double* v = (double*)(base + o_vec);
   D.b = v; D.x = v + k * ndof; D.r = v + 2 * k * ndof; D.p = v + 3 * k * ndof; D.q = v + 4 * k * ndof; D.z = v + 5 * k * ndof;
@@ -146,6 +151,7 @@ int Engine::build(int n, dgasm_prec_s* const* pcs_, const int* nrhs_, const doub
     P_(K_SPMV_P + pc->sys->p - 1, i + 1) += D.n_spmv_items;
     P_(K_GRP, i + 1) += D.ngrp;
     P_(K_COARSE, i + 1) += D.nq > 0 ? D.n_coarse_items : 0;
+    P_(K_RNN, i + 1) += D.r0t_ptr ? D.nc : 0;
     if (pc->blocks) {
       P_(K_BJAC, i + 1) += D.n_chunk_items;
     } else {
@@ -159,6 +165,7 @@ int Engine::build(int n, dgasm_prec_s* const* pcs_, const int* nrhs_, const doub
   tot_spmv = P_(K_SPMV, n);
   tot_grp = P_(K_GRP, n);
   tot_coarse = P_(K_COARSE, n);
+  tot_rnn = P_(K_RNN, n);
   const size_t o_pre = sizeof(ProbDev) * n;
   const size_t o_rem = (o_pre + sizeof(int) * pre.size() + 15) & ~(size_t)15;
   const size_t tb = o_rem + 16;
@@ -214,6 +221,8 @@ int Engine::spmv(int operand, EventPairs* ev) {
 
 int Engine::precond(int mode, EventPairs* ev) {
   const int n = nprob;
+  if (tot_rnn)   // non-nested coarse spaces: r_0 = R_0 r before the coarse solve forks off
+    DG_CUDA(timed_launch(PK_UPDATE, stream, ev, launches, [&] { return launch_restrict_nn(B, tot_rnn, km, stream); }));
   DG_CUDA(cudaEventRecord(ev_fork, stream));
   DG_CUDA(cudaStreamWaitEvent(side, ev_fork, 0));
   if (tot_coarse) DG_CUDA(timed_launch(PK_COARSE, side, ev, launches, [&] { return launch_coarse(B, tot_coarse, km, side); }));

@@ -22,7 +22,8 @@ constexpr long long ZERO_TILE = -(1LL << 62);   // solve-stream entry: a tile of
 enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
 constexpr int K_SPMV_P = K_NKINDS + 8;   // per-degree SpMV prefix slots p = 1..8
 constexpr int K_BJAC = K_SPMV_P + 8;     // element-block local solves (subdomains = elements)
-constexpr int K_NSLOTS = K_BJAC + 1;
+constexpr int K_RNN = K_BJAC + 1;        // restriction r_0 = R_0 r of non-nested coarse spaces (one item per cell)
+constexpr int K_NSLOTS = K_RNN + 1;
 enum Counter { C_SPMV = 0, C_GRP = 1, C_PUPD = 2, C_NCOUNTERS = 4 };
 
 // One problem (one preconditioner with k right-hand sides) of a batch.
@@ -63,7 +64,15 @@ struct ProbDev {
   const int* grp_ptr;
   const int* grp_elems;
   const int* agg_int; // agglomerate of each internal element
-  const double* r0t;  // [ne][np][nq] R_0^T blocks, internal element order
+  const double* r0t;  // [ne][np][nq] R_0^T blocks, internal element order; non-nested: [npair][np][nq]
+  // non-nested coarse space (r0t_ptr == nullptr for agglomerates): pairs (element, coarse cell) by element
+  // (r0t_ptr [ne+1], r0t_col) and by coarse cell (rT_ptr [nc+1], rT_pair); r0t_elem = element of a pair
+  const int* r0t_ptr;
+  const int* r0t_col;
+  const int* r0t_elem;
+  const int* rT_ptr;
+  const int* rT_pair;
+  int nc;             // coarse cells (non-nested) or agglomerates
   const double* A0inv;// [n0][n0]
   // caller-order input/output, column-major ndof x k
   const double* b_user;
@@ -109,6 +118,8 @@ int launch_coarse(const BatchDev& B, int total, int km, void* stream);
 int launch_wait_selftest(int* err, long long limit, void* stream);
 int launch_bjac(const BatchDev& B, int total, int km, void* stream);
 int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* stream);
+// r_0 = R_0 r for non-nested coarse spaces: one CTA per coarse cell (prefix slot K_RNN)
+int launch_restrict_nn(const BatchDev& B, int total, int km, void* stream);
 int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);
 // dynamic shared memory of a local-solve launch over subdomains of at most ndof_max dofs
 int local_smem_bytes(int prec, int ndof_max, int kc);
@@ -157,6 +168,10 @@ int launch_r0t(const int* perm, const double* bbox, const int* agg_int, const do
 int launch_galerkin(const int* grp_ptr, const int* grp_elems, const int* agg_int, const int* rowptr,
                     const int* col, const double* vals, const double* r0t, int ne, long long nnzb, int nagg, int np,
                     int np2s, int nq, double* W, double* A0, void* stream);
+// A_0 = R_0 A R_0^T for a non-nested coarse space (pairs as in ProbDev); A0 [n0][n0] must be zero on entry
+int launch_galerkin_nn(const int* rowptr, const int* col, const double* vals, int np, int np2s, int nq,
+                       const int* r0t_ptr, const int* r0t_col, const int* r0t_elem, const double* r0t, const int* rT_ptr,
+                       const int* rT_pair, int nc, int n0, double* A0, void* stream);
 int launch_coarse_extract(const double* A0, int n0, double* scale0, const EnvDev& E0, double* Lr0, void* stream);
 int launch_identity(double* I, int n, void* stream);
 

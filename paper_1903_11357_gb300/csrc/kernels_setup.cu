@@ -467,6 +467,46 @@ __global__ void k_galerkin_sum(const int* __restrict__ grp_ptr, const int* __res
   for (int t = lane; t < nq * n0; t += 32) A0[(long long)(J * nq + t / n0) * n0 + t % n0] = rowJ[t];
 }
 
+// A_0 = R_0 A R_0^T (Eq. A0) for a non-nested coarse space: one CTA per coarse cell J owns the rows J*nq ..
+// of A_0 and adds, for every pair t = (e, J), block (e, e') of A and pair t' = (e', J'), the product
+// R_t^T A_ee' R_t' into columns J'*nq .. (W = A_ee' R_t' first, in shared memory).  Each entry is updated by
+// one thread, in the loop order, so the sum is deterministic.
+__global__ void __launch_bounds__(128) k_galerkin_nn(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                     const double* __restrict__ vals, int np, int np2s, int nq,
+                                                     const int* __restrict__ r0t_ptr, const int* __restrict__ r0t_col,
+                                                     const int* __restrict__ r0t_elem, const double* __restrict__ r0t,
+                                                     const int* __restrict__ rT_ptr, const int* __restrict__ rT_pair,
+                                                     int n0, double* __restrict__ A0) {
+  extern __shared__ double Wsm[];   // [np][nq]
+  const int J = blockIdx.x;
+  for (int pr = rT_ptr[J]; pr < rT_ptr[J + 1]; ++pr) {
+    const int t = rT_pair[pr], e = r0t_elem[t];
+    const double* R = r0t + (long long)t * np * nq;
+    for (int kb = rowptr[e]; kb < rowptr[e + 1]; ++kb) {
+      const int e2 = col[kb];
+      const double* Ab = vals + (long long)kb * np2s;   // column-major: (a, b) at b * np + a
+      for (int t2 = r0t_ptr[e2]; t2 < r0t_ptr[e2 + 1]; ++t2) {
+        const double* R2 = r0t + (long long)t2 * np * nq;
+        const long long c0 = (long long)r0t_col[t2] * nq;
+        __syncthreads();   // the previous W has been used
+        for (int i = threadIdx.x; i < np * nq; i += blockDim.x) {
+          const int a = i / nq, c2 = i % nq;
+          double w = 0.0;
+          for (int b = 0; b < np; ++b) w = fma(Ab[b * np + a], R2[b * nq + c2], w);
+          Wsm[i] = w;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nq * nq; i += blockDim.x) {
+          const int c = i / nq, c2 = i % nq;
+          double v = 0.0;
+          for (int a = 0; a < np; ++a) v = fma(R[a * nq + c], Wsm[a * nq + c2], v);
+          A0[(long long)(J * nq + c) * n0 + c0 + c2] += v;
+        }
+      }
+    }
+  }
+}
+
 // symmetrise, scale to unit diagonal and write the lower triangle of A_0 into its (dense) tile envelope
 __global__ void k_coarse_scale(const double* __restrict__ A0, int n0, double* __restrict__ scale0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -606,6 +646,15 @@ int launch_r0t(const int* perm, const double* bbox, const int* agg_int, const do
   const int np = (p + 1) * (p + 2) / 2, nq = (q + 1) * (q + 2) / 2;
   const long long n = (long long)ne * np * nq;
   k_r0t<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)st>>>(perm, bbox, agg_int, agg_bbox, ne, p, q, gl_t, gl_w, mq, r0t);
+  return (int)cudaGetLastError();
+}
+
+int launch_galerkin_nn(const int* rowptr, const int* col, const double* vals, int np, int np2s, int nq,
+                       const int* r0t_ptr, const int* r0t_col, const int* r0t_elem, const double* r0t, const int* rT_ptr,
+                       const int* rT_pair, int nc, int n0, double* A0, void* st) {
+  if (nc <= 0) return 0;
+  k_galerkin_nn<<<nc, 128, sizeof(double) * np * nq, (cudaStream_t)st>>>(rowptr, col, vals, np, np2s, nq, r0t_ptr, r0t_col,
+                                                                        r0t_elem, r0t, rT_ptr, rT_pair, n0, A0);
   return (int)cudaGetLastError();
 }
 

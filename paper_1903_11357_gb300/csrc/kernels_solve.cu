@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
 #pragma unroll
     for (int c = 0; c < NQ1; ++c) pr0[kk][c] = 0.0;
   }
-  const bool fused_r0 = nq == NQ1;
-  const bool restrict_ = nq > 0;
+  // non-nested coarse spaces restrict in their own kernel (an element meets several coarse cells)
+  const bool restrict_ = nq > 0 && P.r0t_ptr == nullptr;
+  const bool fused_r0 = restrict_ && nq == NQ1;
   for (int base = 0; base < nd && any; base += UPD_THREADS) {
     const int t = base + threadIdx.x;
     if (t >= nd) break;
@@ -461,13 +462,21 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
     if (t < nel * np) {
       const int e = e_begin + t / np, a = t % np;
       const long long d = (long long)e * np + a;
-      const int J = nq > 0 ? P.agg_int[e] : 0;
+      const bool nn = nq > 0 && P.r0t_ptr != nullptr;
+      const int J = nq > 0 && !nn ? P.agg_int[e] : 0;
 #pragma unroll
       for (int kk = 0; kk < KM; ++kk) {
         if (!act[kk]) continue;
         const long long o = kk * (long long)P.ndof + d;
         double zv = P.z[o];
-        if (nq > 0) {
+        if (nn) {
+          // non-nested: every coarse cell that meets the element, in ascending order
+          for (int t = P.r0t_ptr[e]; t < P.r0t_ptr[e + 1]; ++t) {
+            const double* R = P.r0t + ((long long)t * np + a) * nq;
+            const double* z0 = P.z0 + (long long)kk * P.n0 + (long long)P.r0t_col[t] * nq;
+            for (int c = 0; c < nq; ++c) zv = fma(R[c], z0[c], zv);
+          }
+        } else if (nq > 0) {
           const double* R = P.r0t + d * nq;
           const double* z0 = P.z0 + (long long)kk * P.n0 + J * nq;
           for (int c = 0; c < nq; ++c) zv = fma(R[c], z0[c], zv);
@@ -491,6 +500,42 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
       P.done[kk] = 3;
       atomicSub(P.remaining, 1);
     }
+  }
+}
+
+// ---- r_0 = R_0 r for a non-nested coarse space: one CTA per coarse cell J, over the pairs (element, J) in
+// ascending order; per coarse basis function c a deterministic block sum of R[pair][a][c] r[e a]
+template <int KM>
+__global__ void __launch_bounds__(NTHREADS) k_restrict_nn(BatchDev B) {
+  __shared__ double red[NW * KMAX];
+  __shared__ double tot[KMAX];
+  const int pi = find_prob(B.prefix[K_RNN], B.nprob, blockIdx.x);
+  const ProbDev& P = B.probs[pi];
+  const int J = blockIdx.x - B.prefix[K_RNN][pi];
+  const int k = P.k, np = P.np, nq = P.nq;
+  bool act[KM];
+  bool any = false;
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk) {
+    act[kk] = kk < k && P.done[kk] == 0;
+    any |= act[kk];
+  }
+  if (!any) return;
+  const int t0 = P.rT_ptr[J], n = (P.rT_ptr[J + 1] - t0) * np;
+  for (int c = 0; c < nq; ++c) {
+    double v[KM];
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) v[kk] = 0.0;
+    for (int i = threadIdx.x; i < n; i += NTHREADS) {
+      const int t = P.rT_pair[t0 + i / np], a = i % np;
+      const double w = P.r0t[((long long)t * np + a) * nq + c];
+      const long long d = (long long)P.r0t_elem[t] * np + a;
+#pragma unroll
+      for (int kk = 0; kk < KM; ++kk)
+        if (act[kk]) v[kk] = fma(w, P.r[kk * (long long)P.ndof + d], v[kk]);
+    }
+    block_sum_k<KM>(v, k, red, tot);
+    if (threadIdx.x < k && act[threadIdx.x]) P.r0[(long long)threadIdx.x * P.n0 + (long long)J * nq + c] = tot[threadIdx.x];
   }
 }
 
@@ -577,6 +622,12 @@ int launch_bjac(const BatchDev& B, int total, int km, void* st) {
 int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* st) {
   if (km == 1) k_pupdate<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
   else k_pupdate<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
+  return (int)cudaGetLastError();
+}
+
+int launch_restrict_nn(const BatchDev& B, int total, int km, void* st) {
+  if (km == 1) k_restrict_nn<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
+  else k_restrict_nn<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B);
   return (int)cudaGetLastError();
 }
 

@@ -210,7 +210,7 @@ std::vector<int> rcm_order(const std::vector<int>& elems, const std::vector<int>
 }  // namespace
 
 int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const int* sub_in, const int* agg_in, int sr,
-               Plan& P) {
+               Plan& P, const MeshData* coarse) {
   const MeshData& m = sys.mesh->m;
   const int ne = m.ne, np = sys.np;
   P.ne = ne;
@@ -232,8 +232,13 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   }
   P.nsub = nsub;
   P.q = q;
-  P.nq = ncoarse > 0 || agg_in ? n_basis(q) : 0;
-  if (agg_in) {
+  P.nq = ncoarse > 0 || agg_in || coarse ? n_basis(q) : 0;
+  P.nonnested = coarse != nullptr;
+  P.agg_of.clear();
+  if (coarse) {
+    if (coarse->ne < 1) return set_error(DGASM_EINVAL, "the coarse mesh has no cells");
+    P.nagg = coarse->ne;
+  } else if (agg_in) {
     P.agg_of.assign(agg_in, agg_in + ne);
     int mx = 0;
     for (int e = 0; e < ne; ++e) {
@@ -264,7 +269,7 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   } else {
     P.nagg = 0;
   }
-  if (P.nagg > 0) {
+  if (P.nagg > 0 && !P.nonnested) {
     std::vector<int> cnt(P.nagg, 0);
     for (int e = 0; e < ne; ++e) cnt[P.agg_of[e]]++;
     for (int j = 0; j < P.nagg; ++j) if (!cnt[j]) return set_error(DGASM_EINVAL, "agglomerate %d is empty", j);
@@ -327,7 +332,7 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   P.agg_int.assign(ne, -1);
   P.grp_ptr.assign(1, 0);
   P.grp_elems.clear();
-  if (P.nagg > 0) {
+  if (P.nagg > 0 && !P.nonnested) {
     std::vector<std::vector<int>> mem(P.nagg);
     for (int i = 0; i < ne; ++i) { P.agg_int[i] = P.agg_of[P.perm[i]]; mem[P.agg_int[i]].push_back(i); }
     for (int j = 0; j < P.nagg; ++j) {
@@ -348,9 +353,6 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
       P.agg_bbox[4 * j + 2] = std::min(P.agg_bbox[4 * j + 2], b[2]);
       P.agg_bbox[4 * j + 3] = std::max(P.agg_bbox[4 * j + 3], b[3]);
     }
-    int n0 = P.nagg * P.nq;
-    std::vector<std::vector<int>> fc0(1, std::vector<int>(n0, 0));
-    P.env0.build(fc0, super_row(DGASM_FP64));
   } else {
     const int G = 64;
     for (int i = 0; i < ne; i += G) {
@@ -358,6 +360,11 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
       P.grp_ptr.push_back((int)P.grp_elems.size());
     }
     P.ngrp = (int)P.grp_ptr.size() - 1;
+  }
+  if (P.nagg > 0) {   // the coarse factor: one dense block
+    int n0 = P.nagg * P.nq;
+    std::vector<std::vector<int>> fc0(1, std::vector<int>(n0, 0));
+    P.env0.build(fc0, super_row(DGASM_FP64));
   }
   return DGASM_OK;
 }

@@ -59,8 +59,19 @@ struct Envelope {
   void build(const std::vector<std::vector<int>>& first_col, int sr_);
 };
 
+// R_0^T of a non-nested coarse mesh in internal element order: pairs (element i, coarse cell J) with blocks
+// [np][nq] (row a, column c), grouped by element (ptr, ascending J) and listed again by coarse cell (tptr,
+// tpair: pair indices, ascending)
+struct R0TPairs {
+  std::vector<int> ptr, col, elem, tptr, tpair;
+  std::vector<double> blocks;
+};
+int nonnested_r0t(const MeshData& fine, const std::vector<int>& perm, const MeshData& coarse, int p, int q,
+                  R0TPairs& out);
+
 struct Plan {
   int ne = 0, np = 0, nsub = 0, nagg = 0, q = 0, nq = 0;
+  bool nonnested = false;            // coarse space on an independent mesh (nagg = its cell count)
   std::vector<int> sub_of, agg_of;   // caller's element order
   std::vector<int> perm, iperm;      // perm[internal] = caller element; iperm inverse
   std::vector<int> sub_e0;           // [nsub+1] internal element ranges
@@ -77,7 +88,8 @@ struct Plan {
 };
 
 // sr: tile rows per super-row of the local factors (the coarse factor takes super_row(DGASM_FP64))
+// coarse: an independent coarse mesh (non-nested coarse space); ncoarse and agg_in are then ignored
 int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const int* sub_in, const int* agg_in, int sr,
-               Plan& P);
+               Plan& P, const MeshData* coarse = nullptr);
 
 }  // namespace dgasm

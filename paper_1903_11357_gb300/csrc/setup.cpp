@@ -126,7 +126,7 @@ namespace dgasm {
 int prec_plan(dgasm_system_s* s, const dgasm_setup_opts* o, std::unique_ptr<dgasm_prec_s>& pc) {
   if (!s || !o) return set_error(DGASM_EINVAL, "dgasm_setup: NULL argument");
   if (o->precision < DGASM_FP64 || o->precision > DGASM_BF16) return set_error(DGASM_EINVAL, "unknown precision %d", o->precision);
-  const bool coarse = o->ncoarse > 0 || o->agg_of_elem;
+  const bool coarse = o->ncoarse > 0 || o->agg_of_elem || o->coarse_mesh;
   if (coarse && (o->p_c < 1 || o->p_c > s->p)) return set_error(DGASM_EINVAL, "p_c=%d must lie in [1, p=%d]", o->p_c, s->p);
   const auto t_start = std::chrono::steady_clock::now();
   pc.reset(new (std::nothrow) dgasm_prec_s());
@@ -137,9 +137,12 @@ int prec_plan(dgasm_system_s* s, const dgasm_setup_opts* o, std::unique_ptr<dgas
   DG_TRY(s->ensure_device());
   DG_TRY(pc->init_streams(o->stream));
   Plan& P = pc->P;
+  const MeshData* cm = o->coarse_mesh ? &o->coarse_mesh->m : nullptr;
   DG_TRY(build_plan(*s, o->nsub, o->ncoarse, coarse ? o->p_c : 1, o->sub_of_elem, o->agg_of_elem,
-                    super_row(o->precision), P));
+                    super_row(o->precision), P, cm));
   pc->n0 = P.nagg * P.nq;
+  // non-nested coarse space: R_0^T blocks over the fine/coarse cell intersections (host, like the assembly)
+  if (P.nonnested) DG_TRY(nonnested_r0t(s->mesh->m, P.perm, *cm, s->p, P.q, pc->nn));
   pc->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return DGASM_OK;
 }
@@ -155,6 +158,7 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
   b += (t + td) * (pc.precision == DGASM_FP64 ? 8 : 4) + ts * (pc.precision == DGASM_FP64 ? 8 : 4) + ns * 8;
   b += (P.env.upd_task.size() + P.env.tc_task.size() + P.env.panel_task.size() + P.env.diag_task.size() +
         P.env.trow_F.size() * 3) * 4;
+  b += pc.nn.blocks.size() * 8 + (pc.nn.ptr.size() + pc.nn.col.size() * 3 + pc.nn.tptr.size()) * 4;
   if (n0) b += ndof * P.nq * 8 + n0 * n0 * 8 * 3 + (size_t)P.env0.ntiles * TILE * TILE * 16 + P.col.size() * P.nq * P.nq * 8;
   const int epi = NTHREADS / P.np;
   b += 8 * ((size_t)6 * nrhs * ndof + 2 * nrhs * std::max<size_t>(n0, 1) + 2 * (size_t)nrhs * maxit +
@@ -220,16 +224,31 @@ int prec_build(dgasm_prec_s* pc) {
     DG_TRY(upload(d_gt, gt));
     DG_TRY(upload(d_gw, gw));
     DG_TRY(upload(d_aggbox, P.agg_bbox));
-    DG_TRY(pc->r0t.alloc(sizeof(double) * (size_t)ne * np * nq));
-    DG_CUDA(launch_r0t(pc->perm.as<int>(), s->d_bbox.as<double>(), pc->agg_int.as<int>(), d_aggbox.as<double>(), ne,
-                       s->p, q, d_gt.as<double>(), d_gw.as<double>(), mq, pc->r0t.as<double>(), st));
     DevBuf A0;
     DG_TRY(A0.alloc(sizeof(double) * (size_t)n0 * n0));
-    DevBuf W;
-    DG_TRY(W.alloc(sizeof(double) * P.col.size() * (size_t)nq * nq));
-    DG_CUDA(launch_galerkin(pc->grp_ptr.as<int>(), pc->grp_elems.as<int>(), pc->agg_int.as<int>(), pc->rowptr.as<int>(),
-                            pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), ne, (long long)P.col.size(),
-                            P.nagg, np, np2s, nq, W.as<double>(), A0.as<double>(), st));
+    if (P.nonnested) {
+      // R_0^T pairs from the plan; A_0 accumulated row block by row block on the device
+      DG_TRY(upload(pc->r0t, pc->nn.blocks));
+      DG_TRY(upload(pc->r0t_ptr, pc->nn.ptr));
+      DG_TRY(upload(pc->r0t_col, pc->nn.col));
+      DG_TRY(upload(pc->r0t_elem, pc->nn.elem));
+      DG_TRY(upload(pc->rT_ptr, pc->nn.tptr));
+      DG_TRY(upload(pc->rT_pair, pc->nn.tpair));
+      DG_CUDA(cudaMemsetAsync(A0.ptr, 0, A0.bytes, st));
+      DG_CUDA(launch_galerkin_nn(pc->rowptr.as<int>(), pc->col.as<int>(), pc->vals.as<double>(), np, np2s, nq,
+                                 pc->r0t_ptr.as<int>(), pc->r0t_col.as<int>(), pc->r0t_elem.as<int>(), pc->r0t.as<double>(),
+                                 pc->rT_ptr.as<int>(), pc->rT_pair.as<int>(), P.nagg, n0, A0.as<double>(), st));
+      pc->nn = R0TPairs{};
+    } else {
+      DG_TRY(pc->r0t.alloc(sizeof(double) * (size_t)ne * np * nq));
+      DG_CUDA(launch_r0t(pc->perm.as<int>(), s->d_bbox.as<double>(), pc->agg_int.as<int>(), d_aggbox.as<double>(), ne,
+                         s->p, q, d_gt.as<double>(), d_gw.as<double>(), mq, pc->r0t.as<double>(), st));
+      DevBuf W;
+      DG_TRY(W.alloc(sizeof(double) * P.col.size() * (size_t)nq * nq));
+      DG_CUDA(launch_galerkin(pc->grp_ptr.as<int>(), pc->grp_elems.as<int>(), pc->agg_int.as<int>(), pc->rowptr.as<int>(),
+                              pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), ne, (long long)P.col.size(),
+                              P.nagg, np, np2s, nq, W.as<double>(), A0.as<double>(), st));
+    }
     DG_TRY(upload_env(P.env0, pc->env0));
     DevBuf scale0, Lr0, Lc0, Lb0;
     DG_TRY(scale0.alloc(sizeof(double) * n0));
@@ -345,7 +364,8 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
 
 size_t dgasm_prec_s::footprint() const {
   size_t b = perm.bytes + rowptr.bytes + col.bytes + vals.bytes + sub_e0.bytes + scale.bytes + Lr.bytes + Lc.bytes +
-             grp_ptr.bytes + grp_elems.bytes + agg_int.bytes + r0t.bytes + A0inv.bytes + err.bytes + dinv.bytes;
+             grp_ptr.bytes + grp_elems.bytes + agg_int.bytes + r0t.bytes + A0inv.bytes + err.bytes + dinv.bytes +
+             r0t_ptr.bytes + r0t_col.bytes + r0t_elem.bytes + rT_ptr.bytes + rT_pair.bytes;
   const EnvBufs* es[2] = {&env, &env0};
   for (const EnvBufs* e : es)
     b += e->ndof.bytes + e->sub_trow.bytes + e->trow_F.bytes + e->trow_ptr.bytes + e->diag_task.bytes +

@@ -45,7 +45,7 @@ struct Engine {
   std::vector<ProbDev> hp;
   std::vector<int> pre;
   int max_smem[8] = {0};
-  int tot_spmv = 0, tot_grp = 0, tot_coarse = 0;
+  int tot_spmv = 0, tot_grp = 0, tot_coarse = 0, tot_rnn = 0;
   int total_rhs = 0;
   int km = 1;   // 1 when every problem has one right-hand side
   DevBuf tables;
@@ -103,6 +103,8 @@ struct dgasm_prec_s {
   cudaStream_t stream = nullptr, own_stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   dgasm::DevBuf perm, rowptr, col, vals, src_blk, sub_e0, scale, Lr, Lc, grp_ptr, grp_elems, agg_int, r0t, A0inv, err, io;
+  dgasm::DevBuf r0t_ptr, r0t_col, r0t_elem, rT_ptr, rT_pair;   // non-nested coarse space: R_0^T pairs
+  dgasm::R0TPairs nn;       // host copy of the pairs between the plan and the upload
   bool blocks = false;      // every subdomain is one element: local solves with explicit block inverses
   dgasm::DevBuf dinv;       // [ne][np][np] FP64, internal element order
   dgasm::EnvBufs env, env0;

@@ -25,7 +25,7 @@ RHS_FN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)
 class SetupOpts(C.Structure):
     _fields_ = [("nsub", C.c_int), ("ncoarse", C.c_int), ("p_c", C.c_int),
                 ("sub_of_elem", C.POINTER(C.c_int)), ("agg_of_elem", C.POINTER(C.c_int)),
-                ("precision", C.c_int), ("stream", C.c_void_p)]
+                ("precision", C.c_int), ("stream", C.c_void_p), ("coarse_mesh", C.c_void_p)]
 
 
 class SolveOpts(C.Structure):
@@ -241,9 +241,13 @@ class System:
 
 class Prec:
     def __init__(self, system: System, nsub: int, ncoarse: int, p_c: int = 1, precision="fp64", sub_of_elem=None,
-                 agg_of_elem=None, stream=None):
+                 agg_of_elem=None, stream=None, coarse_mesh=None):
+        """coarse_mesh: a Mesh of the same domain carrying a non-nested coarse space (ncoarse is ignored)."""
         self.system = system
+        self._coarse = coarse_mesh
         o = SetupOpts()
+        if coarse_mesh is not None:
+            o.coarse_mesh = coarse_mesh.h
         o.nsub, o.ncoarse, o.p_c = nsub, ncoarse, p_c
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self._sub = self._agg = None
@@ -386,11 +390,14 @@ class Server:
         self._keep = {}
 
     def submit(self, system: System, nsub, ncoarse, p_c, b, x, precision="fp64", rtol=1e-8, maxit=10000,
-               sub_of_elem=None, agg_of_elem=None):
+               sub_of_elem=None, agg_of_elem=None, coarse_mesh=None):
         o = SetupOpts()
         o.nsub, o.ncoarse, o.p_c = nsub, ncoarse, p_c
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         keep = [b, x]
+        if coarse_mesh is not None:
+            keep.append(coarse_mesh)
+            o.coarse_mesh = coarse_mesh.h
         if sub_of_elem is not None:
             a = np.ascontiguousarray(sub_of_elem, np.int32)
             keep.append(a)
