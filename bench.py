@@ -561,6 +561,19 @@ def main():
     b_host = S.rhs()
     b = torch.tensor(b_host, dtype=torch.float64, device="cuda")
     ndof = S.ndof
+    # the matrix assembly (outside the timed step: the step starts from the assembled system), on the host
+    # threads and on the device, second call of each timed
+    asm = {}
+    for dev_asm in (False, True):
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S_tmp = dg.System(M, P_DEG, 10.0, device=dev_asm, stream=stream)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            del S_tmp
+        asm["device_ms" if dev_asm else "host_ms"] = 1000.0 * dt
+    asm.update({"cells": N_ELEM, "p": P_DEG, "host_threads": os.cpu_count(), "what": "block matrix only (no load vector)"})
 
     def step(precision="fp64", keep=None):
         P = dg.Prec(S, NSUB, NCOARSE, P_C, precision=precision, stream=stream)
@@ -696,6 +709,7 @@ def main():
         "setup": {"plan_ms": info["plan_ms"], "setup_ms": info["setup_ms"], "local_tiles": info["local_tiles"],
                   "stream_tiles": tiles, "factor_flops": info["factor_flops"]},
         "gpu_launches": int(launches),
+        "assembly": asm,
         "kernels_one_step": breakdown,
         "roofline": roof,
         "e2e": {"value": world * args.steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": ndof * 8,

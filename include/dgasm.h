@@ -116,6 +116,13 @@ int dgasm_partition(dgasm_mesh_t m, int nsub, int ncoarse, int* sub_of_elem, int
  * by the system.  Errors: DGASM_EINVAL (p < 1 or p > 8, c_sigma <= 0), DGASM_ENOMEM, DGASM_ECUDA. */
 int dgasm_assemble(dgasm_mesh_t m, int p, double c_sigma, dgasm_rhs_fn f, void* user,
                    dgasm_system_t* out);
+/* The same system with the matrix assembled on the device (one CTA per element block row, the same terms,
+ * rules and summation order as dgasm_assemble; entries agree up to the contraction of products into FMAs),
+ * written straight into the device block layout on `stream` (cudaStream_t, NULL = default stream); the
+ * load vector, a host callback, is assembled on the host while the kernel runs.  Synchronous.  The host copy
+ * of the blocks (dgasm_system_blocks) is made on first request.  Errors as dgasm_assemble. */
+int dgasm_assemble_device(dgasm_mesh_t m, int p, double c_sigma, dgasm_rhs_fn f, void* user, void* stream,
+                          dgasm_system_t* out);
 /* Number of dofs (ne * n_p) and n_p. */
 int dgasm_system_dofs(dgasm_system_t s, int64_t* ndof, int* n_p);
 /* Host copy of the load vector (ndof doubles); DGASM_EINVAL if no f was given. */

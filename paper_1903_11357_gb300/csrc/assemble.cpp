@@ -9,12 +9,14 @@
 // in ascending face order, so the result does not depend on the thread count.
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <thread>
 
 #include <cuda_runtime.h>
 
 #include "basis.h"
 #include "common.h"
+#include "engine.h"
 
 using namespace dgasm;
 
@@ -118,24 +120,19 @@ void assemble_rows(const MeshData& m, const Basis& B, double c_sigma, const std:
 
 }  // namespace
 
-extern "C" int dgasm_assemble(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_fn f, void* user,
-                              dgasm_system_t* out) {
-  clear_error();
-  if (!out) return set_error(DGASM_EINVAL, "dgasm_assemble: out is NULL");
-  *out = nullptr;
-  if (!mh) return set_error(DGASM_EINVAL, "dgasm_assemble: NULL mesh");
-  if (p < 1 || p > 8) return set_error(DGASM_EINVAL, "p=%d must lie in [1, 8]", p);
-  if (!(c_sigma > 0.0)) return set_error(DGASM_EINVAL, "c_sigma must be positive");
+namespace {
+
+// a fresh system with the block sparsity: each element and its face neighbours, ascending
+dgasm_system_s* new_system(dgasm_mesh_t mh, int p, double c_sigma) {
   const MeshData& m = mh->m;
   auto* s = new (std::nothrow) dgasm_system_s();
-  if (!s) return set_error(DGASM_ENOMEM, "host allocation failed");
+  if (!s) return nullptr;
   s->mesh = mh;
   s->p = p;
   s->np = n_basis(p);
   s->np2s = (s->np * s->np + 1) & ~1;
   s->c_sigma = c_sigma;
-  const int ne = m.ne, nb = s->np;
-  // sparsity: e and its face neighbours, ascending
+  const int ne = m.ne;
   s->rowptr.assign(ne + 1, 0);
   std::vector<std::vector<int>> nbr(ne);
   for (int e = 0; e < ne; ++e) {
@@ -151,6 +148,59 @@ extern "C" int dgasm_assemble(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_
   }
   s->col.resize(s->rowptr[ne]);
   for (int e = 0; e < ne; ++e) std::copy(nbr[e].begin(), nbr[e].end(), s->col.begin() + s->rowptr[e]);
+  return s;
+}
+
+// load vector b_a = int f phi_a, (p+5)-point rule, callback on this thread in chunks
+void assemble_rhs(const MeshData& m, const Basis& B, dgasm_rhs_fn f, void* user, dgasm_system_s* s) {
+  const int ne = m.ne, nb = B.nb, p = B.p;
+  s->b.assign((size_t)ne * nb, 0.0);
+  s->has_b = true;
+  std::vector<double> t, w, pts, wts, allp, fv, v(nb);
+  gauss_legendre01(p + 5, t, w);
+  const int chunk = 256;
+  for (int c0 = 0; c0 < ne; c0 += chunk) {
+    int c1 = std::min(ne, c0 + chunk);
+    std::vector<size_t> off(1, 0);
+    allp.clear();
+    std::vector<double> allw;
+    for (int e = c0; e < c1; ++e) {
+      polygon_points(m, e, t, w, pts, wts);
+      allp.insert(allp.end(), pts.begin(), pts.end());
+      allw.insert(allw.end(), wts.begin(), wts.end());
+      off.push_back(allw.size());
+    }
+    fv.assign(allw.size(), 0.0);
+    f((int)allw.size(), allp.data(), fv.data(), user);
+    for (int e = c0; e < c1; ++e) {
+      double* be = &s->b[(size_t)e * nb];
+      for (size_t qp = off[e - c0]; qp < off[e - c0 + 1]; ++qp) {
+        B.eval(&m.bbox[4 * (size_t)e], allp[2 * qp], allp[2 * qp + 1], v.data(), nullptr);
+        for (int a = 0; a < nb; ++a) be[a] += allw[qp] * fv[qp] * v[a];
+      }
+    }
+  }
+}
+
+int check_args(dgasm_mesh_t mh, int p, double c_sigma, dgasm_system_t* out) {
+  if (!out) return set_error(DGASM_EINVAL, "dgasm_assemble: out is NULL");
+  *out = nullptr;
+  if (!mh) return set_error(DGASM_EINVAL, "dgasm_assemble: NULL mesh");
+  if (p < 1 || p > 8) return set_error(DGASM_EINVAL, "p=%d must lie in [1, 8]", p);
+  if (!(c_sigma > 0.0)) return set_error(DGASM_EINVAL, "c_sigma must be positive");
+  return DGASM_OK;
+}
+
+}  // namespace
+
+extern "C" int dgasm_assemble(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_fn f, void* user,
+                              dgasm_system_t* out) {
+  clear_error();
+  DG_TRY(check_args(mh, p, c_sigma, out));
+  const MeshData& m = mh->m;
+  dgasm_system_s* s = new_system(mh, p, c_sigma);
+  if (!s) return set_error(DGASM_ENOMEM, "host allocation failed");
+  const int ne = m.ne, nb = s->np;
   s->vals.assign((size_t)s->rowptr[ne] * nb * nb, 0.0);
   Basis B(p);
   unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
@@ -161,36 +211,52 @@ extern "C" int dgasm_assemble(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_
     th.emplace_back([&, e0, e1]() { assemble_rows(m, B, c_sigma, s->rowptr, s->col, s->vals, e0, e1); });
   }
   for (auto& x : th) x.join();
-  // load vector b_a = int f phi_a, (p+5)-point rule, callback on this thread in chunks
-  if (f) {
-    s->b.assign((size_t)ne * nb, 0.0);
-    s->has_b = true;
-    std::vector<double> t, w, pts, wts, allp, fv, v(nb);
-    gauss_legendre01(p + 5, t, w);
-    const int chunk = 256;
-    for (int c0 = 0; c0 < ne; c0 += chunk) {
-      int c1 = std::min(ne, c0 + chunk);
-      std::vector<size_t> off(1, 0);
-      allp.clear();
-      std::vector<double> allw;
-      for (int e = c0; e < c1; ++e) {
-        polygon_points(m, e, t, w, pts, wts);
-        allp.insert(allp.end(), pts.begin(), pts.end());
-        allw.insert(allw.end(), wts.begin(), wts.end());
-        off.push_back(allw.size());
-      }
-      fv.assign(allw.size(), 0.0);
-      f((int)allw.size(), allp.data(), fv.data(), user);
-      for (int e = c0; e < c1; ++e) {
-        double* be = &s->b[(size_t)e * nb];
-        for (size_t qp = off[e - c0]; qp < off[e - c0 + 1]; ++qp) {
-          B.eval(&m.bbox[4 * (size_t)e], allp[2 * qp], allp[2 * qp + 1], v.data(), nullptr);
-          for (int a = 0; a < nb; ++a) be[a] += allw[qp] * fv[qp] * v[a];
-        }
-      }
-    }
-  }
+  if (f) assemble_rhs(m, B, f, user, s);
   *out = s;
+  return DGASM_OK;
+}
+
+// The same system with the matrix assembled on the device, straight into the device block layout; the
+// load vector (a host callback) stays on the host.  The host copy of the blocks is made on demand.
+extern "C" int dgasm_assemble_device(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_fn f, void* user, void* stream,
+                                     dgasm_system_t* out) {
+  clear_error();
+  DG_TRY(check_args(mh, p, c_sigma, out));
+  const MeshData& m = mh->m;
+  std::unique_ptr<dgasm_system_s> s(new_system(mh, p, c_sigma));
+  if (!s) return set_error(DGASM_ENOMEM, "host allocation failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf rho, diam, efp, eff, fep, fem, fva, fvb, gt, gw;
+  std::vector<double> t, w;
+  gauss_legendre01(p + 2, t, w);
+  DG_TRY(upload(s->d_rowptr, s->rowptr));
+  DG_TRY(upload(s->d_col, s->col));
+  DG_TRY(upload(s->d_xy, m.xy));
+  DG_TRY(upload(s->d_pptr, m.ptr));
+  DG_TRY(upload(s->d_pvtx, m.vtx));
+  DG_TRY(upload(s->d_bbox, m.bbox));
+  DG_TRY(upload(rho, m.rho));
+  DG_TRY(upload(diam, m.diam));
+  DG_TRY(upload(efp, m.ef_ptr));
+  DG_TRY(upload(eff, m.ef_face));
+  DG_TRY(upload(fep, m.f_ep));
+  DG_TRY(upload(fem, m.f_em));
+  DG_TRY(upload(fva, m.f_va));
+  DG_TRY(upload(fvb, m.f_vb));
+  DG_TRY(upload(gt, t));
+  DG_TRY(upload(gw, w));
+  DevBuf vals;
+  DG_TRY(vals.alloc(sizeof(double) * (size_t)s->rowptr[m.ne] * s->np2s));
+  DG_CUDA(cudaMemsetAsync(vals.ptr, 0, vals.bytes, st));
+  AsmMesh A{m.ne, s->d_xy.as<double>(), s->d_pptr.as<int>(), s->d_pvtx.as<int>(), s->d_bbox.as<double>(),
+            rho.as<double>(), diam.as<double>(), efp.as<int>(), eff.as<int>(), fep.as<int>(), fem.as<int>(),
+            fva.as<int>(), fvb.as<int>()};
+  DG_CUDA(launch_assemble(A, p, c_sigma, gt.as<double>(), gw.as<double>(), s->d_rowptr.as<int>(), s->d_col.as<int>(),
+                          s->np2s, vals.as<double>(), st));
+  if (f) assemble_rhs(m, Basis(p), f, user, s.get());   // overlaps the kernel
+  DG_CUDA(cudaStreamSynchronize(st));
+  s->d_vals = std::move(vals);
+  *out = s.release();
   return DGASM_OK;
 }
 
@@ -213,7 +279,10 @@ extern "C" int dgasm_system_blocks(dgasm_system_t s, int64_t* nnzb, int* rowptr,
   *nnzb = (int64_t)s->col.size();
   if (rowptr) std::copy(s->rowptr.begin(), s->rowptr.end(), rowptr);
   if (col) std::copy(s->col.begin(), s->col.end(), col);
-  if (vals) std::copy(s->vals.begin(), s->vals.end(), vals);
+  if (vals) {
+    DG_TRY(s->ensure_host());
+    std::copy(s->vals.begin(), s->vals.end(), vals);
+  }
   return DGASM_OK;
 }
 
@@ -240,5 +309,19 @@ int dgasm_system_s::ensure_device() {
   DG_TRY(upload(d_pvtx, m.vtx));
   DG_TRY(upload(d_bbox, m.bbox));
   DG_TRY(upload(d_vals, dv));
+  return DGASM_OK;
+}
+
+// Host copy of the blocks of a device-assembled system (row-major per block)
+int dgasm_system_s::ensure_host() {
+  std::lock_guard<std::mutex> lk(dev_mu);
+  const size_t nnzb = col.size();
+  if (vals.size() == nnzb * np * np) return DGASM_OK;
+  std::vector<double> dv(nnzb * np2s);
+  DG_CUDA(cudaMemcpy(dv.data(), d_vals.ptr, sizeof(double) * dv.size(), cudaMemcpyDeviceToHost));
+  vals.assign(nnzb * np * np, 0.0);
+  for (size_t k = 0; k < nnzb; ++k)
+    for (int a = 0; a < np; ++a)
+      for (int c = 0; c < np; ++c) vals[k * np * np + (size_t)a * np + c] = dv[k * np2s + (size_t)c * np + a];
   return DGASM_OK;
 }

@@ -92,4 +92,5 @@ struct dgasm_system_s {
   dgasm::DevBuf d_xy, d_pptr, d_pvtx, d_bbox;
   std::mutex dev_mu;
   int ensure_device();
+  int ensure_host();   // host blocks of a device-assembled system
 };

@@ -168,6 +168,25 @@ int launch_r0t(const int* perm, const double* bbox, const int* agg_int, const do
 int launch_galerkin(const int* grp_ptr, const int* grp_elems, const int* agg_int, const int* rowptr,
                     const int* col, const double* vals, const double* r0t, int ne, long long nnzb, int nagg, int np,
                     int np2s, int nq, double* W, double* A0, void* stream);
+// SIPG assembly on the device (kernels_assemble.cu): mesh arrays as in MeshData, on the device
+struct AsmMesh {
+  int ne;
+  const double* xy;
+  const int* ptr;
+  const int* vtx;
+  const double* bbox;
+  const double* rho;
+  const double* diam;
+  const int* ef_ptr;
+  const int* ef_face;
+  const int* f_ep;
+  const int* f_em;
+  const int* f_va;
+  const int* f_vb;
+};
+// vals: the device blocks (column-major, stride np2s), zero on entry; gt, gw: the (p+2)-point Gauss rule on [0, 1]
+int launch_assemble(const AsmMesh& M, int p, double c_sigma, const double* gt, const double* gw, const int* rowptr,
+                    const int* col, int np2s, double* vals, void* stream);
 // A_0 = R_0 A R_0^T for a non-nested coarse space (pairs as in ProbDev); A0 [n0][n0] must be zero on entry
 int launch_galerkin_nn(const int* rowptr, const int* col, const double* vals, int np, int np2s, int nq,
                        const int* r0t_ptr, const int* r0t_col, const int* r0t_elem, const double* r0t, const int* rT_ptr,

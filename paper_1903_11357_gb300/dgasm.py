@@ -79,6 +79,7 @@ def lib():
             "dgasm_mesh_destroy": [vp],
             "dgasm_partition": [vp, C.c_int, C.c_int, ip, ip],
             "dgasm_assemble": [vp, C.c_int, C.c_double, RHS_FN, vp, C.POINTER(vp)],
+            "dgasm_assemble_device": [vp, C.c_int, C.c_double, RHS_FN, vp, vp, C.POINTER(vp)],
             "dgasm_system_dofs": [vp, i64p, ip],
             "dgasm_system_rhs": [vp, dp],
             "dgasm_system_blocks": [vp, i64p, ip, ip, dp],
@@ -197,7 +198,8 @@ class Mesh:
 
 
 class System:
-    def __init__(self, mesh: Mesh, p: int, c_sigma: float = 10.0, f=None):
+    def __init__(self, mesh: Mesh, p: int, c_sigma: float = 10.0, f=None, device=False, stream=None):
+        """device=True assembles the matrix on the GPU (dgasm_assemble_device)."""
         self.mesh = mesh  # keeps the mesh alive
         self.p = p
         h = C.c_void_p()
@@ -209,7 +211,10 @@ class System:
                 o[:] = f(pts)
             cb = RHS_FN(_cb)
         self._cb = cb
-        check(lib().dgasm_assemble(mesh.h, p, c_sigma, cb, None, C.byref(h)))
+        if device:
+            check(lib().dgasm_assemble_device(mesh.h, p, c_sigma, cb, None, _stream_ptr(stream), C.byref(h)))
+        else:
+            check(lib().dgasm_assemble(mesh.h, p, c_sigma, cb, None, C.byref(h)))
         self.h = h
         n = C.c_int64()
         npb = C.c_int()
