@@ -237,7 +237,7 @@ int Engine::precond(int mode, EventPairs* ev) {
   if (tot_bjac)
     DG_CUDA(timed_launch(PK_LOCAL, stream, ev, launches, [&] { return launch_bjac(B, tot_bjac, km, stream); }));
   DG_CUDA(cudaStreamWaitEvent(stream, ev_join, 0));
-  DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, km, stream); }));
+  DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, km, tot_rnn > 0, stream); }));
   return DGASM_OK;
 }
 

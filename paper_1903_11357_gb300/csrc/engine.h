@@ -117,7 +117,8 @@ int launch_coarse(const BatchDev& B, int total, int km, void* stream);
 // up and set the error word), err[1] = 1 (the wait returned false)
 int launch_wait_selftest(int* err, long long limit, void* stream);
 int launch_bjac(const BatchDev& B, int total, int km, void* stream);
-int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* stream);
+// nonnested: some problem of the batch has a non-nested coarse space
+int launch_pupdate(const BatchDev& B, int total, int mode, int km, int nonnested, void* stream);
 // r_0 = R_0 r for non-nested coarse spaces: one CTA per coarse cell (prefix slot K_RNN)
 int launch_restrict_nn(const BatchDev& B, int total, int km, void* stream);
 int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);

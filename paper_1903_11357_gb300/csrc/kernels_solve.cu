@@ -426,7 +426,9 @@ __global__ void __launch_bounds__(NTHREADS) k_bjac(BatchDev B) {
 }
 
 // ---- p = z + R_0^T z_0 + beta p, beta = (r, z)_new / (r, z)_old ----------------------------------
-template <int KM>
+// NN: the batch holds a non-nested coarse space (prolongation over (element, coarse cell) pairs); the
+// instantiation without it keeps the agglomerate path lean
+template <int KM, bool NN>
 __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
   __shared__ double beta_s[KMAX];
   __shared__ double gnew_s[KMAX];
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
     if (t < nel * np) {
       const int e = e_begin + t / np, a = t % np;
       const long long d = (long long)e * np + a;
-      const bool nn = nq > 0 && P.r0t_ptr != nullptr;
+      const bool nn = NN && nq > 0 && P.r0t_ptr != nullptr;
       const int J = nq > 0 && !nn ? P.agg_int[e] : 0;
 #pragma unroll
       for (int kk = 0; kk < KM; ++kk) {
@@ -619,9 +621,15 @@ int launch_bjac(const BatchDev& B, int total, int km, void* st) {
   return (int)cudaGetLastError();
 }
 
-int launch_pupdate(const BatchDev& B, int total, int mode, int km, void* st) {
-  if (km == 1) k_pupdate<1><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
-  else k_pupdate<KMAX><<<total, NTHREADS, 0, (cudaStream_t)st>>>(B, mode);
+int launch_pupdate(const BatchDev& B, int total, int mode, int km, int nonnested, void* st) {
+  cudaStream_t s = (cudaStream_t)st;
+  if (nonnested) {
+    if (km == 1) k_pupdate<1, true><<<total, NTHREADS, 0, s>>>(B, mode);
+    else k_pupdate<KMAX, true><<<total, NTHREADS, 0, s>>>(B, mode);
+  } else {
+    if (km == 1) k_pupdate<1, false><<<total, NTHREADS, 0, s>>>(B, mode);
+    else k_pupdate<KMAX, false><<<total, NTHREADS, 0, s>>>(B, mode);
+  }
   return (int)cudaGetLastError();
 }
 
