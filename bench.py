@@ -662,6 +662,31 @@ def main():
                 "iters": stm["iters"], "true_relres": stm["true_relres"], "rel_diff_vs_fp64": err,
                 "speedup_vs_fp64": (args.steps / tm) / (args.steps / elapsed), "kernels_one_step": breakdown_m}
 
+    def rhs_chunk_tuning():
+        """Eight right-hand sides on a problem with few subdomains (4096 cells, p = 3, 16 subdomains): the
+        local-solve work split into 1 or 4 right-hand sides per CTA pair, each timed, and the tuner's pick."""
+        from synth.voronoi import voronoi_mesh
+        mm = voronoi_mesh(4096, SEED)
+        Sx = dg.System(dg.Mesh.from_polymesh(mm, np.ones(mm.n_elem)), P_DEG, 10.0)
+        Px = dg.Prec(Sx, 16, 64, P_C, stream=stream)
+        Bx = torch.tensor(np.random.default_rng(3).standard_normal((8, Sx.ndof)), dtype=torch.float64, device="cuda")
+        res = {"case": "4096 cells, p=3, 16 subdomains, 64 agglomerates, 8 N(0,1) right-hand sides, FP64"}
+        for kc in (4, 1):
+            Px.set_rhs_chunk(8, kc)
+            for rep in range(2):
+                Xx = torch.zeros_like(Bx)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                Px.solve(Bx, Xx, rtol=1e-8, stream=stream)
+                torch.cuda.synchronize()
+                res[f"solve_ms_kc{kc}"] = 1000.0 * (time.perf_counter() - t0)
+        Px.set_rhs_chunk(8, 0)
+        Px.solve(Bx, torch.zeros_like(Bx), rtol=1e-8, stream=stream)
+        res["tuned_kc"] = Px.rhs_chunk(8)
+        return res
+
+    tuning = rhs_chunk_tuning() if rank == 0 else None
+
     mixed = mixed_tf32 = None
     if not args.no_mixed:
         mixed = run_mixed("fp32", "fp32 local factors, fp64 outer")
@@ -710,6 +735,7 @@ def main():
                   "stream_tiles": tiles, "factor_flops": info["factor_flops"]},
         "gpu_launches": int(launches),
         "assembly": asm,
+        "rhs_chunk_tuning": tuning,
         "kernels_one_step": breakdown,
         "roofline": roof,
         "e2e": {"value": world * args.steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": ndof * 8,

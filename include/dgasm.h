@@ -198,6 +198,14 @@ typedef struct {
 int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_prec_t* out);
 /* z = B r for nrhs vectors (device, caller's dof order, column-major ndof x nrhs). */
 int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, double* z, void* stream);
+/* Right-hand sides per local-solve work item for solves of nrhs right-hand sides (2 <= nrhs <= 8): 1 or 4.
+ * With 4, a pair of SMs streams each local factor once for 4 vectors; with 1 there are 4 times as many work
+ * items, which is faster when there are few subdomains.  0 (the default) lets the first dgasm_solve with that
+ * nrhs measure both (one warm-up and two timed preconditioner applications each) and keep the faster; both
+ * give bitwise the same solutions.  get returns the current choice (0 = not measured yet; 1 for nrhs = 1).
+ * Errors: DGASM_EINVAL. */
+int dgasm_prec_set_rhs_chunk(dgasm_prec_t pc, int nrhs, int kc);
+int dgasm_prec_get_rhs_chunk(dgasm_prec_t pc, int nrhs, int* kc);
 /* Partition actually used (host arrays [ne]); either pointer may be NULL; agg_of_elem is not written when
  * the coarse space lives on a coarse_mesh. */
 int dgasm_prec_partition(dgasm_prec_t pc, int* sub_of_elem, int* agg_of_elem);

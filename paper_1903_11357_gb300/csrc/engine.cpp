@@ -59,7 +59,7 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.epi_spmv = SPMV_THREADS / P.np;
   D.n_spmv_items = n_spmv_items;
   D.n_coarse_items = n_coarse_items;
-  D.kc = kk > 1 ? KC : 1;
+  D.kc = kk > 1 ? (pc.rhs_chunk[kk] ? pc.rhs_chunk[kk] : KC) : 1;
   D.n_rhs_chunks = (kk + D.kc - 1) / D.kc;
   D.fixed_iters = fixed;
   D.rtol = rtol;
@@ -470,6 +470,82 @@ int solve_all(Engine& E, int n, dgasm_prec_s* const* pcs, const int* nrhs, const
 using namespace dgasm;
 
 // ---- C entry points --------------------------------------------------------------------------------
+namespace dgasm {
+
+// z = B r with the engine of the preconditioner (internal: the caller holds pc->mu)
+int apply_locked(dgasm_prec_s* pc, int nrhs, const double* r, double* z, cudaStream_t stream) {
+  if (!pc->engine) pc->engine.reset(new (std::nothrow) Engine());
+  if (!pc->engine) return set_error(DGASM_ENOMEM, "host allocation failed");
+  dgasm_solve_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.maxit = 1;
+  dgasm_prec_s* arr[1] = {pc};
+  const double* bb[1] = {r};
+  double* xx[1] = {z};
+  Engine& E = *pc->engine;
+  const dgasm_solve_opts* os[1] = {&o};
+  DG_TRY(E.build(1, arr, &nrhs, bb, xx, os, stream, -1));
+  DG_TRY(E.reset_state());
+  // a zero right-hand side is finished by the initial step, and p keeps its old contents: clear it
+  DG_CUDA(cudaMemsetAsync(E.hp[0].p, 0, sizeof(double) * (size_t)pc->ws.k * pc->P.ne * pc->P.np, stream));
+  DG_TRY(E.init());
+  DG_TRY(E.apply_out());
+  return DGASM_OK;
+}
+
+// The local-solve kernel can give each CTA pair 1 or KC right-hand sides.  KC reads each factor once for KC
+// vectors; 1 gives KC times as many CTA pairs, which wins when there are few subdomains.  The choice is
+// measured once per (preconditioner, k): one warm-up and two timed applications of b per candidate.  Both
+// choices add the same products in the same order for every right-hand side, so the solution does not
+// depend on the outcome (tested bitwise).
+int tune_rhs_chunk(dgasm_prec_s* pc, int nrhs, const double* b, cudaStream_t stream) {
+  if (nrhs <= 1 || pc->rhs_chunk[nrhs] != 0 || pc->blocks) return DGASM_OK;
+  const size_t n = (size_t)pc->P.ne * pc->P.np * nrhs;
+  DevBuf z;
+  DG_TRY(z.alloc(n * sizeof(double)));
+  cudaEvent_t e0, e1;
+  DG_CUDA(cudaEventCreate(&e0));
+  DG_CUDA(cudaEventCreate(&e1));
+  const int cand[2] = {KC, 1};
+  float best = 0.f;
+  int pick = KC, rc = DGASM_OK;
+  for (int c = 0; c < 2 && rc == DGASM_OK; ++c) {
+    pc->rhs_chunk[nrhs] = cand[c];
+    rc = apply_locked(pc, nrhs, b, z.as<double>(), stream);
+    if (rc) break;
+    cudaEventRecord(e0, stream);
+    for (int r = 0; r < 2 && rc == DGASM_OK; ++r) rc = apply_locked(pc, nrhs, b, z.as<double>(), stream);
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_error((int)cudaGetLastError(), "right-hand-side chunk tuning");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (c == 0 || ms < best) { best = ms; pick = cand[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pc->rhs_chunk[nrhs] = rc == DGASM_OK ? pick : 0;
+  return rc;
+}
+
+}  // namespace dgasm
+
+extern "C" int dgasm_prec_set_rhs_chunk(dgasm_prec_t pc, int nrhs, int kc) {
+  clear_error();
+  if (!pc || nrhs < 1 || nrhs > KMAX) return set_error(DGASM_EINVAL, "dgasm_prec_set_rhs_chunk: bad arguments");
+  if (kc != 0 && kc != 1 && kc != KC) return set_error(DGASM_EINVAL, "kc=%d must be 0 (tune), 1 or %d", kc, KC);
+  std::lock_guard<std::mutex> lk(pc->mu);
+  pc->rhs_chunk[nrhs] = kc;
+  return DGASM_OK;
+}
+
+extern "C" int dgasm_prec_get_rhs_chunk(dgasm_prec_t pc, int nrhs, int* kc) {
+  clear_error();
+  if (!pc || !kc || nrhs < 1 || nrhs > KMAX) return set_error(DGASM_EINVAL, "dgasm_prec_get_rhs_chunk: bad arguments");
+  std::lock_guard<std::mutex> lk(pc->mu);
+  *kc = nrhs == 1 ? 1 : pc->rhs_chunk[nrhs];
+  return DGASM_OK;
+}
+
 extern "C" int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x, const dgasm_solve_opts* o,
                            dgasm_stats* st) {
   clear_error();
@@ -487,6 +563,7 @@ extern "C" int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x
     double* dx = db + n;
     DG_CUDA(cudaMemcpyAsync(db, b, n * sizeof(double), cudaMemcpyHostToDevice, stream));
     if (o->x0_given) DG_CUDA(cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, stream));
+    DG_TRY(tune_rhs_chunk(pc, nrhs, db, stream));
     const double* bb[1] = {db};
     double* xx[1] = {dx};
     int rc = solve_all(*pc->engine, 1, arr, &nrhs, bb, xx, o, stream, st);
@@ -495,6 +572,7 @@ extern "C" int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x
     DG_CUDA(cudaStreamSynchronize(stream));
     return rc;
   }
+  DG_TRY(tune_rhs_chunk(pc, nrhs, b, stream));
   const double* bb[1] = {b};
   double* xx[1] = {x};
   return solve_all(*pc->engine, 1, arr, &nrhs, bb, xx, o, stream, st);
@@ -524,23 +602,8 @@ extern "C" int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, doub
   if (!pc || !r || !z) return set_error(DGASM_EINVAL, "dgasm_prec_apply: NULL argument");
   if (nrhs < 1 || nrhs > KMAX) return set_error(DGASM_EINVAL, "nrhs=%d must lie in [1, %d]", nrhs, KMAX);
   std::lock_guard<std::mutex> lk(pc->mu);
-  if (!pc->engine) pc->engine.reset(new (std::nothrow) Engine());
-  if (!pc->engine) return set_error(DGASM_ENOMEM, "host allocation failed");
   cudaStream_t stream = stream_ ? (cudaStream_t)stream_ : pc->stream;
-  dgasm_solve_opts o;
-  std::memset(&o, 0, sizeof(o));
-  o.maxit = 1;
-  dgasm_prec_s* arr[1] = {pc};
-  const double* bb[1] = {r};
-  double* xx[1] = {z};
-  Engine& E = *pc->engine;
-  const dgasm_solve_opts* os[1] = {&o};
-  DG_TRY(E.build(1, arr, &nrhs, bb, xx, os, stream, -1));
-  DG_TRY(E.reset_state());
-  // a zero right-hand side is finished by the initial step, and p keeps its old contents: clear it
-  DG_CUDA(cudaMemsetAsync(E.hp[0].p, 0, sizeof(double) * (size_t)pc->ws.k * pc->P.ne * pc->P.np, stream));
-  DG_TRY(E.init());
-  DG_TRY(E.apply_out());
+  DG_TRY(apply_locked(pc, nrhs, r, z, stream));
   DG_CUDA(cudaStreamSynchronize(stream));
   return DGASM_OK;
 }

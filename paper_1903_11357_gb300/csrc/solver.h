@@ -89,6 +89,10 @@ int solve_all(Engine& E, int n, dgasm_prec_s* const* pcs, const int* nrhs, const
 int prec_plan(dgasm_system_s* s, const dgasm_setup_opts* o, std::unique_ptr<dgasm_prec_s>& pc);
 size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit);
 int prec_build(dgasm_prec_s* pc);
+// times one preconditioner application of b with each right-hand-side chunking and keeps the faster
+int tune_rhs_chunk(dgasm_prec_s* pc, int nrhs, const double* b, cudaStream_t stream);
+// z = B r (the caller holds pc->mu)
+int apply_locked(dgasm_prec_s* pc, int nrhs, const double* r, double* z, cudaStream_t stream);
 
 }  // namespace dgasm
 
@@ -105,6 +109,9 @@ struct dgasm_prec_s {
   dgasm::DevBuf perm, rowptr, col, vals, src_blk, sub_e0, scale, Lr, Lc, grp_ptr, grp_elems, agg_int, r0t, A0inv, err, io;
   dgasm::DevBuf r0t_ptr, r0t_col, r0t_elem, rT_ptr, rT_pair;   // non-nested coarse space: R_0^T pairs
   dgasm::R0TPairs nn;       // host copy of the pairs between the plan and the upload
+  // right-hand sides per local-solve item for a solve of k right-hand sides: 0 = not chosen yet (the default
+  // KC, tuned by the first dgasm_solve with k > 1), else 1 or KC
+  int rhs_chunk[dgasm::KMAX + 1] = {0};
   bool blocks = false;      // every subdomain is one element: local solves with explicit block inverses
   dgasm::DevBuf dinv;       // [ne][np][np] FP64, internal element order
   dgasm::EnvBufs env, env0;

@@ -89,6 +89,8 @@ def lib():
             "dgasm_prec_apply": [vp, C.c_int, vp, vp, vp],
             "dgasm_prec_partition": [vp, ip, ip],
             "dgasm_prec_footprint": [vp, i64p],
+            "dgasm_prec_set_rhs_chunk": [vp, C.c_int, C.c_int],
+            "dgasm_prec_get_rhs_chunk": [vp, C.c_int, ip],
             "dgasm_prec_destroy": [vp],
             "dgasm_solve": [vp, C.c_int, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats)],
             "dgasm_solve_batch": [C.c_int, C.POINTER(vp), ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
@@ -267,6 +269,16 @@ class Prec:
         check(lib().dgasm_setup(system.h, C.byref(o), C.byref(h)))
         self.h = h
         self.ndof = system.ndof
+
+    def set_rhs_chunk(self, nrhs, kc):
+        """Right-hand sides per local-solve item for nrhs-vector solves: 1, 4, or 0 to let the first solve
+        measure both."""
+        check(lib().dgasm_prec_set_rhs_chunk(self.h, int(nrhs), int(kc)))
+
+    def rhs_chunk(self, nrhs):
+        v = C.c_int()
+        check(lib().dgasm_prec_get_rhs_chunk(self.h, int(nrhs), C.byref(v)))
+        return v.value
 
     def apply(self, r, z, stream=None):
         k = 1 if r.dim() == 1 else r.shape[0]

@@ -211,3 +211,25 @@ def test_batch_equals_alone():
     assert rc == 0
     for a, b in zip(xs_alone, xs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rhs_chunk_choices_give_identical_solutions(precision):
+    """1 or 4 right-hand sides per local-solve item: the same products in the same order for every vector,
+    so the tuner's (timing-dependent) choice cannot change a solution."""
+    c = build_case(300, 4, 2, 4, 16, precision=precision)
+    B = dev(np.random.default_rng(8).standard_normal((3, len(c["b"]))))
+    out = {}
+    for kc in (1, 4):
+        c["P"].set_rhs_chunk(3, kc)
+        X = torch.zeros_like(B)
+        rc, st = c["P"].solve(B, X, rtol=1e-8)
+        assert rc == 0
+        out[kc] = (X, [s["iters"] for s in st])
+    assert torch.equal(out[1][0], out[4][0]) and out[1][1] == out[4][1]
+    c["P"].set_rhs_chunk(3, 0)
+    assert c["P"].rhs_chunk(3) == 0
+    X = torch.zeros_like(B)
+    rc, st = c["P"].solve(B, X, rtol=1e-8)
+    assert rc == 0 and c["P"].rhs_chunk(3) in (1, 4)
+    assert torch.equal(X, out[1][0])
