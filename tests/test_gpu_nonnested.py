@@ -104,3 +104,24 @@ def test_example4_trends_p1():
     assert 1 / 1.5 <= k_4096_256 / k_1024_64 <= 1.5      # paper: 106.42 vs 100.89
     assert 2.5 <= k_4096_64 / k_1024_64 <= 6.0           # paper: 411.02 / 106.42 = 3.9
     assert 50 <= it_4096_64 <= 400                        # paper: 167 iterations
+
+
+def test_server_mixes_nested_and_nonnested_requests():
+    """A non-nested request admitted next to a nested one gives the bits of its solve alone."""
+    nn = build_case(256, 16, 2, 1, 4)
+    m = mesh(300, 3)
+    S2 = dg.System(dg.Mesh.from_polymesh(m, np.ones(300)), 3, 10.0, f=f_sin)
+    b1, b2 = dev(nn["b"]), dev(S2.rhs())
+    x1a = torch.zeros_like(b1)
+    nn["P"].solve(b1, x1a)
+    x2a = torch.zeros_like(b2)
+    dg.Prec(S2, 4, 16, 1).solve(b2, x2a)
+    sv = dg.Server(hbm_budget=4 << 30, max_slots=2)
+    x1, x2 = torch.zeros_like(b1), torch.zeros_like(b2)
+    t1 = sv.submit(nn["S"], 4, 0, 1, b1, x1, coarse_mesh=nn["CM"])
+    t2 = sv.submit(S2, 4, 16, 1, b2, x2)
+    for t in (t1, t2):
+        rc, st = sv.wait(t, 60000)
+        assert rc == 0 and all(s["converged"] for s in st)
+    assert torch.equal(x1, x1a) and torch.equal(x2, x2a)
+    sv.close()
