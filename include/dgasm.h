@@ -198,6 +198,14 @@ typedef struct {
 int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_prec_t* out);
 /* z = B r for nrhs vectors (device, caller's dof order, column-major ndof x nrhs). */
 int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, double* z, void* stream);
+/* The R_0^T of a non-nested coarse mesh as dgasm_setup builds it (Eq. R0T over the clipped intersections of the
+ * fine element kappa with the coarse cells D_j), on the host, in the caller's element order: *npair pairs
+ * (kappa, j); ptr [ne+1] the pairs of each fine element, col [npair] their coarse cells (ascending), blocks
+ * [npair][n_p][n_q] (row a = fine basis function, column c = coarse one) = M_kappa^{-1} int_{kappa cap D_j} phi_a
+ * psi_c.  Call with NULL arrays to get *npair first.  1 <= q <= p <= 8.  Errors: DGASM_EINVAL (bad degrees, a
+ * cell that overlaps nothing). */
+int dgasm_nonnested_prolongation(dgasm_mesh_t fine, dgasm_mesh_t coarse, int p, int q, int64_t* npair, int* ptr,
+                                 int* col, double* blocks);
 /* Right-hand sides per local-solve work item for solves of nrhs right-hand sides (2 <= nrhs <= 8): 1 or 4.
  * With 4, a pair of SMs streams each local factor once for 4 vectors; with 1 there are 4 times as many work
  * items, which is faster when there are few subdomains.  0 (the default) lets the first dgasm_solve with that

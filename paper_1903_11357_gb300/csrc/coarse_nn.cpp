@@ -238,3 +238,21 @@ int nonnested_r0t(const MeshData& f, const std::vector<int>& perm, const MeshDat
 }
 
 }  // namespace dgasm
+
+// Host query of the non-nested R_0^T blocks in the caller's element order (no device work)
+extern "C" int dgasm_nonnested_prolongation(dgasm_mesh_t fine, dgasm_mesh_t coarse, int p, int q, int64_t* npair,
+                                            int* ptr, int* col, double* blocks) {
+  using namespace dgasm;
+  clear_error();
+  if (!fine || !coarse || !npair) return set_error(DGASM_EINVAL, "dgasm_nonnested_prolongation: NULL argument");
+  if (p < 1 || p > 8 || q < 1 || q > p) return set_error(DGASM_EINVAL, "need 1 <= q <= p <= 8 (p=%d, q=%d)", p, q);
+  std::vector<int> perm(fine->m.ne);
+  for (int i = 0; i < fine->m.ne; ++i) perm[i] = i;
+  R0TPairs out;
+  DG_TRY(nonnested_r0t(fine->m, perm, coarse->m, p, q, out));
+  *npair = (int64_t)out.col.size();
+  if (ptr) std::copy(out.ptr.begin(), out.ptr.end(), ptr);
+  if (col) std::copy(out.col.begin(), out.col.end(), col);
+  if (blocks) std::copy(out.blocks.begin(), out.blocks.end(), blocks);
+  return DGASM_OK;
+}

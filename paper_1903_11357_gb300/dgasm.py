@@ -90,6 +90,7 @@ def lib():
             "dgasm_prec_partition": [vp, ip, ip],
             "dgasm_prec_footprint": [vp, i64p],
             "dgasm_prec_set_rhs_chunk": [vp, C.c_int, C.c_int],
+            "dgasm_nonnested_prolongation": [vp, vp, C.c_int, C.c_int, i64p, ip, ip, dp],
             "dgasm_prec_get_rhs_chunk": [vp, C.c_int, ip],
             "dgasm_prec_destroy": [vp],
             "dgasm_solve": [vp, C.c_int, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats)],
@@ -354,6 +355,18 @@ def selftest_bounded_wait(limit_ms=5.0):
     ms = C.c_double()
     check(lib().dgasm_selftest_bounded_wait(float(limit_ms), C.byref(g), C.byref(ms)))
     return bool(g.value), ms.value
+
+
+def nonnested_prolongation(fine: "Mesh", coarse: "Mesh", p: int, q: int):
+    """R_0^T of a non-nested coarse mesh (host): (ptr [ne+1], col [npair], blocks [npair, n_p, n_q])."""
+    n = C.c_int64()
+    check(lib().dgasm_nonnested_prolongation(fine.h, coarse.h, p, q, C.byref(n), None, None, None))
+    ptr = np.empty(fine.ne + 1, np.int32)
+    col = np.empty(n.value, np.int32)
+    nb, nq = (p + 1) * (p + 2) // 2, (q + 1) * (q + 2) // 2
+    blk = np.empty(n.value * nb * nq)
+    check(lib().dgasm_nonnested_prolongation(fine.h, coarse.h, p, q, C.byref(n), _ip(ptr), _ip(col), _dp(blk)))
+    return ptr, col, blk.reshape(-1, nb, nq)
 
 
 def selftest_tc_update(tiles):

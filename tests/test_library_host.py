@@ -100,3 +100,26 @@ def test_last_error_roundtrip():
     dg.lib().dgasm_partition(None, 1, 0, None, None)
     assert dg.lib().dgasm_last_error(buf, 64) == dg.EINVAL
     assert b"NULL" in buf.value
+
+
+@pytest.mark.parametrize("nf,nc,p,q", [(300, 20, 2, 1), (200, 12, 3, 3), (150, 40, 2, 2)])
+def test_nonnested_prolongation_matches_oracle(nf, nc, p, q):
+    """The library's host R_0^T of a non-nested coarse mesh (the blocks dgasm_setup uploads) against the
+    oracle's, computed independently from Eq. R0T."""
+    from oracle import schwarz
+    from oracle.basis import n_basis
+    from oracle.geometry import build_geometry
+    fm, cm = mesh(nf, 1), mesh(nc, 21)
+    F = dg.Mesh.from_polymesh(fm, np.ones(nf))
+    Cm = dg.Mesh.from_polymesh(cm, np.ones(nc))
+    ptr, col, blk = dg.nonnested_prolongation(F, Cm, p, q)
+    nb, nq = n_basis(p), n_basis(q)
+    L = np.zeros((nf * nb, nc * nq))
+    for e in range(nf):
+        assert np.all(np.diff(col[ptr[e]:ptr[e + 1]]) > 0)   # ascending coarse cells
+        for t in range(ptr[e], ptr[e + 1]):
+            L[e * nb:(e + 1) * nb, col[t] * nq:(col[t] + 1) * nq] = blk[t]
+    O = schwarz.prolongation_nonnested(fm, build_geometry(fm), cm, build_geometry(cm), p, q).toarray()
+    assert np.abs(L - O).max() <= 1e-12 * np.abs(O).max()
+    with pytest.raises(dg.DgasmError):
+        dg.nonnested_prolongation(F, Cm, 2, 3)   # q > p
