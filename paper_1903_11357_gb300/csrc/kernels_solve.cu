@@ -59,6 +59,17 @@ __device__ void block_sum_k(const double* v, int k, double* red /*[NWB][KMAX]*/,
   __syncthreads();
 }
 
+// the problem descriptor in shared memory: one coalesced copy per CTA, so the kernel's many field reads
+// (and the pointer chains that start from them) do not each pay a global-memory round trip
+static_assert(sizeof(ProbDev) % 8 == 0, "ProbDev is copied as 8-byte words");
+__device__ __forceinline__ const ProbDev& stage_prob(const ProbDev* src, ProbDev* dst) {
+  constexpr int W = (int)(sizeof(ProbDev) / 8);
+  for (int i = threadIdx.x; i < W; i += blockDim.x)
+    reinterpret_cast<long long*>(dst)[i] = reinterpret_cast<const long long*>(src)[i];
+  __syncthreads();
+  return *dst;
+}
+
 // sum of v[i * stride] for i < n by one warp, in a fixed order (lane-strided partial sums, then a fixed
 // shuffle tree); every lane returns the total
 __device__ __forceinline__ double warp_sum_strided(const double* v, int n, int stride) {
@@ -137,8 +148,9 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv(BatchDev B, int operand, 
   __shared__ double red[SW * KMAX];
   __shared__ double tot[KMAX];
   __shared__ int lastf;
+  __shared__ __align__(16) ProbDev Ps;
   const int pi = find_prob(B.prefix[slot], B.nprob, blockIdx.x);
-  const ProbDev& P = B.probs[pi];
+  const ProbDev& P = stage_prob(B.probs + pi, &Ps);
   const int item = blockIdx.x - B.prefix[slot][pi];
   const int k = P.k;
   bool act[KM];
@@ -181,8 +193,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
   __shared__ double red[UPD_NW * KMAX];
   __shared__ double tot[KMAX];
   __shared__ int lastf;
+  __shared__ __align__(16) ProbDev Ps;
   const int pi = find_prob(B.prefix[K_GRP], B.nprob, blockIdx.x);
-  const ProbDev& P = B.probs[pi];
+  const ProbDev& P = stage_prob(B.probs + pi, &Ps);
   const int g = blockIdx.x - B.prefix[K_GRP][pi];
   const int k = P.k, np = P.np, nq = P.nq;
   bool act[KM];
@@ -433,8 +446,9 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
   __shared__ double beta_s[KMAX];
   __shared__ double gnew_s[KMAX];
   __shared__ int lastf;
+  __shared__ __align__(16) ProbDev Ps;
   const int pi = find_prob(B.prefix[K_SPMV], B.nprob, blockIdx.x);
-  const ProbDev& P = B.probs[pi];
+  const ProbDev& P = stage_prob(B.probs + pi, &Ps);
   const int item = blockIdx.x - B.prefix[K_SPMV][pi];
   const int k = P.k, np = P.np, nq = P.nq;
   bool act[KM];
