@@ -28,7 +28,8 @@ int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
   n_chunk_items = (P.ne + epi - 1) / epi;
   const int epis = SPMV_THREADS / P.np;
   n_spmv_items = (P.ne + epis - 1) / epis;
-  n_coarse_items = n0 > 0 ? (n0 + 7) / 8 : 0;
+  const int rows_per_item = COARSE_ROWS_PER_WARP * (NTHREADS / 32);
+  n_coarse_items = n0 > 0 ? (n0 + rows_per_item - 1) / rows_per_item : 0;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
   o_vec = take(sizeof(double) * 6 * k * ndof);

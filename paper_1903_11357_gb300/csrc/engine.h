@@ -18,6 +18,7 @@ constexpr int SUPER_ROW_MAX = 8;   // tile rows per super-row of the local trian
 // solve) and FP32 (139 vs 158 us), and 16 gained FP32 only 3%.
 constexpr int super_row(int /*prec*/) { return 8; }
 constexpr long long ZERO_TILE = -(1LL << 62);   // solve-stream entry: a tile of zeros
+constexpr int COARSE_ROWS_PER_WARP = 4;          // k_coarse: rows of A_0^{-1} per warp (32 per CTA)
 
 enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
 constexpr int K_SPMV_P = K_NKINDS + 8;   // per-degree SpMV prefix slots p = 1..8

@@ -356,7 +356,6 @@ __global__ void __launch_bounds__(NTHREADS) k_coarse(BatchDev B) {
   const int item = blockIdx.x - B.prefix[K_COARSE][pi];
   const int k = P.k, n0 = P.n0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int row = item * NW + w;
   bool act[KM];
   bool any = false;
 #pragma unroll
@@ -365,31 +364,38 @@ __global__ void __launch_bounds__(NTHREADS) k_coarse(BatchDev B) {
     any |= act[kk];
   }
   if (!any) return;
-  double acc[KM];
+  double prod[KM];
 #pragma unroll
-  for (int kk = 0; kk < KM; ++kk) acc[kk] = 0.0;
-  if (row < n0) {
-    const double* Arow = P.A0inv + (long long)row * n0;
-    for (int j = lane; j < n0; j += 32) {
-      const double a = __ldg(Arow + j);
+  for (int kk = 0; kk < KM; ++kk) prod[kk] = 0.0;
+  // COARSE_ROWS_PER_WARP rows per warp, so that the GEMV of a 768-row A_0^{-1} takes 24 CTAs: the SMs the
+  // local-solve clusters leave free, instead of SMs a cluster then has to wait for
+  for (int i = 0; i < COARSE_ROWS_PER_WARP; ++i) {
+    const int row = (item * COARSE_ROWS_PER_WARP + i) * NW + w;
+    double acc[KM];
 #pragma unroll
-      for (int kk = 0; kk < KM; ++kk)
-        if (act[kk]) acc[kk] = fma(a, P.r0[(long long)kk * n0 + j], acc[kk]);
-    }
-  }
+    for (int kk = 0; kk < KM; ++kk) acc[kk] = 0.0;
+    if (row < n0) {
+      const double* Arow = P.A0inv + (long long)row * n0;
+      for (int j = lane; j < n0; j += 32) {
+        const double a = __ldg(Arow + j);
 #pragma unroll
-  for (int kk = 0; kk < KM; ++kk) {
-    if (kk >= k) break;
-    double v = warp_sum(acc[kk]);
-    if (lane == 0) {
-      double prod = 0.0;
-      if (row < n0 && act[kk]) {
-        P.z0[(long long)kk * n0 + row] = v;
-        prod = v * P.r0[(long long)kk * n0 + row];
+        for (int kk = 0; kk < KM; ++kk)
+          if (act[kk]) acc[kk] = fma(a, P.r0[(long long)kk * n0 + j], acc[kk]);
       }
-      wpart[w][kk] = prod;
+    }
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) {
+      if (kk >= k) break;
+      const double v = warp_sum(acc[kk]);
+      if (lane == 0 && row < n0 && act[kk]) {
+        P.z0[(long long)kk * n0 + row] = v;
+        prod[kk] += v * P.r0[(long long)kk * n0 + row];
+      }
     }
   }
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk)
+    if (kk < k && lane == 0) wpart[w][kk] = prod[kk];
   __syncthreads();
   if (threadIdx.x < k) {
     double s = 0.0;
