@@ -421,16 +421,20 @@ def run_sweep(args):
 
 # Sec. 7, Example 4 (independent Voronoi grids, rho = 1): K(P_ad) (iterations) for p = q, by fine element
 # count N_h (columns) and coarse element count N_H (rows).  Context only: the paper's meshes are not published.
-PAPER_EX4 = {
-    1: {16: {64: (23.29, 38), 256: (92.13, 77), 1024: (387.61, 159), 4096: (1624.26, 324), 16384: (6370.86, 657)},
-        64: {256: (25.91, 39), 1024: (106.42, 84), 4096: (411.02, 167), 16384: (1774.19, 342)},
-        256: {1024: (26.73, 41), 4096: (100.89, 82), 16384: (425.97, 169)},
-        1024: {4096: (31.81, 44), 16384: (118.61, 86)}, 4096: {16384: (30.56, 43)}},
-    3: {16: {64: (148.36, 83), 256: (429.84, 143), 1024: (1602.53, 275), 4096: (5405.40, 529), 16384: (21263.66, 1058)},
-        64: {256: (142.42, 76), 1024: (405.44, 135), 4096: (1525.94, 263), 16384: (5170.13, 498)},
-        256: {1024: (157.47, 80), 4096: (452.41, 137), 16384: (1469.08, 249)},
-        1024: {4096: (147.97, 77), 16384: (402.98, 124)}, 4096: {16384: (135.77, 70)}},
-}
+def paper_table(example, p):
+    """The paper's printed K(P_ad) and iteration counts (Sec. 7, Example 2: nested grids, Example 4: non-nested
+    grids; p = q), from the cited fixtures in tests/golden: {(N_h, N_H): (K, iterations)}."""
+    out = {}
+    path = os.path.join(ROOT, "tests", "golden", f"paper_example{example}_p{p}.txt")
+    if not os.path.exists(path):
+        return out
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            nh, nH, K, it = line.split()
+            out[(int(nh), int(nH))] = (float(K), int(it))
+    return out
 
 
 def run_paper(args):
@@ -438,8 +442,8 @@ def run_paper(args):
     local solves), q = p, rho = 1, C_sigma = 10, rtol 1e-8 from x0 = 0 with an N(0,1) right-hand side; K(P_ad)
     from the Lanczos estimate.  Fine meshes of 256 .. 16384 cells; coarse spaces of 16 .. 1024 cells
     (n_0 <= 3072) of two kinds: RCB agglomerates of the fine mesh (nested) and an independently generated
-    Voronoi mesh (non-nested, Example 4's setting, seed 7); p = q = 1 and 3.  The paper's Example 4 numbers
-    (its own meshes and machine) are attached to the non-nested rows as context."""
+    Voronoi mesh (non-nested, Example 4's setting, seed 7); p = q = 1 and 3.  The paper's numbers (its own
+    meshes and machine) are attached as context: Example 2 to the nested rows, Example 4 to the non-nested ones."""
     from synth.voronoi import voronoi_mesh
     import torch
     from paper_1903_11357_gb300 import dgasm as dg
@@ -472,10 +476,12 @@ def run_paper(args):
                         rc, st = P.solve(b, x, rtol=1e-8, maxit=20000, stream=stream)
                         torch.cuda.synchronize()
                         dt = time.perf_counter() - t0
-                    ctx = PAPER_EX4.get(p, {}).get(nH, {}).get(nh) if cm is not None else None
+                    ctx = paper_table(4 if cm is not None else 2, p).get((nh, nH))
                     rows.append({"N_h": nh, "N_H": nH, "p": p, "coarse": kind, "rc": rc, "iters": st[0]["iters"],
                                  "kappa": st[0]["kappa"], "true_relres": st[0]["true_relres"], "ms": 1000 * dt,
-                                 "paper_ex4_kappa_iters": ctx})
+                                 "paper_kappa_iters": ctx,
+                                 "paper_table": ("Example 4 (non-nested)" if cm is not None else "Example 2 (nested)")
+                                 if ctx else None})
                     if (nh, nH, p, kind) == (16384, 256, 3, "nested"):
                         t_ref = dt
                     del P

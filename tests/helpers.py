@@ -27,3 +27,19 @@ def have_gpu():
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def paper_table(example: int, p: int):
+    """The paper's printed K(P_ad) and iteration counts (Sec. 7, Example 2 or 4, p = q), from the cited
+    fixture tests/golden/paper_example{example}_p{p}.txt: {(N_h, N_H): (K, iterations)}."""
+    out = {}
+    with open(f"{GOLDEN}/paper_example{example}_p{p}.txt") as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            nh, nH, K, it = line.split()
+            out[(int(nh), int(nH))] = (float(K), int(it))
+    return out

@@ -11,7 +11,7 @@ import pytest
 from oracle import partition, pcg, schwarz, sipg
 from oracle.geometry import build_geometry
 from synth.voronoi import voronoi_mesh
-from tests.helpers import f_sin, have_gpu, mesh
+from tests.helpers import f_sin, have_gpu, mesh, paper_table
 
 pytestmark = pytest.mark.gpu
 
@@ -98,12 +98,14 @@ def K_nonnested(nh, nH, p):
 
 
 def test_example4_trends_p1():
+    T = paper_table(4, 1)   # the paper's non-nested table (Example 4, p = q = 1)
     k_1024_64, _ = K_nonnested(1024, 64, 1)
     k_4096_256, _ = K_nonnested(4096, 256, 1)
     k_4096_64, it_4096_64 = K_nonnested(4096, 64, 1)
-    assert 1 / 1.5 <= k_4096_256 / k_1024_64 <= 1.5      # paper: 106.42 vs 100.89
-    assert 2.5 <= k_4096_64 / k_1024_64 <= 6.0           # paper: 411.02 / 106.42 = 3.9
-    assert 50 <= it_4096_64 <= 400                        # paper: 167 iterations
+    # N_h / N_H fixed (paper 100.89 / 106.42) and N_h x 4 at fixed N_H (paper 411.02 / 106.42): same ratios
+    assert 1 / 1.5 <= (k_4096_256 / k_1024_64) / (T[4096, 256][0] / T[1024, 64][0]) <= 1.5
+    assert 0.6 <= (k_4096_64 / k_1024_64) / (T[4096, 64][0] / T[1024, 64][0]) <= 1.6
+    assert 0.5 * T[4096, 64][1] <= it_4096_64 <= 2.0 * T[4096, 64][1]   # paper: 167 iterations
 
 
 def test_server_mixes_nested_and_nonnested_requests():

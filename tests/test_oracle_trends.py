@@ -17,6 +17,7 @@ import pytest
 from oracle import partition, pcg, schwarz, sipg
 from oracle.geometry import build_geometry
 from synth.voronoi import voronoi_mesh
+from tests.helpers import paper_table
 
 
 def paper_mode_K(n, n_coarse, p, q, seed=1, rho_fn=None):
@@ -33,13 +34,20 @@ def paper_mode_K(n, n_coarse, p, q, seed=1, rho_fn=None):
     return pcg.condition_estimate(res), res.iters
 
 
+def ratio_close(ours, paper, lo, hi):
+    """Our trend ratio against the paper's (its meshes differ, so only the ratio is compared)."""
+    return lo <= ours / paper <= hi
+
+
 @pytest.mark.slow
 def test_example2_h_over_H():
+    T = paper_table(2, 1)
     k_256_16, _ = paper_mode_K(256, 16, 1, 1)
     k_1024_64, _ = paper_mode_K(1024, 64, 1, 1)
     k_1024_16, _ = paper_mode_K(1024, 16, 1, 1)
-    assert 1 / 1.5 <= k_1024_64 / k_256_16 <= 1.5          # diagonal of the table: H/h fixed
-    assert 2.5 <= k_1024_16 / k_256_16 <= 6.0              # along a row: h halves at fixed H
+    # diagonal of the table (H/h fixed): paper 73.42 / 72.31; along a row (h halves at fixed H): 269.70 / 72.31
+    assert ratio_close(k_1024_64 / k_256_16, T[1024, 64][0] / T[256, 16][0], 1 / 1.5, 1.5)
+    assert ratio_close(k_1024_16 / k_256_16, T[1024, 16][0] / T[256, 16][0], 0.6, 1.6)
 
 
 def test_example1_alignment():
@@ -72,8 +80,10 @@ def paper_mode_K_nonnested(n, n_coarse, p, q, seed=1, coarse_seed=7):
 
 
 def test_example4_nonnested_h_over_H():
+    T = paper_table(4, 1)
     k_64_16, _ = paper_mode_K_nonnested(64, 16, 1, 1)
     k_256_64, _ = paper_mode_K_nonnested(256, 64, 1, 1)
     k_256_16, _ = paper_mode_K_nonnested(256, 16, 1, 1)
-    assert 1 / 1.5 <= k_256_64 / k_64_16 <= 1.5            # H/h fixed
-    assert 2.5 <= k_256_16 / k_64_16 <= 6.0                # h halves at fixed H
+    # H/h fixed: paper 25.91 / 23.29; h halves at fixed H: 92.13 / 23.29
+    assert ratio_close(k_256_64 / k_64_16, T[256, 64][0] / T[64, 16][0], 1 / 1.5, 1.5)
+    assert ratio_close(k_256_16 / k_64_16, T[256, 16][0] / T[64, 16][0], 0.6, 1.6)
