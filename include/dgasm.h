@@ -198,6 +198,11 @@ typedef struct {
 int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_prec_t* out);
 /* z = B r for nrhs vectors (device, caller's dof order, column-major ndof x nrhs). */
 int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, double* z, void* stream);
+/* Consistency self-check of the host plan dgasm_setup would build for nsub RCB subdomains (no device work): the
+ * tensor-core trailing-update groups cover exactly the plain update tasks of every Cholesky step, and every
+ * subdomain's forward and backward solve streams and run tables match their definitions from the tile envelope.
+ * *violations = number of mismatches (0 expected); *checks = entries compared.  Errors: DGASM_EINVAL. */
+int dgasm_selftest_plan(dgasm_system_t s, int nsub, int64_t* violations, int64_t* checks);
 /* The R_0^T of a non-nested coarse mesh as dgasm_setup builds it (Eq. R0T over the clipped intersections of the
  * fine element kappa with the coarse cells D_j), on the host, in the caller's element order: *npair pairs
  * (kappa, j); ptr [ne+1] the pairs of each fine element, col [npair] their coarse cells (ascending), blocks

@@ -9,7 +9,9 @@
 #include <numeric>
 #include <queue>
 #include <thread>
+#include <tuple>
 
+#include "engine.h"
 #include "plan.h"
 
 namespace dgasm {
@@ -369,4 +371,86 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   return DGASM_OK;
 }
 
+// Consistency checks of an envelope against its own definitions (for tests; no device work):
+//  * the tensor-core update groups of every step K cover exactly the plain update tasks (s, I, J), I >= J,
+//    each block inside the panel and targets inside the envelope right of K;
+//  * each subdomain's forward stream is, per super-row q and row o, the factor tiles (I0+o, J), J = F .. I0-1,
+//    then the inverse-block tiles (o, j), j <= o; the backward stream, per super-row q descending and column
+//    o, the tiles (I, I0+o) of the rows below from the first to the last that reach column I0+o (zero tiles
+//    in between where a row does not), then the inverse-block tiles (i, o), i >= o; run tables match.
+// Returns the number of violations; *checks counts what was compared.
+long long check_envelope(const Envelope& E, long long* checks) {
+  long long bad = 0, n = 0;
+  const int SR = E.sr;
+  for (int K = 0; K < E.max_nbt; ++K) {
+    std::vector<std::tuple<int, int, int>> ref, got;
+    for (int t = E.upd_off[K]; t < E.upd_off[K + 1]; ++t)
+      ref.emplace_back(E.upd_task[3 * t], E.upd_task[3 * t + 1], E.upd_task[3 * t + 2]);
+    for (int t = E.tc_off[K]; t < E.tc_off[K + 1]; ++t) {
+      const int pstart = E.tc_task[4 * t], nn = E.tc_task[4 * t + 1], mb = E.tc_task[4 * t + 2], nb = E.tc_task[4 * t + 3];
+      const int s = E.panel_task[2 * pstart];
+      const int a0 = 4 * mb, na = std::min(4, nn - a0), b0 = 8 * nb, nbt = std::min(8, std::min(nn, a0 + 4) - b0);
+      bad += (na <= 0 || nbt <= 0 || pstart < E.panel_off[K] || pstart + nn > E.panel_off[K + 1]);
+      for (int w = 0; w < na; ++w)
+        for (int u = 0; u < nbt && b0 + u <= a0 + w; ++u) {
+          const int I = E.panel_task[2 * (pstart + a0 + w) + 1], J = E.panel_task[2 * (pstart + b0 + u) + 1];
+          const int tr = E.sub_trow[s] + I;
+          bad += (J < E.trow_F[tr] || J > I || J <= K || E.panel_task[2 * (pstart + b0 + u)] != s);
+          got.emplace_back(s, I, J);
+        }
+    }
+    std::sort(ref.begin(), ref.end());
+    std::sort(got.begin(), got.end());
+    bad += ref != got;
+    n += (long long)ref.size();
+  }
+  for (int s = 0; s < E.nsub; ++s) {
+    const int t0 = E.sub_trow[s], nbt = E.sub_trow[s + 1] - t0, nsr = (nbt + SR - 1) / SR, q0 = E.sub_sr[s];
+    auto tile = [&](int I, int J) -> long long { return E.trow_ptr[t0 + I] + (J - E.trow_F[t0 + I]); };
+    long long f = E.fwd_ptr[s];
+    for (int q = 0; q < nsr; ++q) {
+      const int I0 = q * SR, ntr = std::min(SR, nbt - I0);
+      for (int o = 0; o < ntr; ++o) {
+        const int I = I0 + o, F = std::min(E.trow_F[t0 + I], I0);
+        bad += E.fwd_run[((size_t)(q0 + q) * SR + o) * 2] != F || E.fwd_run[((size_t)(q0 + q) * SR + o) * 2 + 1] != I0 - F;
+        for (int J = F; J < I0; ++J, ++f, ++n) bad += E.fwd_src[f] != tile(I, J);
+      }
+      for (int o = 0; o < ntr; ++o)
+        for (int j = 0; j <= o; ++j, ++f, ++n) bad += E.fwd_src[f] != -(E.dinv_ptr[q0 + q] + o * (o + 1) / 2 + j + 1);
+    }
+    bad += f != E.fwd_ptr[s + 1];
+    long long b = E.bwd_ptr[s];
+    for (int q = nsr - 1; q >= 0; --q) {
+      const int I0 = q * SR, ntr = std::min(SR, nbt - I0), I1 = I0 + ntr;
+      for (int o = 0; o < ntr; ++o) {
+        const int J = I0 + o;
+        int first = -1, last = -1;
+        for (int I = I1; I < nbt; ++I)
+          if (E.trow_F[t0 + I] <= J) { if (first < 0) first = I; last = I; }
+        const int len = first >= 0 ? last - first + 1 : 0;
+        bad += E.bwd_run[((size_t)(q0 + q) * SR + o) * 2 + 1] != len;
+        for (int I = first; len > 0 && I <= last; ++I, ++b, ++n)
+          bad += E.bwd_src[b] != (E.trow_F[t0 + I] <= J ? tile(I, J) : ZERO_TILE);
+      }
+      for (int o = 0; o < ntr; ++o)
+        for (int i = o; i < ntr; ++i, ++b, ++n) bad += E.bwd_src[b] != -(E.dinv_ptr[q0 + q] + i * (i + 1) / 2 + o + 1);
+    }
+    bad += b != E.bwd_ptr[s + 1];
+  }
+  if (checks) *checks = n;
+  return bad;
+}
+
 }  // namespace dgasm
+
+extern "C" int dgasm_selftest_plan(dgasm_system_t s, int nsub, int64_t* violations, int64_t* checks) {
+  using namespace dgasm;
+  clear_error();
+  if (!s || !violations || nsub < 1) return set_error(DGASM_EINVAL, "dgasm_selftest_plan: bad arguments");
+  Plan P;
+  DG_TRY(build_plan(*s, nsub, 0, 1, nullptr, nullptr, super_row(DGASM_FP64), P));
+  long long n = 0;
+  *violations = check_envelope(P.env, &n);
+  if (checks) *checks = n;
+  return DGASM_OK;
+}

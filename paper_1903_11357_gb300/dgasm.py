@@ -91,6 +91,7 @@ def lib():
             "dgasm_prec_footprint": [vp, i64p],
             "dgasm_prec_set_rhs_chunk": [vp, C.c_int, C.c_int],
             "dgasm_nonnested_prolongation": [vp, vp, C.c_int, C.c_int, i64p, ip, ip, dp],
+            "dgasm_selftest_plan": [vp, C.c_int, i64p, i64p],
             "dgasm_prec_get_rhs_chunk": [vp, C.c_int, ip],
             "dgasm_prec_destroy": [vp],
             "dgasm_solve": [vp, C.c_int, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats)],
@@ -367,6 +368,13 @@ def nonnested_prolongation(fine: "Mesh", coarse: "Mesh", p: int, q: int):
     blk = np.empty(n.value * nb * nq)
     check(lib().dgasm_nonnested_prolongation(fine.h, coarse.h, p, q, C.byref(n), _ip(ptr), _ip(col), _dp(blk)))
     return ptr, col, blk.reshape(-1, nb, nq)
+
+
+def selftest_plan(system: "System", nsub: int):
+    """Host plan consistency check: (violations, entries compared)."""
+    v, n = C.c_int64(), C.c_int64()
+    check(lib().dgasm_selftest_plan(system.h, int(nsub), C.byref(v), C.byref(n)))
+    return v.value, n.value
 
 
 def selftest_tc_update(tiles):

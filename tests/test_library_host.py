@@ -123,3 +123,12 @@ def test_nonnested_prolongation_matches_oracle(nf, nc, p, q):
     assert np.abs(L - O).max() <= 1e-12 * np.abs(O).max()
     with pytest.raises(dg.DgasmError):
         dg.nonnested_prolongation(F, Cm, 2, 3)   # q > p
+
+
+@pytest.mark.parametrize("n,p,nsub", [(256, 2, 4), (600, 3, 8), (400, 4, 2), (300, 1, 16), (200, 3, 1)])
+def test_plan_self_check(n, p, nsub):
+    """Tensor-core update groups cover the Cholesky update tasks, and the solve streams and run tables
+    match the tile envelope, on subdomains of 1 to 32 tile rows."""
+    S = dg.System(dg.Mesh.from_polymesh(mesh(n, 5), np.ones(n)), p, 10.0)
+    violations, checks = dg.selftest_plan(S, nsub)
+    assert violations == 0 and checks > 0
