@@ -304,7 +304,8 @@ class Prec:
         return b.value
 
     def solve(self, b, x, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None, host_buffers=False, x0_given=False):
-        """b, x: (k, ndof) or (ndof,) float64 CUDA tensors (numpy arrays if host_buffers); with x0_given
+        """b, x: (k, ndof) or (ndof,) float64 CUDA tensors (numpy arrays if host_buffers; views of pinned
+        memory, e.g. torch.zeros(n, dtype=torch.float64).pin_memory().numpy(), copy fastest); with x0_given
         x holds the initial guess on entry.  Returns (return code, [stats dict per right-hand side])."""
         o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=1 if x0_given else 0,
                       host_buffers=1 if host_buffers else 0, stream=_stream_ptr(stream))
