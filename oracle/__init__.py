@@ -9,8 +9,8 @@ with the CUDA library.  Only the tests, ``__graft_entry__.smoke()`` and the CPU-
 
 Modules: ``quadrature`` (Gauss-Legendre, Duffy triangles, polygon fans), ``basis`` (scaled Legendre
 products on element bounding boxes), ``geometry`` (areas, diameters, faces), ``sipg`` (assembly),
-``partition`` (recursive coordinate bisection, colouring), ``schwarz`` (A_i, R_0^T, A_0,
-preconditioner), ``pcg`` (ASPCG and the Lanczos estimate), ``error`` (L2 error).
+``partition`` (recursive coordinate bisection, colouring), ``schwarz`` (A_i, R_0^T for agglomerated and for
+non-nested coarse meshes, A_0, preconditioner), ``pcg`` (ASPCG and the Lanczos estimate), ``error`` (L2 error).
 
 Parity unpinned: the exact digits of the paper's tables (its meshes are not published); every
 function here is otherwise pinned by the tests in ``tests/test_oracle_*.py``.
