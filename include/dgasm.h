@@ -180,7 +180,8 @@ typedef struct {
   int precision;            /* dgasm_precision for the local factors and solves */
   void* stream;             /* cudaStream_t or NULL */
   dgasm_mesh_t coarse_mesh; /* optional: an independent polygonal mesh of the same domain whose (convex) cells
-                               D_j carry the coarse space V_0 = P_q(D_j) (non-nested coarse space, Example 4);
+                               D_j carry the coarse space V_0 = P_q(D_j) (non-nested coarse space, Example 4;
+                               a non-convex cell is rejected with DGASM_EINVAL);
                                ncoarse and agg_of_elem are then ignored.  Borrowed for the call (dgasm_setup)
                                or until the request finishes (dgasm_submit).  NULL = agglomerates. */
 } dgasm_setup_opts;

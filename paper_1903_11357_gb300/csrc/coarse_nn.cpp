@@ -181,6 +181,19 @@ void element_pairs(const MeshData& f, int e, const MeshData& c, const std::vecto
 
 int nonnested_r0t(const MeshData& f, const std::vector<int>& perm, const MeshData& c, int p, int q, R0TPairs& out) {
   const int ne = f.ne, nc = c.ne;
+  // the clipping needs convex (counter-clockwise) coarse cells: every turn left or straight
+  for (int J = 0; J < nc; ++J) {
+    const Poly cj = cell(c, J);
+    const int n = cj.n();
+    double scale = 0.0;
+    for (int k = 0; k < n; ++k) scale = std::max(scale, std::fabs(cj.xy[2 * k]) + std::fabs(cj.xy[2 * k + 1]));
+    for (int k = 0; k < n; ++k) {
+      const int a = k, b = (k + 1) % n, d = (k + 2) % n;
+      const double cr = (cj.xy[2 * b] - cj.xy[2 * a]) * (cj.xy[2 * d + 1] - cj.xy[2 * b + 1]) -
+                        (cj.xy[2 * b + 1] - cj.xy[2 * a + 1]) * (cj.xy[2 * d] - cj.xy[2 * b]);
+      if (cr < -1e-12 * scale * scale) return set_error(DGASM_EINVAL, "coarse cell %d is not convex", J);
+    }
+  }
   const Basis Bp(p), Bq(q);
   std::vector<double> gt, gw;
   gauss_legendre01(p + 2, gt, gw);

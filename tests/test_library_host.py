@@ -132,3 +132,15 @@ def test_plan_self_check(n, p, nsub):
     S = dg.System(dg.Mesh.from_polymesh(mesh(n, 5), np.ones(n)), p, 10.0)
     violations, checks = dg.selftest_plan(S, nsub)
     assert violations == 0 and checks > 0
+
+
+def test_nonnested_prolongation_rejects_a_non_convex_coarse_cell():
+    fm = mesh(60, 1)
+    F = dg.Mesh.from_polymesh(fm, np.ones(60))
+    # two cells of the unit square: an L-shaped (non-convex) cell and the square that completes it
+    xy = np.array([[0, 0], [1, 0], [1, 0.5], [0.5, 0.5], [0.5, 1], [0, 1], [1, 1]], float)
+    cm = PolyMesh(xy=xy, poly_ptr=np.array([0, 6, 10], np.int32),
+                  poly_vtx=np.array([0, 1, 2, 3, 4, 5, 3, 2, 6, 4], np.int32))
+    Cm = dg.Mesh.from_polymesh(cm, np.ones(2))
+    with pytest.raises(dg.DgasmError, match="not convex"):
+        dg.nonnested_prolongation(F, Cm, 2, 1)
