@@ -144,3 +144,13 @@ def test_nonnested_prolongation_rejects_a_non_convex_coarse_cell():
     Cm = dg.Mesh.from_polymesh(cm, np.ones(2))
     with pytest.raises(dg.DgasmError, match="not convex"):
         dg.nonnested_prolongation(F, Cm, 2, 1)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libdgasm.so every call raises instead of computing anything."""
+    monkeypatch.setattr(dg, "_lib", None)
+    monkeypatch.setattr(dg, "LIB_PATH", str(tmp_path / "libdgasm.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        dg.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        dg.Mesh.from_polymesh(mesh(32, 1), np.ones(32))
