@@ -35,6 +35,21 @@ struct Basis {
       }
     }
   }
+  // the scaling c_a of every function on a box (a function of the box alone)
+  void coefs(const double* box, double* c) const {
+    double wx = box[1] - box[0], wy = box[3] - box[2];
+    for (int a = 0; a < nb; ++a) c[a] = std::sqrt((2.0 * ii[a] + 1.0) * (2.0 * jj[a] + 1.0) / (wx * wy));
+  }
+  // values v[nb] at (x, y) with the scaling c from coefs(box): the same numbers as eval
+  void values(const double* box, const double* c, double x, double y, double* v) const {
+    double wx = box[1] - box[0], wy = box[3] - box[2];
+    double xi = 2.0 * (x - 0.5 * (box[0] + box[1])) / wx;
+    double eta = 2.0 * (y - 0.5 * (box[2] + box[3])) / wy;
+    double Lx[16], dLx[16], Ly[16], dLy[16];
+    legendre(xi, Lx, dLx);
+    legendre(eta, Ly, dLy);
+    for (int a = 0; a < nb; ++a) v[a] = c[a] * Lx[ii[a]] * Ly[jj[a]];
+  }
   void legendre(double t, double* L, double* dL) const {
     L[0] = 1.0; dL[0] = 0.0;
     if (p >= 1) { L[1] = t; dL[1] = 1.0; }

@@ -125,14 +125,20 @@ void element_pairs(const MeshData& f, int e, const MeshData& c, const std::vecto
   cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
   const Poly pe = cell(f, e);
   const double ae = area(pe);
-  std::vector<double> pts, wts, v(np), u(nq);
+  std::vector<double> pts, wts, v(np), u(nq), cf(np), cc(nq), wv(np);
+  Bp.coefs(fb, cf.data());
   // M_kappa and its Cholesky factor
   poly_rule(pe, gt, gw, pts, wts);
   std::vector<double> M((size_t)np * np, 0.0);
   for (size_t k = 0; k < wts.size(); ++k) {
-    Bp.eval(fb, pts[2 * k], pts[2 * k + 1], v.data(), nullptr);
-    for (int a = 0; a < np; ++a)
-      for (int b = 0; b <= a; ++b) M[(size_t)a * np + b] += wts[k] * v[a] * v[b];
+    Bp.values(fb, cf.data(), pts[2 * k], pts[2 * k + 1], v.data());
+    double* __restrict Mp = M.data();
+    const double* __restrict vp = v.data();
+    const double wk = wts[k];
+    for (int a = 0; a < np; ++a) {
+      const double wa = wk * vp[a];
+      for (int b = 0; b <= a; ++b) Mp[(size_t)a * np + b] += wa * vp[b];
+    }
   }
   for (int j = 0; j < np; ++j) {   // in-place lower Cholesky
     double d = M[(size_t)j * np + j];
@@ -153,11 +159,17 @@ void element_pairs(const MeshData& f, int e, const MeshData& c, const std::vecto
     if (piece.n() < 3 || area(piece) <= MIN_REL_AREA * ae) continue;
     poly_rule(piece, gt, gw, pts, wts);
     std::fill(N.begin(), N.end(), 0.0);
+    Bq.coefs(cb, cc.data());
     for (size_t k = 0; k < wts.size(); ++k) {
-      Bp.eval(fb, pts[2 * k], pts[2 * k + 1], v.data(), nullptr);
-      Bq.eval(cb, pts[2 * k], pts[2 * k + 1], u.data(), nullptr);
-      for (int a = 0; a < np; ++a)
-        for (int b = 0; b < nq; ++b) N[(size_t)a * nq + b] += wts[k] * v[a] * u[b];
+      Bp.values(fb, cf.data(), pts[2 * k], pts[2 * k + 1], v.data());
+      Bq.values(cb, cc.data(), pts[2 * k], pts[2 * k + 1], u.data());
+      double* __restrict Np = N.data();
+      const double* __restrict up = u.data();
+      const double wk = wts[k];
+      for (int a = 0; a < np; ++a) {
+        const double wa = wk * v[a];
+        for (int b = 0; b < nq; ++b) Np[(size_t)a * nq + b] += wa * up[b];
+      }
     }
     // M^{-1} N by the two triangular solves, column by column
     for (int b = 0; b < nq; ++b) {
