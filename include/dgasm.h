@@ -305,7 +305,8 @@ int dgasm_profile_read(int kind, double* total_ms, int64_t* launches, int reset)
  * Krylov state for nrhs) fits in hbm_budget next to the admitted ones and one of max_slots slots is
  * free.  Admitted requests are set up, then advance together, one PCG iteration each per batched
  * round; finished requests retire between rounds and queued ones join.  b and x are device pointers
- * (ndof x nrhs, column-major) borrowed until completion. */
+ * (ndof x nrhs, column-major) borrowed until completion; so is the system handle sys, which must not be
+ * destroyed while one of its requests is queued or running. */
 int dgasm_server_create(size_t hbm_budget, int max_slots, void* stream, dgasm_server_t* out);
 int dgasm_submit(dgasm_server_t sv, dgasm_system_t sys, const dgasm_setup_opts* so, int nrhs,
                  const double* b, double* x, const dgasm_solve_opts* o, uint64_t* ticket);

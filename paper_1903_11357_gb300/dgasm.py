@@ -433,7 +433,7 @@ class Server:
         o = SetupOpts()
         o.nsub, o.ncoarse, o.p_c = nsub, ncoarse, p_c
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        keep = [b, x]
+        keep = [b, x, system]   # the server reads the system until the request finishes
         if coarse_mesh is not None:
             keep.append(coarse_mesh)
             o.coarse_mesh = coarse_mesh.h

@@ -113,3 +113,21 @@ def test_restarts_from_the_true_residual_in_the_mix():
         assert rc == 0 and all(s["converged"] and s["true_relres"] <= 1e-12 for s in st)
         assert torch.equal(x, ref)
     sv.close()
+
+
+def test_server_keeps_the_system_of_a_pending_request():
+    """The server reads a request's system until it finishes: the binding holds the reference, so a
+    system the caller no longer names is not destroyed under a queued request."""
+    import gc
+    ref_S = make_system(300, 9, 2)
+    b = rhs(ref_S, 1, 40)
+    ref = alone(ref_S, 4, 16, b, "fp64")
+    sv = dg.Server(hbm_budget=8 << 30, max_slots=1)
+    xs = [torch.zeros_like(b) for _ in range(3)]
+    ts = [sv.submit(make_system(300, 9, 2), 4, 16, 1, b, x) for x in xs]   # temporaries only
+    gc.collect()
+    for t, x in zip(ts, xs):
+        rc, st = sv.wait(t, 60000)
+        assert rc == 0 and st[0]["converged"]
+        assert torch.equal(x, ref)
+    sv.close()
