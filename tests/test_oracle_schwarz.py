@@ -110,6 +110,36 @@ def test_one_subdomain_no_coarse_one_iteration():
     assert res.iters == 1 and res.converged
 
 
+def test_one_subdomain_with_coarse_space_spectrum():
+    """One subdomain covering the mesh: A_1 = A, so B A = P_0 + I (Sec. 3) with P_0 the A-orthogonal projection
+    onto V_0.  Its spectrum is exactly 2 on V_0 (n0 times) and 1 elsewhere, and PCG ends after two iterations
+    (two distinct eigenvalues); a coarse term with any other weight moves the upper eigenvalue."""
+    _, _, A, _, _, S = setup_problem(n=40, p=2, nsub=1, ncoarse=8, q=1)
+    Ad = A.toarray()
+    n, n0 = Ad.shape[0], S.A0.shape[0]
+    ev = np.sort(np.linalg.eigvals(S.dense(n) @ Ad).real)
+    assert np.abs(ev[:n - n0] - 1.0).max() < 1e-9
+    assert np.abs(ev[n - n0:] - 2.0).max() < 1e-9
+    b = np.random.default_rng(3).standard_normal(n)
+    res = pcg.pcg(A, b, S.apply, rtol=1e-8)
+    assert res.converged and res.iters == 2
+
+
+def test_stop_test_on_the_unpreconditioned_residual():
+    """Sec. 7 stops when the Euclidean norm of the residual b - A x, relative to ||b||, drops below the tolerance:
+    the recorded residual history is that of b - A x_k (the recursive residual agrees with the true one far above
+    rounding here), the last entry is the first below rtol, and the iterate before it is still above."""
+    _, _, A, _, _, S = setup_problem(n=48, p=2, nsub=4, ncoarse=8)
+    b = np.random.default_rng(4).standard_normal(A.shape[0])
+    rtol = 1e-6
+    res = pcg.pcg(A, b, S.apply, rtol=rtol)
+    true_rel = lambda x: np.linalg.norm(b - A @ x) / np.linalg.norm(b)  # noqa: E731
+    assert res.converged and res.resid[-1] <= rtol < res.resid[-2]
+    assert true_rel(res.x) == pytest.approx(res.resid[-1], rel=1e-6)
+    prev = pcg.pcg(A, b, S.apply, fixed_iters=res.iters - 1)
+    assert true_rel(prev.x) == pytest.approx(res.resid[-2], rel=1e-6)
+
+
 def test_pcg_matches_direct_solve():
     _, _, A, _, _, S = setup_problem(n=32, p=2, nsub=4, ncoarse=8)
     b = np.random.default_rng(2).standard_normal(A.shape[0])

@@ -1,7 +1,8 @@
 """Pins for the oracle's SIPG assembly (Sec. 2, Eq. Ah, Eq. lifting, Eq. Sigma).
 
-* hand-derived entries on a two-square mesh (closed forms below) pin the penalty with harmonic
-  averages of rho and h, the consistency factor <rho>/2 and the boundary terms;
+* hand-derived entries on a two-square mesh (closed forms below) pin the penalty with the harmonic
+  average of rho, the consistency factor <rho>/2 and the boundary terms; a square next to a 2 x 1
+  rectangle pins the harmonic average of h (Sec. 2 defines <.> for both);
 * symmetry and positive definiteness (Lemma 5.1: coercive for C_sigma large enough);
 * consistency: u = x(1-x)y(1-y) lies in P_4 and vanishes on the boundary, so for p >= 4 the SIPG
   solution reproduces it to rounding;
@@ -57,6 +58,24 @@ def test_two_square_entries_closed_form():
     for (i, j), v in expect.items():
         assert A[i, j] == pytest.approx(v, rel=1e-13, abs=1e-13), (i, j)
         assert A[j, i] == pytest.approx(v, rel=1e-13, abs=1e-13), (j, i)
+
+
+def test_unequal_cells_penalty_uses_harmonic_h():
+    """kappa_1 = [0,1]^2, kappa_2 = [1,3]x[0,1], rho = 1, p = 1, C_sigma = 10.  h_1 = sqrt2, h_2 = sqrt5, so
+    <h> = 2 sqrt2 sqrt5 / (sqrt2 + sqrt5) and sigma_I = 10 / <h>; sigma_B2 = 10 / sqrt5.  phi_0 = 1 on kappa_1
+    and 1/sqrt2 on kappa_2 (box 2 x 1), with zero gradient, so only penalty terms reach these entries:
+      A[1.phi0, 2.phi0] = sigma_I (+1)(-1) int_0^1 1 * (1/sqrt2) dy           = -sigma_I / sqrt2
+      A[2.phi0, 2.phi0] = sigma_I / 2 (face x = 1) + sigma_B2 / 2 * (1 + 2 + 2) = sigma_I / 2 + 5 sqrt5
+    (the arithmetic mean or the larger of h_1, h_2 in place of <h> changes both)."""
+    xy = np.array([[0, 0], [1, 0], [3, 0], [3, 1], [1, 1], [0, 1]], float)
+    mesh = PolyMesh(xy=xy, poly_ptr=np.array([0, 4, 8], np.int32),
+                    poly_vtx=np.array([0, 1, 4, 5, 1, 2, 3, 4], np.int32))
+    A = sipg.assemble(mesh, np.ones(2), 1, 10.0)[0].toarray()
+    r2, r5 = math.sqrt(2.0), math.sqrt(5.0)
+    sI = 10.0 * (r2 + r5) / (2.0 * r2 * r5)
+    assert A[0, 3] == pytest.approx(-sI / r2, rel=1e-13)
+    assert A[3, 0] == pytest.approx(-sI / r2, rel=1e-13)
+    assert A[3, 3] == pytest.approx(sI / 2.0 + 5.0 * r5, rel=1e-13)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3])
