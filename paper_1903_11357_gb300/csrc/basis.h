@@ -40,15 +40,35 @@ struct Basis {
     double wx = box[1] - box[0], wy = box[3] - box[2];
     for (int a = 0; a < nb; ++a) c[a] = std::sqrt((2.0 * ii[a] + 1.0) * (2.0 * jj[a] + 1.0) / (wx * wy));
   }
-  // values v[nb] at (x, y) with the scaling c from coefs(box): the same numbers as eval
-  void values(const double* box, const double* c, double x, double y, double* v) const {
-    double wx = box[1] - box[0], wy = box[3] - box[2];
-    double xi = 2.0 * (x - 0.5 * (box[0] + box[1])) / wx;
-    double eta = 2.0 * (y - 0.5 * (box[2] + box[3])) / wy;
-    double Lx[16], dLx[16], Ly[16], dLy[16];
-    legendre(xi, Lx, dLx);
-    legendre(eta, Ly, dLy);
-    for (int a = 0; a < nb; ++a) v[a] = c[a] * Lx[ii[a]] * Ly[jj[a]];
+  // values at n points (x_k, y_k interleaved in xy) with the scaling c from coefs(box), V[k * nb + a]: the
+  // same numbers as eval, computed degree by degree over all points.  L holds 2 (p + 1) n doubles.
+  void values_at(const double* box, const double* c, const double* xy, int n, double* V, double* L) const {
+    const double wx = box[1] - box[0], wy = box[3] - box[2];
+    const double mx = 0.5 * (box[0] + box[1]), my = 0.5 * (box[2] + box[3]);
+    double* __restrict Lx = L;
+    double* __restrict Ly = L + (size_t)(p + 1) * n;
+    for (int k = 0; k < n; ++k) {
+      Lx[k] = 1.0;
+      Ly[k] = 1.0;
+    }
+    if (p >= 1)
+      for (int k = 0; k < n; ++k) {
+        Lx[n + k] = 2.0 * (xy[2 * k] - mx) / wx;
+        Ly[n + k] = 2.0 * (xy[2 * k + 1] - my) / wy;
+      }
+    for (int d = 1; d < p; ++d) {
+      const double* __restrict tx = Lx + n;
+      const double* __restrict ty = Ly + n;
+      for (int k = 0; k < n; ++k) {
+        Lx[(size_t)(d + 1) * n + k] = ((2.0 * d + 1.0) * tx[k] * Lx[(size_t)d * n + k] - d * Lx[(size_t)(d - 1) * n + k]) / (d + 1.0);
+        Ly[(size_t)(d + 1) * n + k] = ((2.0 * d + 1.0) * ty[k] * Ly[(size_t)d * n + k] - d * Ly[(size_t)(d - 1) * n + k]) / (d + 1.0);
+      }
+    }
+    for (int a = 0; a < nb; ++a) {
+      const double* __restrict lx = Lx + (size_t)ii[a] * n;
+      const double* __restrict ly = Ly + (size_t)jj[a] * n;
+      for (int k = 0; k < n; ++k) V[(size_t)k * nb + a] = c[a] * lx[k] * ly[k];
+    }
   }
   void legendre(double t, double* L, double* dL) const {
     L[0] = 1.0; dL[0] = 0.0;

@@ -4,9 +4,9 @@
 //     R_0^T|_kappa = M_kappa^{-1} [N_kappa,j]_j,   N_kappa,j = int_{kappa cap D_j} phi psi_j^T,
 // over every coarse element D_j that overlaps kappa.  The cells are convex (clipped Voronoi cells), so each
 // piece kappa cap D_j is a convex polygon: Sutherland-Hodgman clipping of kappa against the half-planes of
-// D_j's edges.  Pieces are integrated with the element rule (fan from the vertex average, Duffy-collapsed
-// (p+2)-point Gauss rule per triangle: exact for the degree p + q <= 2p integrands); pieces smaller than
-// 1e-12 |kappa| are dropped.  Candidates come from a uniform grid over the coarse cells' bounding boxes.
+// D_j's edges.  Integrals use a fan of triangles from the vertex average with a Duffy-collapsed m-point
+// Gauss rule per triangle, exact for total degree 2m - 2: m = p + 1 for M_kappa (degree 2p) and
+// m = ceil((p + q + 2) / 2) on the pieces (degree p + q); pieces smaller than 1e-12 |kappa| are dropped.  Candidates come from a uniform grid over the coarse cells' bounding boxes.
 // Host C++ like the SIPG assembly; elements are split over threads and each element's pairs are computed
 // by one thread in ascending coarse order, so the result does not depend on the thread count.
 #include <algorithm>
@@ -105,10 +105,50 @@ void poly_rule(const Poly& p, const std::vector<double>& t, const std::vector<do
   }
 }
 
+// C[a][b] = sum_k (w_k A[k][a]) B[k][b] for a < na and b < nb (A is [n][na], B is [n][nb], C is [na][nb]), each
+// entry summed over k in ascending order.  lower: only b <= a is needed (entries above it may be written too).
+// Columns go in blocks of 8 whose partial sums stay in registers; WA (na * n doubles) holds w_k A[k][a].
+void weighted_products(int n, const double* w, const double* A, int na, const double* B, int nb, double* C, bool lower,
+                       double* WA) {
+  for (int k = 0; k < n; ++k)
+    for (int a = 0; a < na; ++a) WA[(size_t)a * n + k] = w[k] * A[(size_t)k * na + a];
+  for (int a = 0; a < na; ++a) {
+    const double* wa = WA + (size_t)a * n;
+    const int ncol = lower ? std::min(nb, a + 1) : nb;
+    for (int b0 = 0; b0 < ncol; b0 += 8) {
+      double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      const int r = std::min(8, nb - b0);
+      if (r == 8) {
+        for (int k = 0; k < n; ++k) {
+          const double* bk = B + (size_t)k * nb + b0;
+          for (int j = 0; j < 8; ++j) s[j] += wa[k] * bk[j];
+        }
+      } else {
+        for (int k = 0; k < n; ++k) {
+          const double* bk = B + (size_t)k * nb + b0;
+          for (int j = 0; j < r; ++j) s[j] += wa[k] * bk[j];
+        }
+      }
+      for (int j = 0; j < r; ++j) C[(size_t)a * nb + b0 + j] = s[j];
+    }
+  }
+}
+
+// per-thread work arrays, reused from element to element
+struct Scratch {
+  std::vector<double> pts, wts, V, U, L, M, N, WA;
+  std::vector<int> cand;
+};
+
+// the integration rules: m points per direction for M_kappa (degree 2p) and for the pieces (degree p + q)
+struct Rules {
+  std::vector<double> tM, wM, tN, wN;
+};
+
 // the pairs of one fine element: coarse cells (ascending) and blocks [np][nq]
 void element_pairs(const MeshData& f, int e, const MeshData& c, const std::vector<std::vector<int>>& bins, int G,
-                   const double* gb, const Basis& Bp, const Basis& Bq, const std::vector<double>& gt,
-                   const std::vector<double>& gw, std::vector<int>& cj, std::vector<double>& blk) {
+                   const double* gb, const Basis& Bp, const Basis& Bq, const Rules& R, Scratch& W,
+                   std::vector<int>& cj, std::vector<double>& blk) {
   const int np = Bp.nb, nq = Bq.nb;
   const double* fb = &f.bbox[4 * (size_t)e];
   // candidates: coarse cells registered in the bins under this element's box, boxes overlapping
@@ -118,29 +158,30 @@ void element_pairs(const MeshData& f, int e, const MeshData& c, const std::vecto
   };
   const int i0 = bin(fb[0], gb[0], gb[1]), i1 = bin(fb[1], gb[0], gb[1]);
   const int j0 = bin(fb[2], gb[2], gb[3]), j1 = bin(fb[3], gb[2], gb[3]);
-  std::vector<int> cand;
+  std::vector<int>& cand = W.cand;
+  cand.clear();
   for (int j = j0; j <= j1; ++j)
     for (int i = i0; i <= i1; ++i) cand.insert(cand.end(), bins[(size_t)j * G + i].begin(), bins[(size_t)j * G + i].end());
   std::sort(cand.begin(), cand.end());
   cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
   const Poly pe = cell(f, e);
   const double ae = area(pe);
-  std::vector<double> pts, wts, v(np), u(nq), cf(np), cc(nq), wv(np);
-  Bp.coefs(fb, cf.data());
+  double cf[64], cc[64];
+  Bp.coefs(fb, cf);
+  auto values = [&](const Basis& B, const double* box, const double* coef, std::vector<double>& out) {
+    const int n = (int)W.wts.size();
+    out.resize((size_t)n * B.nb);
+    W.L.resize((size_t)2 * (B.p + 1) * n);
+    B.values_at(box, coef, W.pts.data(), n, out.data(), W.L.data());
+  };
   // M_kappa and its Cholesky factor
-  poly_rule(pe, gt, gw, pts, wts);
-  std::vector<double> M((size_t)np * np, 0.0);
-  for (size_t k = 0; k < wts.size(); ++k) {
-    Bp.values(fb, cf.data(), pts[2 * k], pts[2 * k + 1], v.data());
-    double* __restrict Mp = M.data();
-    const double* __restrict vp = v.data();
-    const double wk = wts[k];
-    for (int a = 0; a < np; ++a) {
-      const double wa = wk * vp[a];
-      for (int b = 0; b <= a; ++b) Mp[(size_t)a * np + b] += wa * vp[b];
-    }
-  }
-  for (int j = 0; j < np; ++j) {   // in-place lower Cholesky
+  poly_rule(pe, R.tM, R.wM, W.pts, W.wts);
+  values(Bp, fb, cf, W.V);
+  std::vector<double>& M = W.M;
+  M.resize((size_t)np * np);
+  W.WA.resize((size_t)np * W.wts.size());
+  weighted_products((int)W.wts.size(), W.wts.data(), W.V.data(), np, W.V.data(), np, M.data(), true, W.WA.data());
+  for (int j = 0; j < np; ++j) {   // in-place lower Cholesky of the lower triangle
     double d = M[(size_t)j * np + j];
     for (int k = 0; k < j; ++k) d -= M[(size_t)j * np + k] * M[(size_t)j * np + k];
     d = std::sqrt(d);
@@ -151,26 +192,19 @@ void element_pairs(const MeshData& f, int e, const MeshData& c, const std::vecto
       M[(size_t)i * np + j] = s / d;
     }
   }
-  std::vector<double> N((size_t)np * nq);
+  std::vector<double>& N = W.N;
+  N.resize((size_t)np * nq);
   for (int J : cand) {
     const double* cb = &c.bbox[4 * (size_t)J];
     if (!(cb[0] < fb[1] && cb[1] > fb[0] && cb[2] < fb[3] && cb[3] > fb[2])) continue;
     const Poly piece = clip(pe, cell(c, J));
     if (piece.n() < 3 || area(piece) <= MIN_REL_AREA * ae) continue;
-    poly_rule(piece, gt, gw, pts, wts);
-    std::fill(N.begin(), N.end(), 0.0);
-    Bq.coefs(cb, cc.data());
-    for (size_t k = 0; k < wts.size(); ++k) {
-      Bp.values(fb, cf.data(), pts[2 * k], pts[2 * k + 1], v.data());
-      Bq.values(cb, cc.data(), pts[2 * k], pts[2 * k + 1], u.data());
-      double* __restrict Np = N.data();
-      const double* __restrict up = u.data();
-      const double wk = wts[k];
-      for (int a = 0; a < np; ++a) {
-        const double wa = wk * v[a];
-        for (int b = 0; b < nq; ++b) Np[(size_t)a * nq + b] += wa * up[b];
-      }
-    }
+    poly_rule(piece, R.tN, R.wN, W.pts, W.wts);
+    Bq.coefs(cb, cc);
+    values(Bp, fb, cf, W.V);
+    values(Bq, cb, cc, W.U);
+    W.WA.resize((size_t)np * W.wts.size());
+    weighted_products((int)W.wts.size(), W.wts.data(), W.V.data(), np, W.U.data(), nq, N.data(), false, W.WA.data());
     // M^{-1} N by the two triangular solves, column by column
     for (int b = 0; b < nq; ++b) {
       for (int a = 0; a < np; ++a) {
@@ -207,8 +241,10 @@ int nonnested_r0t(const MeshData& f, const std::vector<int>& perm, const MeshDat
     }
   }
   const Basis Bp(p), Bq(q);
-  std::vector<double> gt, gw;
-  gauss_legendre01(p + 2, gt, gw);
+  // an m-point collapsed rule integrates total degree 2m - 2 exactly
+  Rules R;
+  gauss_legendre01(p + 1, R.tM, R.wM);
+  gauss_legendre01((p + q + 3) / 2, R.tN, R.wN);
   // uniform grid over both meshes' boxes, each coarse cell in every bin its box touches
   double gb[4] = {1e300, -1e300, 1e300, -1e300};
   for (const MeshData* m : {&f, &c})
@@ -236,7 +272,8 @@ int nonnested_r0t(const MeshData& f, const std::vector<int>& perm, const MeshDat
   std::vector<std::thread> th;
   for (unsigned t = 0; t < nt; ++t)
     th.emplace_back([&, t]() {
-      for (int i = (int)t; i < ne; i += (int)nt) element_pairs(f, perm[i], c, bins, G, gb, Bp, Bq, gt, gw, cj[i], blk[i]);
+      Scratch W;
+      for (int i = (int)t; i < ne; i += (int)nt) element_pairs(f, perm[i], c, bins, G, gb, Bp, Bq, R, W, cj[i], blk[i]);
     });
   for (auto& x : th) x.join();
   out.ptr.assign(ne + 1, 0);
