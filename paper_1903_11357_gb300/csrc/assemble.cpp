@@ -182,10 +182,10 @@ void assemble_rhs(const MeshData& m, const Basis& B, dgasm_rhs_fn f, void* user,
   }
 }
 
-int check_args(dgasm_mesh_t mh, int p, double c_sigma, dgasm_system_t* out) {
-  if (!out) return set_error(DGASM_EINVAL, "dgasm_assemble: out is NULL");
+int check_args(const char* fn, dgasm_mesh_t mh, int p, double c_sigma, dgasm_system_t* out) {
+  if (!out) return set_error(DGASM_EINVAL, "%s: out is NULL", fn);
   *out = nullptr;
-  if (!mh) return set_error(DGASM_EINVAL, "dgasm_assemble: NULL mesh");
+  if (!mh) return set_error(DGASM_EINVAL, "%s: NULL mesh", fn);
   if (p < 1 || p > 8) return set_error(DGASM_EINVAL, "p=%d must lie in [1, 8]", p);
   if (!(c_sigma > 0.0)) return set_error(DGASM_EINVAL, "c_sigma must be positive");
   return DGASM_OK;
@@ -196,7 +196,7 @@ int check_args(dgasm_mesh_t mh, int p, double c_sigma, dgasm_system_t* out) {
 extern "C" int dgasm_assemble(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_fn f, void* user,
                               dgasm_system_t* out) {
   clear_error();
-  DG_TRY(check_args(mh, p, c_sigma, out));
+  DG_TRY(check_args("dgasm_assemble", mh, p, c_sigma, out));
   const MeshData& m = mh->m;
   dgasm_system_s* s = new_system(mh, p, c_sigma);
   if (!s) return set_error(DGASM_ENOMEM, "host allocation failed");
@@ -221,7 +221,7 @@ extern "C" int dgasm_assemble(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_
 extern "C" int dgasm_assemble_device(dgasm_mesh_t mh, int p, double c_sigma, dgasm_rhs_fn f, void* user, void* stream,
                                      dgasm_system_t* out) {
   clear_error();
-  DG_TRY(check_args(mh, p, c_sigma, out));
+  DG_TRY(check_args("dgasm_assemble_device", mh, p, c_sigma, out));
   const MeshData& m = mh->m;
   std::unique_ptr<dgasm_system_s> s(new_system(mh, p, c_sigma));
   if (!s) return set_error(DGASM_ENOMEM, "host allocation failed");

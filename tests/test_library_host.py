@@ -1,5 +1,6 @@
-"""Host-side checks of libdgasm.so (no GPU): it loads, exports every entry point of include/dgasm.h,
-validates meshes, and its partition and SIPG assembly agree with the oracle."""
+"""Host-side checks of libdgasm.so (no GPU): it loads, exports every entry point of include/dgasm.h, answers
+NULL arguments with DGASM_EINVAL, validates meshes, and its partition, SIPG assembly and non-nested R_0^T agree
+with the oracle."""
 import ctypes
 
 import numpy as np
@@ -18,6 +19,55 @@ def test_library_loads_and_exports_header_symbols():
     assert "dgasm_solve" in names and "dgasm_setup" in names and "dgasm_submit" in names
     for n in names:
         assert hasattr(L, n), n
+
+
+# every entry point with NULL handles and buffers: an argument check answers before any CUDA call
+NULL_CALLS = {
+    "dgasm_setup": (None, None, None),
+    "dgasm_prec_apply": (None, 1, None, None, None),
+    "dgasm_prec_set_rhs_chunk": (None, 1, 1),
+    "dgasm_prec_get_rhs_chunk": (None, 1, None),
+    "dgasm_prec_partition": (None, None, None),
+    "dgasm_prec_footprint": (None, None),
+    "dgasm_prec_info": (None, None),
+    "dgasm_solve": (None, 1, None, None, None, None),
+    "dgasm_solve_batch": (0, None, None, None, None, None, None),
+    "dgasm_system_spmv": (None, None, None, None),
+    "dgasm_system_spmv_dot_noalloc": (None, None, None, None, None),
+    "dgasm_system_dofs": (None, None, None),
+    "dgasm_system_rhs": (None, None),
+    "dgasm_system_blocks": (None, None, None, None, None),
+    "dgasm_mesh_info": (None, None, None, None),
+    "dgasm_mesh_centroids": (None, None),
+    "dgasm_partition": (None, 4, 0, None, None),
+    "dgasm_submit": (None, None, None, 1, None, None, None, None),
+    "dgasm_poll": (None, 0, None),
+    "dgasm_wait": (None, 0, 0, None),
+    "dgasm_cancel": (None, 0),
+    "dgasm_server_stats": (None, None, None, None, None),
+    "dgasm_nonnested_prolongation": (None, None, 1, 1, None, None, None, None),
+    "dgasm_selftest_plan": (None, 4, None, None),
+    "dgasm_selftest_tc_update": (0, None, None),
+    "dgasm_lanczos": (0, None, None, None, None),
+}
+
+
+def test_every_entry_rejects_null_arguments():
+    """Each entry point answers NULL handles or buffers with DGASM_EINVAL and a message naming the problem, and
+    each destroy accepts NULL; none of these calls reaches the GPU."""
+    L = dg.lib()
+    buf = ctypes.create_string_buffer(512)
+    calls = dict(NULL_CALLS)
+    calls["dgasm_assemble"] = (None, 3, 10.0, dg.RHS_FN(), None, None)
+    calls["dgasm_assemble_device"] = (None, 3, 10.0, dg.RHS_FN(), None, None, None)
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == dg.EINVAL, name
+        L.dgasm_last_error(buf, 512)
+        assert buf.value, name
+    L.dgasm_last_error(buf, 512)
+    assert buf.value.startswith(b"dgasm_assemble_device")
+    for name in ("dgasm_prec_destroy", "dgasm_system_destroy", "dgasm_mesh_destroy", "dgasm_server_destroy"):
+        assert getattr(L, name)(None) == dg.OK, name
 
 
 def test_mesh_validation_errors():
