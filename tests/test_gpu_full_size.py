@@ -1,0 +1,107 @@
+"""The headline workload at full size, in the configuration bench.py times, against the oracle: 16384
+Lloyd-relaxed Voronoi cells (seed 2), p = 3 (163840 dofs), C_sigma = 10, 64 RCB subdomains, 256 RCB
+agglomerates at q = 1, rho = 1e4 on the odd cells of a 4 x 4 checkerboard of subdomains, FP64, launches on a
+non-default stream.  The oracle assembles the system and builds its Schwarz operator at this size (about 1.5
+minutes of host time), so every output of one SpMV and one application of B is compared entry by entry; the
+solve (293 iterations here, too many for the oracle in a test) is checked through the true residual, recomputed
+on the host with the oracle's matrix.
+
+Tolerances:
+* partition and agglomerates: identical (index work);
+* SpMV: max |y - A x| <= 1e-12 max |A x| (the same products summed in another order);
+* B r: two backward-stable Cholesky solves of the same matrix differ by about kappa * 2^-53 relative, so the
+  bound is 10 * kappa_max * 2^-53 with kappa_max measured here: the coarse matrix A_0 (unscaled and
+  Jacobi-scaled; the larger one, about 3e6, dominates) and every eighth Jacobi-scaled subdomain matrix (about
+  2e4 to 6e4: rho is constant on each subdomain, so their conditioning is alike);
+* solve: converged, the library's own true relative residual <= 1e-8, and ||b - A x|| / ||b|| with the oracle's
+  A <= 1e-8 + 10 * 2^-53 * || |A| |x| || / ||b|| (the rounding floor of any residual evaluated in FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import partition, schwarz, sipg
+from oracle.geometry import build_geometry
+from synth.coeff import checker_per_subdomain
+from synth.voronoi import voronoi_mesh
+from tests.helpers import f_sin, have_gpu
+
+pytestmark = pytest.mark.gpu
+
+if have_gpu():
+    import torch
+    from paper_1903_11357_gb300 import dgasm as dg
+
+N_ELEM, SEED, P_DEG, NSUB, NCOARSE, Q, CONTRAST = 16384, 2, 3, 64, 256, 1, 1e4
+EPS = 2.0 ** -53
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def case():
+    m = voronoi_mesh(N_ELEM, SEED)
+    g = build_geometry(m)
+    sub = partition.subdomains(g.centroid, NSUB)
+    agg = partition.agglomerates(g.centroid, sub, NSUB, NCOARSE)
+    rho = checker_per_subdomain(m, sub, CONTRAST)
+    A, _, _ = sipg.assemble(m, rho, P_DEG, 10.0, geom=g)
+    A = A.tocsr()
+    O = schwarz.build(A, m, g, P_DEG, sub, agg, Q)
+    stream = torch.cuda.Stream()
+    S = dg.System(dg.Mesh.from_polymesh(m, rho), P_DEG, 10.0, f=f_sin)
+    P = dg.Prec(S, NSUB, NCOARSE, Q, precision="fp64", stream=stream)
+    return dict(A=A, O=O, S=S, P=P, sub=sub, agg=agg, stream=stream)
+
+
+def test_full_size_partition_is_the_oracles(case):
+    sub, agg = case["P"].partition()
+    assert np.array_equal(sub, case["sub"])
+    assert np.array_equal(agg, case["agg"])
+
+
+def test_full_size_spmv_matches_oracle(case):
+    A = case["A"]
+    x = np.random.default_rng(11).standard_normal(A.shape[0])
+    xd = dev(x)
+    y = torch.zeros_like(xd)
+    torch.cuda.synchronize()
+    case["S"].spmv(xd, y, stream=case["stream"])
+    torch.cuda.synchronize()
+    ref = A @ x
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_full_size_apply_matches_oracle(case):
+    A, O = case["A"], case["O"]
+    kmax = 0.0
+    mats = [A[idx][:, idx].toarray() for idx in O.local_dofs[::8]] + [O.A0]
+    for M in mats:
+        d = 1.0 / np.sqrt(np.diag(M))
+        ev = np.linalg.eigvalsh(M * d[:, None] * d[None, :])
+        kmax = max(kmax, ev[-1] / ev[0])
+    ev = np.linalg.eigvalsh(O.A0)
+    kmax = max(kmax, ev[-1] / ev[0])
+    r = np.random.default_rng(12).standard_normal(A.shape[0])
+    rd = dev(r)
+    z = torch.zeros_like(rd)
+    torch.cuda.synchronize()
+    case["P"].apply(rd, z, stream=case["stream"])
+    torch.cuda.synchronize()
+    ref = O.apply(r)
+    assert np.linalg.norm(z.cpu().numpy() - ref) <= 10.0 * kmax * EPS * np.linalg.norm(ref)
+
+
+def test_full_size_solve_reaches_the_tolerance(case):
+    A = case["A"]
+    b = case["S"].rhs()
+    bd = dev(b)
+    x = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    rc, st = case["P"].solve(bd, x, rtol=1e-8, stream=case["stream"])
+    torch.cuda.synchronize()
+    assert rc == 0 and st[0]["converged"] and st[0]["true_relres"] <= 1e-8
+    xh = x.cpu().numpy()
+    floor = 10.0 * EPS * np.linalg.norm(abs(A) @ np.abs(xh)) / np.linalg.norm(b)
+    assert np.linalg.norm(b - A @ xh) / np.linalg.norm(b) <= 1e-8 + floor
