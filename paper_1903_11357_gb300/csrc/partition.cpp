@@ -2,6 +2,7 @@
 // recursive coordinate bisection of element area centroids.
 #include <algorithm>
 #include <numeric>
+#include <utility>
 
 #include "common.h"
 #include "plan.h"
@@ -9,7 +10,7 @@
 namespace dgasm {
 
 static void rcb_rec(const double* cx, const double* cy, std::vector<int>& elems, size_t lo, size_t hi, int k,
-                    std::vector<int>& part_of, int& next_part) {
+                    std::vector<int>& part_of, int& next_part, std::vector<std::pair<double, int>>& keys) {
   if (k <= 1) {
     for (size_t i = lo; i < hi; ++i) part_of[elems[i]] = next_part;
     ++next_part;
@@ -26,19 +27,21 @@ static void rcb_rec(const double* cx, const double* cy, std::vector<int>& elems,
   size_t n = hi - lo;
   size_t nl = (n * (size_t)kl) / (size_t)k;
   // the first nl elements in the (coordinate, element id) order: a strict total order, so selecting them
-  // with nth_element gives exactly the set a full sort would
-  if (nl > 0 && nl < n)
-    std::nth_element(elems.begin() + lo, elems.begin() + lo + nl, elems.begin() + hi, [c](int a, int b) {
-      if (c[a] != c[b]) return c[a] < c[b];
-      return a < b;
-    });
-  rcb_rec(cx, cy, elems, lo, lo + nl, kl, part_of, next_part);
-  rcb_rec(cx, cy, elems, lo + nl, hi, k - kl, part_of, next_part);
+  // with nth_element gives exactly the set a full sort would (the keys sit side by side for the selection)
+  if (nl > 0 && nl < n) {
+    keys.resize(n);
+    for (size_t i = 0; i < n; ++i) keys[i] = {c[elems[lo + i]], elems[lo + i]};
+    std::nth_element(keys.begin(), keys.begin() + nl, keys.end());
+    for (size_t i = 0; i < n; ++i) elems[lo + i] = keys[i].second;
+  }
+  rcb_rec(cx, cy, elems, lo, lo + nl, kl, part_of, next_part, keys);
+  rcb_rec(cx, cy, elems, lo + nl, hi, k - kl, part_of, next_part, keys);
 }
 
 void rcb_parts(const MeshData& m, std::vector<int> elems, int k, std::vector<int>& part_of, int first_part) {
   int next = first_part;
-  rcb_rec(m.cx.data(), m.cy.data(), elems, 0, elems.size(), k, part_of, next);
+  std::vector<std::pair<double, int>> keys;
+  rcb_rec(m.cx.data(), m.cy.data(), elems, 0, elems.size(), k, part_of, next, keys);
 }
 
 int compute_partition(const MeshData& m, int nsub, int ncoarse, std::vector<int>& sub, std::vector<int>* agg) {

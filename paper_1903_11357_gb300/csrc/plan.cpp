@@ -300,20 +300,24 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   }
   P.iperm.assign(ne, 0);
   for (int i = 0; i < ne; ++i) P.iperm[P.perm[i]] = i;
-  // permuted CSR (columns ascending in internal ids)
+  // permuted CSR (columns ascending in internal ids; a row's columns are distinct, so insertion places each)
   P.rowptr.assign(ne + 1, 0);
-  P.col.clear();
-  P.src_blk.clear();
-  P.col.reserve(sys.col.size());
-  P.src_blk.reserve(sys.col.size());
-  std::vector<std::pair<int, int>> row;
+  for (int i = 0; i < ne; ++i) P.rowptr[i + 1] = P.rowptr[i] + (sys.rowptr[P.perm[i] + 1] - sys.rowptr[P.perm[i]]);
+  P.col.resize(P.rowptr[ne]);
+  P.src_blk.resize(P.rowptr[ne]);
   for (int i = 0; i < ne; ++i) {
-    int e = P.perm[i];
-    row.clear();
-    for (int k = sys.rowptr[e]; k < sys.rowptr[e + 1]; ++k) row.push_back({P.iperm[sys.col[k]], k});
-    std::sort(row.begin(), row.end());
-    for (auto& c : row) { P.col.push_back(c.first); P.src_blk.push_back(c.second); }
-    P.rowptr[i + 1] = (int)P.col.size();
+    const int e = P.perm[i], base = P.rowptr[i];
+    int n = 0;
+    for (int k = sys.rowptr[e]; k < sys.rowptr[e + 1]; ++k, ++n) {
+      const int c = P.iperm[sys.col[k]];
+      int j = n;
+      for (; j > 0 && P.col[base + j - 1] > c; --j) {
+        P.col[base + j] = P.col[base + j - 1];
+        P.src_blk[base + j] = P.src_blk[base + j - 1];
+      }
+      P.col[base + j] = c;
+      P.src_blk[base + j] = k;
+    }
   }
   // envelopes: first column of each local dof row
   std::vector<std::vector<int>> fc(nsub);
