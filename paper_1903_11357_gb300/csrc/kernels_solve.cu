@@ -16,8 +16,6 @@ namespace dgasm {
 
 namespace {
 
-constexpr int T = 32;
-constexpr int TT = T * T;
 constexpr int NW = NTHREADS / 32;
 // the x / r update runs one CTA per element group (an agglomerate, about 64 elements); 512 threads per CTA
 // measured slower than 256 (the kernel's time is its serial tail, not the pass over the group)
