@@ -2,6 +2,7 @@
 // (Sec. 2: elements kappa, faces F_h = F_h^I u F_h^B, diameter h_kappa).
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <unordered_map>
 
 #include "common.h"
@@ -19,24 +20,25 @@ extern "C" int dgasm_mesh_create(int nv, const double* xy, int ne, const int* po
   *out = nullptr;
   if (nv < 3 || ne < 1 || !xy || !poly_ptr || !poly_vtx || !rho)
     return set_error(DGASM_EINVAL, "dgasm_mesh_create: empty mesh or NULL array");
-  auto* h = new (std::nothrow) dgasm_mesh_s();
+  // owned until it is handed out, so an error return frees it only after its message is formatted
+  std::unique_ptr<dgasm_mesh_s> h(new (std::nothrow) dgasm_mesh_s());
   if (!h) return set_error(DGASM_ENOMEM, "dgasm_mesh_create: host allocation failed");
   MeshData& m = h->m;
   m.nv = nv;
   m.ne = ne;
   m.xy.assign(xy, xy + 2 * (size_t)nv);
-  if (poly_ptr[0] != 0) { delete h; return set_error(DGASM_EINVAL, "poly_ptr[0] must be 0"); }
+  if (poly_ptr[0] != 0) { return set_error(DGASM_EINVAL, "poly_ptr[0] must be 0"); }
   m.ptr.assign(poly_ptr, poly_ptr + ne + 1);
   for (int e = 0; e < ne; ++e) {
-    if (m.ptr[e + 1] - m.ptr[e] < 3) { delete h; return set_error(DGASM_EINVAL, "element %d has fewer than 3 vertices", e); }
+    if (m.ptr[e + 1] - m.ptr[e] < 3) { return set_error(DGASM_EINVAL, "element %d has fewer than 3 vertices", e); }
   }
   m.vtx.assign(poly_vtx, poly_vtx + m.ptr[ne]);
   for (size_t i = 0; i < m.vtx.size(); ++i)
-    if (m.vtx[i] < 0 || m.vtx[i] >= nv) { delete h; return set_error(DGASM_EINVAL, "vertex id %d out of range", m.vtx[i]); }
+    if (m.vtx[i] < 0 || m.vtx[i] >= nv) { return set_error(DGASM_EINVAL, "vertex id %d out of range", m.vtx[i]); }
   m.rho.assign(rho, rho + ne);
   m.area.resize(ne); m.cx.resize(ne); m.cy.resize(ne); m.diam.resize(ne); m.bbox.resize(4 * (size_t)ne);
   for (int e = 0; e < ne; ++e) {
-    if (!(m.rho[e] > 0.0) || !std::isfinite(m.rho[e])) { delete h; return set_error(DGASM_EINVAL, "element %d: rho must be positive and finite", e); }
+    if (!(m.rho[e] > 0.0) || !std::isfinite(m.rho[e])) { return set_error(DGASM_EINVAL, "element %d: rho must be positive and finite", e); }
     int b = m.ptr[e], n = m.ptr[e + 1] - b;
     // shoelace, summed vertex by vertex from the first vertex
     double a2 = 0, sx = 0, sy = 0;
@@ -55,7 +57,7 @@ extern "C" int dgasm_mesh_create(int nv, const double* xy, int ne, const int* po
         dmax = std::max(dmax, std::hypot(P[0] - R[0], P[1] - R[1]));
       }
     }
-    if (!(a2 > 0.0)) { delete h; return set_error(DGASM_EINVAL, "element %d: non-positive signed area (clockwise or degenerate)", e); }
+    if (!(a2 > 0.0)) { return set_error(DGASM_EINVAL, "element %d: non-positive signed area (clockwise or degenerate)", e); }
     m.area[e] = 0.5 * a2;
     m.cx[e] = sx / (3.0 * a2);
     m.cy[e] = sy / (3.0 * a2);
@@ -70,9 +72,9 @@ extern "C" int dgasm_mesh_create(int nv, const double* xy, int ne, const int* po
     int b = m.ptr[e], n = m.ptr[e + 1] - b;
     for (int k = 0; k < n; ++k) {
       int va = m.vtx[b + k], vb = m.vtx[b + (k + 1) % n];
-      if (va == vb) { delete h; return set_error(DGASM_EINVAL, "element %d: repeated consecutive vertex", e); }
+      if (va == vb) { return set_error(DGASM_EINVAL, "element %d: repeated consecutive vertex", e); }
       auto ins = owner.emplace(edge_key(va, vb), e);
-      if (!ins.second) { delete h; return set_error(DGASM_EINVAL, "element %d: edge (%d,%d) used twice in the same direction", e, va, vb); }
+      if (!ins.second) { return set_error(DGASM_EINVAL, "element %d: edge (%d,%d) used twice in the same direction", e, va, vb); }
     }
   }
   struct F { int ep, em, va, vb; };
@@ -110,7 +112,7 @@ extern "C" int dgasm_mesh_create(int nv, const double* xy, int ne, const int* po
     m.ef_face[fill[faces[f].ep]++] = (int)f;
     if (faces[f].em >= 0) m.ef_face[fill[faces[f].em]++] = (int)f;
   }
-  *out = h;
+  *out = h.release();
   return DGASM_OK;
 }
 
