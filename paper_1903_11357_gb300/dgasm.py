@@ -163,6 +163,24 @@ def _dev_ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _nvec(ndof, *arrays, host=False):
+    """Vector count k of arrays shaped (ndof,) or (k, ndof), the same for all of them.  The library reads and
+    writes k * ndof doubles through each pointer, so a shape that does not match is refused here instead of
+    running past the end of a buffer."""
+    k = None
+    for a in arrays:
+        if host and not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise TypeError("expected a C-contiguous float64 numpy array")
+        shape = tuple(a.shape)
+        if len(shape) not in (1, 2) or shape[-1] != ndof:
+            raise ValueError(f"expected shape ({ndof},) or (k, {ndof}), got {shape}")
+        kk = 1 if len(shape) == 1 else shape[0]
+        if k is not None and kk != k:
+            raise ValueError(f"input and output hold different numbers of vectors ({k} and {kk})")
+        k = kk
+    return k
+
+
 class Mesh:
     def __init__(self, xy, poly_ptr, poly_vtx, rho):
         self._xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
@@ -240,6 +258,8 @@ class System:
         return rowptr, col, vals.reshape(-1, self.np, self.np)
 
     def spmv(self, x, y, stream=None):
+        if _nvec(self.ndof, x, y) != 1 or x.dim() != 1:
+            raise ValueError("spmv takes one vector")
         check(lib().dgasm_system_spmv(self.h, _dev_ptr(x), _dev_ptr(y), _stream_ptr(stream)))
 
     def __del__(self):
@@ -283,7 +303,7 @@ class Prec:
         return v.value
 
     def apply(self, r, z, stream=None):
-        k = 1 if r.dim() == 1 else r.shape[0]
+        k = _nvec(self.ndof, r, z)
         check(lib().dgasm_prec_apply(self.h, k, _dev_ptr(r), _dev_ptr(z), _stream_ptr(stream)))
 
     def partition(self):
@@ -309,11 +329,10 @@ class Prec:
         x holds the initial guess on entry.  Returns (return code, [stats dict per right-hand side])."""
         o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=1 if x0_given else 0,
                       host_buffers=1 if host_buffers else 0, stream=_stream_ptr(stream))
+        k = _nvec(self.ndof, b, x, host=host_buffers)
         if host_buffers:
-            k = 1 if b.ndim == 1 else b.shape[0]
             bp, xp = C.c_void_p(b.ctypes.data), C.c_void_p(x.ctypes.data)
         else:
-            k = 1 if b.dim() == 1 else b.shape[0]
             bp, xp = _dev_ptr(b), _dev_ptr(x)
         st = (Stats * k)()
         rc = lib().dgasm_solve(self.h, k, bp, xp, C.byref(o), st)
@@ -329,10 +348,12 @@ class Prec:
 
 def solve_batch(precs, bs, xs, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None, x0_given=False):
     n = len(precs)
+    if len(bs) != n or len(xs) != n:
+        raise ValueError("one b and one x per preconditioner")
     hs = (C.c_void_p * n)(*[p.h.value for p in precs])
-    ks = np.array([1 if b.dim() == 1 else b.shape[0] for b in bs], np.int32)
-    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
-    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    ks = np.array([_nvec(p.ndof, b, x) for p, b, x in zip(precs, bs, xs)], np.int32)
+    bp = (C.c_void_p * n)(*[_dev_ptr(b).value for b in bs])
+    xp = (C.c_void_p * n)(*[_dev_ptr(x).value for x in xs])
     o = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=fixed_iters, x0_given=1 if x0_given else 0, host_buffers=0,
                   stream=_stream_ptr(stream))
     st = (Stats * int(ks.sum()))()
@@ -446,7 +467,7 @@ class Server:
             keep.append(a)
             o.agg_of_elem = _ip(a)
         so = SolveOpts(rtol=rtol, maxit=maxit, fixed_iters=0, x0_given=0, host_buffers=0, stream=None)
-        k = 1 if b.dim() == 1 else b.shape[0]
+        k = _nvec(system.ndof, b, x)
         t = C.c_uint64()
         check(lib().dgasm_submit(self.h, system.h, C.byref(o), k, _dev_ptr(b), _dev_ptr(x), C.byref(so), C.byref(t)))
         self._keep[t.value] = (keep, k)

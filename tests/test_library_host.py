@@ -70,6 +70,27 @@ def test_every_entry_rejects_null_arguments():
         assert getattr(L, name)(None) == dg.OK, name
 
 
+def test_binding_refuses_mismatched_vector_shapes():
+    """The library reads and writes k * ndof doubles through each vector pointer, so the binding checks shapes
+    before any call: a wrong length, different vector counts or a wrong host dtype never reach the library."""
+    import torch
+    assert dg._nvec(10, torch.zeros(10), torch.zeros(10)) == 1
+    assert dg._nvec(10, torch.zeros(3, 10), torch.zeros(3, 10)) == 3
+    for a, b in [(torch.zeros(9), torch.zeros(10)), (torch.zeros(2, 10), torch.zeros(3, 10)),
+                 (torch.zeros(10, 2), torch.zeros(10, 2)), (torch.zeros(2, 2, 10), torch.zeros(2, 2, 10))]:
+        with pytest.raises(ValueError):
+            dg._nvec(10, a, b)
+    P = dg.Prec.__new__(dg.Prec)   # no device: only the checks in front of the call run
+    P.ndof, P.h = 10, None
+    with pytest.raises(ValueError):
+        P.solve(np.zeros(9), np.zeros(10), host_buffers=True)
+    with pytest.raises(TypeError):
+        P.solve(np.zeros(10, np.float32), np.zeros(10), host_buffers=True)
+    with pytest.raises(dg.DgasmError) as e:   # shapes agree: the library refuses the NULL handle
+        P.solve(np.zeros(10), np.zeros(10), host_buffers=True)
+    assert e.value.code == dg.EINVAL
+
+
 def test_mesh_validation_errors():
     sq = quad_mesh(1)
     with pytest.raises(dg.DgasmError) as e:
