@@ -4,7 +4,7 @@ agglomerates at q = 1, rho = 1e4 on the odd cells of a 4 x 4 checkerboard of sub
 non-default stream.  The oracle assembles the system and builds its Schwarz operator at this size (about 1.5
 minutes of host time), so every output of one SpMV and one application of B is compared entry by entry; the
 solve (293 iterations here, too many for the oracle in a test) is checked through the true residual, recomputed
-on the host with the oracle's matrix.
+on the host with the oracle's matrix.  The slowest GPU test file, named to run after the quick ones.
 
 Tolerances:
 * partition and agglomerates: identical (index work);
