@@ -214,6 +214,23 @@ def test_batch_equals_alone():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_eight_right_hand_sides_equal_single_solves(precision):
+    """The widest right-hand-side block (8 vectors, more than the persistent vector kernel's warps per CTA):
+    every column takes the same iterations and reaches the same solution as its own single-vector solve
+    (the same products in the same order; 1e-13 leaves room only for contraction differences)."""
+    c = build_case(600, 5, 2, 4, 16, precision=precision)
+    B = np.random.default_rng(9).standard_normal((8, len(c["b"])))
+    X = torch.zeros_like(dev(B))
+    rc, st = c["P"].solve(dev(B), X, rtol=1e-8)
+    assert rc == 0 and all(s["converged"] for s in st)
+    for j in range(8):
+        x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
+        rc1, st1 = c["P"].solve(dev(B[j]), x, rtol=1e-8)
+        assert rc1 == 0 and st1[0]["iters"] == st[j]["iters"], (j, st1[0]["iters"], st[j]["iters"])
+        assert float(torch.linalg.norm(X[j] - x) / torch.linalg.norm(x)) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_rhs_chunk_choices_give_identical_solutions(precision):
     """1 or 4 right-hand sides per local-solve item: the same products in the same order for every vector,
     so the tuner's (timing-dependent) choice cannot change a solution."""
@@ -235,28 +252,65 @@ def test_rhs_chunk_choices_give_identical_solutions(precision):
     assert torch.equal(X, out[1][0])
 
 
+@pytest.mark.parametrize("variant", ["sweeps", "inverse"])
 @pytest.mark.parametrize("n,p,nsub,ncoarse,q", [(64, 8, 2, 4, 1), (80, 6, 4, 8, 2)])
-def test_high_degree_apply_and_solve_match_oracle(n, p, nsub, ncoarse, q):
+def test_high_degree_apply_and_solve_match_oracle(n, p, nsub, ncoarse, q, variant):
     """The largest blocks the library takes (p = 8: 45 dofs per element, the widest SpMV and envelope rows).
     Two backward-stable Cholesky factorisations of the same matrix differ by up to about kappa * 2^-53 relative,
     and at p = 8 the Jacobi-scaled subdomain matrices reach kappa ~ 1e8 (p = 3: ~4e3), so the apply bound is
-    10 * kappa_max * 2^-53 with kappa_max measured here on the oracle's local and coarse matrices; the solves
-    are checked by the stop test and the iteration count."""
+    10 * kappa_max * 2^-53 with kappa_max measured here on the oracle's local and coarse matrices.
+
+    Solves (Sec. 7 stop test): at the oracle's iteration count k_o the two iterates agree to 1e-10 (8.8e-10 seen
+    at p = 8 comes from the same kappa amplification, so the bound there is the apply bound times 10).  Near
+    the tolerance the residual history can stay within rounding of rtol for several iterations (p = 6 here: the
+    oracle's 1.18, 1.07, 1.15, 1.07, 0.91 e-8 at iterations 203-207), and two FP64 recursions whose iterates
+    agree to that bound then stop a few iterations apart: at p = 8 ||A|| ||x|| / ||b|| is large enough that the
+    residual norms differ by up to about half of rtol.  So the library's stopping iteration k_g and the
+    oracle's k_o are compared through the residuals both recursions carry, at every iteration k from
+    min(k_g, k_o) - 1 to max(k_g, k_o): eta_k = | ||r_k|| - ||r_k^oracle|| | / ||b|| must be explained by the
+    iterates' difference, eta_k <= (||A (x_k - x_k^oracle)|| + gap_k + gap_k^oracle) / ||b|| (triangle inequality;
+    gap = || r_k - (b - A x_k) ||, the drift of each recursion from its true residual), and each stop must be a
+    stop of the other history up to eta = max eta_k (the oracle's residual at k_g and the library's at k_o are
+    <= rtol + eta).  Both local-solve variants (sweeps and explicit inverses) are checked."""
     c = build_case(n, 2, p, nsub, ncoarse, q)
+    c["P"].set_local_variant(variant)
     A, O = c["A"].tocsr(), c["O"]
     kmax = 0.0
     for M in [A[idx][:, idx].toarray() for idx in O.local_dofs] + [O.A0]:
         d = 1.0 / np.sqrt(np.diag(M))
         ev = np.linalg.eigvalsh(M * d[:, None] * d[None, :])
         kmax = max(kmax, ev[-1] / ev[0])
+    apply_bound = 10.0 * kmax * 2.0 ** -53
     r = np.random.default_rng(4).standard_normal(A.shape[0])
     z = torch.zeros_like(dev(r))
     c["P"].apply(dev(r), z)
     torch.cuda.synchronize()
     ref = O.apply(r)
-    assert np.linalg.norm(z.cpu().numpy() - ref) <= 10.0 * kmax * 2.0 ** -53 * np.linalg.norm(ref)
-    oref = pcg.pcg(A, c["b"], O.apply, rtol=1e-8)
-    x = torch.zeros(len(c["b"]), dtype=torch.float64, device="cuda")
-    rc, st = c["P"].solve(dev(c["b"]), x, rtol=1e-8)
+    assert np.linalg.norm(z.cpu().numpy() - ref) <= apply_bound * np.linalg.norm(ref)
+    b = c["b"]
+    oref = pcg.pcg(A, b, O.apply, rtol=1e-8)
+    ko = oref.iters
+    xk = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    c["P"].solve(dev(b), xk, fixed_iters=ko)
+    xk = xk.cpu().numpy()
+    assert np.linalg.norm(xk - oref.x) <= max(1e-10, 10.0 * apply_bound) * np.linalg.norm(oref.x)
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    rc, st = c["P"].solve(dev(b), x, rtol=1e-8)
     assert rc == 0 and st[0]["converged"] and st[0]["true_relres"] <= 1e-8
-    assert abs(st[0]["iters"] - oref.iters) <= max(2, 0.02 * oref.iters)
+    kg = st[0]["iters"]
+    bn = np.linalg.norm(b)
+    etas = []
+    rel_g, rel_o = {}, {}
+    for k in range(min(kg, ko) - 1, max(kg, ko) + 1):
+        xf = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+        _, sf = c["P"].solve(dev(b), xf, fixed_iters=k)
+        xg = xf.cpu().numpy()
+        ok = pcg.pcg(A, b, O.apply, fixed_iters=k)
+        rel_g[k], rel_o[k] = sf[0]["relres"], ok.resid[-1]
+        gap_g = abs(rel_g[k] - np.linalg.norm(b - A @ xg) / bn)
+        gap_o = abs(rel_o[k] - np.linalg.norm(b - A @ ok.x) / bn)
+        eta_k = abs(rel_g[k] - rel_o[k])
+        assert eta_k <= 1.01 * (np.linalg.norm(A @ (xg - ok.x)) / bn + gap_g + gap_o), k
+        etas.append(eta_k)
+    eta = max(etas)
+    assert rel_o[kg] <= 1e-8 + eta and rel_g[ko] <= 1e-8 + eta, (kg, ko, eta)

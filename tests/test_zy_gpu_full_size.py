@@ -2,9 +2,11 @@
 Lloyd-relaxed Voronoi cells (seed 2), p = 3 (163840 dofs), C_sigma = 10, 64 RCB subdomains, 256 RCB
 agglomerates at q = 1, rho = 1e4 on the odd cells of a 4 x 4 checkerboard of subdomains, FP64, launches on a
 non-default stream.  The oracle assembles the system and builds its Schwarz operator at this size (about 1.5
-minutes of host time), so every output of one SpMV and one application of B is compared entry by entry; the
-solve (293 iterations here, too many for the oracle in a test) is checked through the true residual, recomputed
-on the host with the oracle's matrix.  The slowest GPU test file, named to run after the quick ones.
+minutes of host time), so every output of one SpMV and one application of B is compared entry by entry, and
+the iterate after a fixed number of PCG iterations (Sec. 7, both from x = 0 with the oracle's load vector) is
+compared with the oracle's.  The solve to 1e-8 is checked against the oracle's own converged solve, stored by
+tests/golden/make_oracle_solutions.py (which calls only the oracle): the iteration count, and the solution at
+1000 sampled dofs through an a-posteriori bound.  The slowest GPU test file, named to run after the quick ones.
 
 Tolerances:
 * partition and agglomerates: identical (index work);
@@ -14,15 +16,20 @@ Tolerances:
   Jacobi-scaled; the larger one, about 3e6, dominates) and every eighth Jacobi-scaled subdomain matrix (about
   2e4 to 6e4: rho is constant on each subdomain, so their conditioning is alike);
 * solve: converged, the library's own true relative residual <= 1e-8, and ||b - A x|| / ||b|| with the oracle's
-  A <= 1e-8 + 10 * 2^-53 * || |A| |x| || / ||b|| (the rounding floor of any residual evaluated in FP64).
+  A <= 1e-8 + 10 * 2^-53 * || |A| |x| || / ||b|| (the rounding floor of any residual evaluated in FP64);
+* fixed iterations: ||x_k - x_k^oracle|| <= 1e-10 ||x_k^oracle|| at k = 40 (the FP64 parity rule: equal
+  iteration counts, so no stopping-iteration difference enters);
+* iterations to 1e-8: within one of the oracle's; the sampled solution entries within the a-posteriori bound
+  (||b - A x|| + ||b - A x_oracle||) / lambda_min(A) of the oracle's (both residuals measured, lambda_min stored).
 """
 import numpy as np
 import pytest
 
-from oracle import partition, schwarz, sipg
+from oracle import partition, pcg, schwarz, sipg
 from oracle.geometry import build_geometry
 from synth.coeff import checker_per_subdomain
 from synth.voronoi import voronoi_mesh
+from tests.golden.make_oracle_solutions import load as load_oracle_solve
 from tests.helpers import f_sin, have_gpu
 
 pytestmark = pytest.mark.gpu
@@ -46,13 +53,13 @@ def case():
     sub = partition.subdomains(g.centroid, NSUB)
     agg = partition.agglomerates(g.centroid, sub, NSUB, NCOARSE)
     rho = checker_per_subdomain(m, sub, CONTRAST)
-    A, _, _ = sipg.assemble(m, rho, P_DEG, 10.0, geom=g)
+    A, b, _ = sipg.assemble(m, rho, P_DEG, 10.0, f_sin, geom=g)
     A = A.tocsr()
     O = schwarz.build(A, m, g, P_DEG, sub, agg, Q)
     stream = torch.cuda.Stream()
     S = dg.System(dg.Mesh.from_polymesh(m, rho), P_DEG, 10.0, f=f_sin)
     P = dg.Prec(S, NSUB, NCOARSE, Q, precision="fp64", stream=stream)
-    return dict(A=A, O=O, S=S, P=P, sub=sub, agg=agg, stream=stream)
+    return dict(A=A, b=b, O=O, S=S, P=P, sub=sub, agg=agg, stream=stream)
 
 
 def test_full_size_partition_is_the_oracles(case):
@@ -105,3 +112,39 @@ def test_full_size_solve_reaches_the_tolerance(case):
     xh = x.cpu().numpy()
     floor = 10.0 * EPS * np.linalg.norm(abs(A) @ np.abs(xh)) / np.linalg.norm(b)
     assert np.linalg.norm(b - A @ xh) / np.linalg.norm(b) <= 1e-8 + floor
+
+
+FIXED_K = 40
+
+
+def test_full_size_fixed_iterations_match_oracle(case):
+    A, O, b = case["A"], case["O"], case["b"]
+    ref = pcg.pcg(A, b, O.apply, fixed_iters=FIXED_K)
+    bd = dev(b)
+    x = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    rc, st = case["P"].solve(bd, x, fixed_iters=FIXED_K, stream=case["stream"])
+    torch.cuda.synchronize()
+    assert st[0]["iters"] == FIXED_K
+    diff = np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x)
+    assert diff <= 1e-10, diff
+
+
+def test_full_size_solve_matches_oracle_solve(case):
+    A, b = case["A"], case["b"]
+    ref = load_oracle_solve("p3_c1e4")
+    idx = ref["idx"]
+    # the stored solve is of this very system (the oracle's load vector, up to the host's rounding of sin)
+    assert np.abs(b[idx] - ref["b"]).max() <= 1e-12 * np.abs(b).max()
+    bd = dev(b)
+    x = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    rc, st = case["P"].solve(bd, x, rtol=1e-8, stream=case["stream"])
+    torch.cuda.synchronize()
+    assert rc == 0 and st[0]["converged"]
+    assert abs(st[0]["iters"] - int(ref["iters"])) <= 1, (st[0]["iters"], ref["iters"])
+    xh = x.cpu().numpy()
+    bn = np.linalg.norm(b)
+    res_gpu = np.linalg.norm(b - A @ xh)
+    bound = (res_gpu + ref["true_relres"] * bn) / ref["lambda_min"]
+    assert np.abs(xh[idx] - ref["x"]).max() <= bound
