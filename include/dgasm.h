@@ -135,19 +135,20 @@ int dgasm_system_blocks(dgasm_system_t s, int64_t* nnzb, int* rowptr, int* col, 
 int dgasm_system_spmv(dgasm_system_t s, const double* x, double* y, void* stream);
 int dgasm_system_destroy(dgasm_system_t s);
 
-/* y = A x and the energy product x^T A x, without any device allocation (the paper has no counterpart:
- * this serves callers that cannot allocate, e.g. code running inside a CUDA stream capture, where
- * cudaMalloc cannot be captured, code whose device memory belongs to another runtime's caching
- * allocator, or real-time loops that forbid allocation after start-up).  x, y are device arrays of ndof
- * doubles in the caller's dof order, xAx a device pointer to one double; all three are the caller's.
- * The per-block partial sums live in a fixed 512 KB (+256 B) __device__ array inside the library, so a
- * call handles at most 65536 thread blocks of 256 threads (65536 * floor(256 / n_p) elements, e.g.
- * 1.6 million elements at p = 3); larger systems get DGASM_ETOOBIG.  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress) with that device current: make that first call
- * before any stream capture.  The array is shared by every call on a device and keeps the last call's
- * contents (its counter is cleared at the start of each call), so calls that overlap on the GPU (on
- * different streams, or from different threads) race: serialise them.  The matrix must already be on
- * the device (dgasm_system_spmv or dgasm_setup upload it on first use); otherwise DGASM_EINVAL.
+/* y = A x and the energy product x^T A x, without any device allocation (the paper has no counterpart).
+ * It serves callers that must not allocate device memory once they run: code whose device memory belongs
+ * to another runtime's caching allocator, which a cudaMalloc would bypass and fragment, and real-time loops
+ * whose memory is fixed at start-up.  x, y are device arrays of ndof doubles in the caller's dof order,
+ * xAx a device pointer to one double; all three are the caller's and must not overlap (DGASM_EINVAL).
+ * The per-block partial sums live in a fixed 512 KB (+256 B) __device__ array inside the library, held by
+ * every GPU that loads it until the process exits, so a call handles at most 65536 thread blocks of 256
+ * threads (65536 * floor(256 / n_p) elements, e.g. 1.6 million elements at p = 3); larger systems get
+ * DGASM_ETOOBIG.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream capture.  The
+ * array is shared by every call on a device and keeps the last call's contents (its counter is cleared at
+ * the start of each call), so calls that overlap on the GPU (on different streams, or from different
+ * threads) race: serialise them.  The matrix must already be on the device (dgasm_system_spmv or
+ * dgasm_setup upload it on first use), and that device must be the current one; otherwise DGASM_EINVAL.
  * Asynchronous on the stream; y is bitwise identical to dgasm_system_spmv's. */
 int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, double* y, double* xAx, void* stream);
 
@@ -220,6 +221,20 @@ int dgasm_nonnested_prolongation(dgasm_mesh_t fine, dgasm_mesh_t coarse, int p, 
  * Errors: DGASM_EINVAL. */
 int dgasm_prec_set_rhs_chunk(dgasm_prec_t pc, int nrhs, int kc);
 int dgasm_prec_get_rhs_chunk(dgasm_prec_t pc, int nrhs, int* kc);
+/* Local-solve variant (Sec. 3, local solvers z_i = A_i^{-1} r_i): 1 = forward and backward substitution with the
+ * tile-envelope Cholesky factors (the sweeps); 2 = explicit inverses X_i = A_i^{-1}, formed once from those
+ * factors (the sweeps applied to unit vectors, in the factor precision) and kept dense (FP64 in FP64 mode, FP32
+ * otherwise), so that a local solve is one matrix-vector product per subdomain with no sequential dependency:
+ * faster for small subdomains, whose sweeps are latency bound.  Only preconditioners whose subdomains have at
+ * most 2048 dofs and whose inverses take at most 1 GiB can use 2 (DGASM_EINVAL otherwise; setting 2 forms the
+ * inverses at once).  0 (the default) lets the first dgasm_solve / dgasm_solve_batch measure both (one warm-up
+ * and two timed preconditioner applications each) and keep the faster; the outcome is reused for later
+ * preconditioners of the same shape (precision, n_p, subdomain count, largest subdomain in steps of 128 dofs,
+ * right-hand sides).  The two variants give the same solution up to rounding.  get returns the current choice
+ * (0 = not measured yet; 2 when every subdomain is one element, whose block inverses are always explicit).
+ * Errors: DGASM_EINVAL. */
+int dgasm_prec_set_local_variant(dgasm_prec_t pc, int variant);
+int dgasm_prec_get_local_variant(dgasm_prec_t pc, int* variant);
 /* Partition actually used (host arrays [ne]); either pointer may be NULL; agg_of_elem is not written when
  * the coarse space lives on a coarse_mesh. */
 int dgasm_prec_partition(dgasm_prec_t pc, int* sub_of_elem, int* agg_of_elem);

@@ -256,6 +256,7 @@ extern "C" int dgasm_assemble_device(dgasm_mesh_t mh, int p, double c_sigma, dga
   if (f) assemble_rhs(m, Basis(p), f, user, s.get());   // overlaps the kernel
   DG_CUDA(cudaStreamSynchronize(st));
   s->d_vals = std::move(vals);
+  DG_CUDA(cudaGetDevice(&s->dev));
   *out = s.release();
   return DGASM_OK;
 }
@@ -309,6 +310,7 @@ int dgasm_system_s::ensure_device() {
   DG_TRY(upload(d_pvtx, m.vtx));
   DG_TRY(upload(d_bbox, m.bbox));
   DG_TRY(upload(d_vals, dv));
+  DG_CUDA(cudaGetDevice(&dev));
   return DGASM_OK;
 }
 

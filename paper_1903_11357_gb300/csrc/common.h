@@ -90,6 +90,7 @@ struct dgasm_system_s {
   dgasm::DevBuf d_rowptr, d_col, d_vals;
   // device geometry for the coarse transfer
   dgasm::DevBuf d_xy, d_pptr, d_pvtx, d_bbox;
+  int dev = -1;                      // CUDA device that holds the device arrays (-1: not uploaded yet)
   std::mutex dev_mu;
   int ensure_device();
   int ensure_host();   // host blocks of a device-assembled system

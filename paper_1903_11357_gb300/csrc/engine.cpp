@@ -5,6 +5,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cuda_runtime.h>
 
@@ -18,7 +21,10 @@ namespace dgasm {
 
 // ---- workspace of one problem for k right-hand sides ------------------------------------------
 int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
-  if (k_ <= k && maxit_ <= maxit && buf.ptr) return DGASM_OK;
+  // partial (r, z) sums: one per subdomain, element chunk (element blocks) or explicit-inverse item
+  const int need_rz = std::max(pc.P.nsub, std::max(pc.n_dli_items, (pc.P.ne + NTHREADS / pc.P.np - 1) / (NTHREADS / pc.P.np)));
+  if (k_ <= k && maxit_ <= maxit && need_rz <= n_rz_cap && buf.ptr) return DGASM_OK;
+  n_rz_cap = need_rz;
   k = std::max(k_, k);
   maxit = std::max(maxit_, maxit);
   const Plan& P = pc.P;
@@ -39,7 +45,7 @@ int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
   o_hist = take(sizeof(double) * 2 * (size_t)k * maxit);
   o_ppq = take(sizeof(double) * (size_t)n_spmv_items * k);
   o_prr = take(sizeof(double) * (size_t)P.ngrp * k);
-  o_prz = take(sizeof(double) * (size_t)P.nsub * k);
+  o_prz = take(sizeof(double) * (size_t)n_rz_cap * k);
   o_pc = take(sizeof(double) * (size_t)std::max(n_coarse_items, 1) * k);
   o_cnt = take(sizeof(unsigned) * C_NCOUNTERS);
   DG_TRY(buf.alloc(off));
@@ -70,7 +76,12 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   D.bwd_ptr = pc.env.bwd_ptr.as<long long>();
   D.sr = pc.P.env.sr;
   D.dinv = pc.blocks ? pc.dinv.as<double>() : nullptr;
-  D.n_rz = pc.blocks ? n_chunk_items : P.nsub;
+  const bool inv = !pc.blocks && pc.local_variant == LV_INVERSE;
+  D.n_rz = pc.blocks ? n_chunk_items : inv ? pc.n_dli_items : P.nsub;
+  D.dli = inv ? pc.dli.ptr : nullptr;
+  D.dli_off = inv ? pc.dli_off.as<long long>() : nullptr;
+  D.dli_item = inv ? pc.dli_item.as<int>() : nullptr;
+  D.n_dli_items = inv ? pc.n_dli_items : 0;
   D.sub_sr = pc.env.sub_sr.as<int>(); D.fwd_run = pc.env.fwd_run.as<int>(); D.bwd_run = pc.env.bwd_run.as<int>();
   D.Lr = pc.Lr.ptr; D.Lc = pc.Lc.ptr; D.scale = pc.scale.as<double>();
   D.fwd_total = (long long)pc.P.env.fwd_src.size();
@@ -155,6 +166,8 @@ int Engine::build(int n, dgasm_prec_s* const* pcs_, const int* nrhs_, const doub
     P_(K_RNN, i + 1) += D.r0t_ptr ? D.nc : 0;
     if (pc->blocks) {
       P_(K_BJAC, i + 1) += D.n_chunk_items;
+    } else if (D.dli) {
+      P_(K_DLI + (D.prec == DGASM_FP64 ? 0 : 1), i + 1) += D.n_dli_items;
     } else {
       const int slot = 2 * D.prec + (D.kc > 1 ? 1 : 0);
       P_(K_NKINDS + slot, i + 1) += D.nsub * D.n_rhs_chunks;
@@ -237,6 +250,10 @@ int Engine::precond(int mode, EventPairs* ev) {
   const int tot_bjac = pre[K_BJAC * (n + 1) + n];
   if (tot_bjac)
     DG_CUDA(timed_launch(PK_LOCAL, stream, ev, launches, [&] { return launch_bjac(B, tot_bjac, km, stream); }));
+  for (int slot = K_DLI; slot <= K_DLI + 1; ++slot) {
+    const int tot = pre[slot * (n + 1) + n];
+    if (tot) DG_CUDA(timed_launch(PK_LOCAL, stream, ev, launches, [&] { return launch_dli(B, slot, tot, km, stream); }));
+  }
   DG_CUDA(cudaStreamWaitEvent(stream, ev_join, 0));
   DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, km, tot_rnn > 0, stream); }));
   return DGASM_OK;
@@ -528,6 +545,73 @@ int tune_rhs_chunk(dgasm_prec_s* pc, int nrhs, const double* b, cudaStream_t str
   return rc;
 }
 
+// The local solves of a preconditioner whose subdomains are small enough can use explicit inverses (one
+// dense matrix-vector product per subdomain) instead of the forward/backward sweeps.  The first solve
+// measures both on b (one warm-up and two timed preconditioner applications each) and keeps the faster; the
+// inverses are freed again if the sweeps win.  Both give the same solution up to rounding.
+// The outcome is kept per shape (precision, n_p, subdomain count, largest subdomain in steps of 128 dofs,
+// right-hand sides), so that a stream of similar problems measures once.
+namespace {
+std::mutex g_variant_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_variant;
+}  // namespace
+
+int tune_local_variant(dgasm_prec_s* pc, int nrhs, const double* b, cudaStream_t stream) {
+  if (pc->blocks || pc->local_variant != LV_TUNE) return DGASM_OK;
+  if (!dli_candidate(*pc)) {
+    pc->local_variant = LV_SWEEPS;
+    return DGASM_OK;
+  }
+  int nmax = 0;
+  for (int s = 0; s < pc->P.nsub; ++s) nmax = std::max(nmax, pc->P.env.ndof[s]);
+  const auto key = std::make_tuple(pc->precision, pc->P.np, pc->P.nsub, (nmax + 127) / 128, nrhs);
+  {
+    std::lock_guard<std::mutex> lk(g_variant_mu);
+    auto it = g_variant.find(key);
+    if (it != g_variant.end()) {
+      if (it->second == LV_INVERSE) DG_TRY(build_dli(pc));
+      pc->local_variant = it->second;
+      return DGASM_OK;
+    }
+  }
+  DG_TRY(build_dli(pc));
+  const size_t n = (size_t)pc->P.ne * pc->P.np * nrhs;
+  DevBuf z;
+  DG_TRY(z.alloc(n * sizeof(double)));
+  cudaEvent_t e0, e1;
+  DG_CUDA(cudaEventCreate(&e0));
+  DG_CUDA(cudaEventCreate(&e1));
+  const int cand[2] = {LV_SWEEPS, LV_INVERSE};
+  float best = 0.f;
+  int pick = LV_SWEEPS, rc = DGASM_OK;
+  for (int c = 0; c < 2 && rc == DGASM_OK; ++c) {
+    pc->local_variant = cand[c];
+    rc = apply_locked(pc, nrhs, b, z.as<double>(), stream);
+    if (rc) break;
+    cudaEventRecord(e0, stream);
+    for (int r = 0; r < 2 && rc == DGASM_OK; ++r) rc = apply_locked(pc, nrhs, b, z.as<double>(), stream);
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_error((int)cudaGetLastError(), "local-solve variant tuning");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (c == 0 || ms < best) { best = ms; pick = cand[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pc->local_variant = rc == DGASM_OK ? pick : LV_TUNE;
+  if (rc == DGASM_OK) {
+    std::lock_guard<std::mutex> lk(g_variant_mu);
+    g_variant[key] = pick;
+  }
+  if (pc->local_variant != LV_INVERSE) {
+    pc->dli.reset();
+    pc->dli_off.reset();
+    pc->dli_item.reset();
+    pc->n_dli_items = 0;
+  }
+  return rc;
+}
+
 }  // namespace dgasm
 
 extern "C" int dgasm_prec_set_rhs_chunk(dgasm_prec_t pc, int nrhs, int kc) {
@@ -536,6 +620,32 @@ extern "C" int dgasm_prec_set_rhs_chunk(dgasm_prec_t pc, int nrhs, int kc) {
   if (kc != 0 && kc != 1 && kc != KC) return set_error(DGASM_EINVAL, "kc=%d must be 0 (tune), 1 or %d", kc, KC);
   std::lock_guard<std::mutex> lk(pc->mu);
   pc->rhs_chunk[nrhs] = kc;
+  return DGASM_OK;
+}
+
+extern "C" int dgasm_prec_set_local_variant(dgasm_prec_t pc, int variant) {
+  clear_error();
+  if (!pc || variant < LV_TUNE || variant > LV_INVERSE)
+    return set_error(DGASM_EINVAL, "dgasm_prec_set_local_variant: bad arguments");
+  std::lock_guard<std::mutex> lk(pc->mu);
+  if (pc->blocks) return variant == LV_INVERSE || variant == LV_TUNE ? DGASM_OK
+                                                                    : set_error(DGASM_EINVAL, "element-block local solves have no sweeps");
+  if (variant == LV_INVERSE) DG_TRY(build_dli(pc));
+  pc->local_variant = variant;
+  if (variant != LV_INVERSE) {
+    pc->dli.reset();
+    pc->dli_off.reset();
+    pc->dli_item.reset();
+    pc->n_dli_items = 0;
+  }
+  return DGASM_OK;
+}
+
+extern "C" int dgasm_prec_get_local_variant(dgasm_prec_t pc, int* variant) {
+  clear_error();
+  if (!pc || !variant) return set_error(DGASM_EINVAL, "dgasm_prec_get_local_variant: bad arguments");
+  std::lock_guard<std::mutex> lk(pc->mu);
+  *variant = pc->blocks ? LV_INVERSE : pc->local_variant;
   return DGASM_OK;
 }
 
@@ -564,6 +674,7 @@ extern "C" int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x
     double* dx = db + n;
     DG_CUDA(cudaMemcpyAsync(db, b, n * sizeof(double), cudaMemcpyHostToDevice, stream));
     if (o->x0_given) DG_CUDA(cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, stream));
+    DG_TRY(tune_local_variant(pc, nrhs, db, stream));
     DG_TRY(tune_rhs_chunk(pc, nrhs, db, stream));
     const double* bb[1] = {db};
     double* xx[1] = {dx};
@@ -573,6 +684,7 @@ extern "C" int dgasm_solve(dgasm_prec_t pc, int nrhs, const double* b, double* x
     DG_CUDA(cudaStreamSynchronize(stream));
     return rc;
   }
+  DG_TRY(tune_local_variant(pc, nrhs, b, stream));
   DG_TRY(tune_rhs_chunk(pc, nrhs, b, stream));
   const double* bb[1] = {b};
   double* xx[1] = {x};
@@ -595,6 +707,7 @@ extern "C" int dgasm_solve_batch(int nprob, const dgasm_prec_t* pcs, const int* 
   if (!eng) eng.reset(new (std::nothrow) Engine());
   if (!eng) return set_error(DGASM_ENOMEM, "host allocation failed");
   cudaStream_t stream = (o && o->stream) ? (cudaStream_t)o->stream : pcs[0]->stream;
+  for (int i = 0; i < nprob; ++i) DG_TRY(tune_local_variant(pcs[i], nrhs[i], b[i], stream));
   return solve_all(*eng, nprob, pcs, nrhs, b, x, o, stream, st);
 }
 

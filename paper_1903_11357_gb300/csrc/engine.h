@@ -24,7 +24,9 @@ enum Kind { K_SPMV = 0, K_GRP = 1, K_LOCAL = 2, K_COARSE = 3, K_NKINDS = 4 };
 constexpr int K_SPMV_P = K_NKINDS + 8;   // per-degree SpMV prefix slots p = 1..8
 constexpr int K_BJAC = K_SPMV_P + 8;     // element-block local solves (subdomains = elements)
 constexpr int K_RNN = K_BJAC + 1;        // restriction r_0 = R_0 r of non-nested coarse spaces (one item per cell)
-constexpr int K_NSLOTS = K_RNN + 1;
+constexpr int K_DLI = K_RNN + 1;         // local solves with explicit inverses: K_DLI FP64, K_DLI + 1 FP32 storage
+constexpr int K_NSLOTS = K_DLI + 2;
+constexpr int DLI_ROWS = 32;             // rows of an explicit-inverse local-solve item
 enum Counter { C_SPMV = 0, C_GRP = 1, C_PUPD = 2, C_NCOUNTERS = 4 };
 
 // One problem (one preconditioner with k right-hand sides) of a batch.
@@ -54,7 +56,14 @@ struct ProbDev {
   long long fwd_total, bwd_total;  // tiles in each stream (all subdomains)
   int sr;                       // tile rows per super-row of the local factors
   const double* dinv;           // subdomains = elements: [ne][np][np] inverses of the diagonal blocks, row-major
-  int n_rz;                     // partial sums of (r, z): nsub (envelope solves) or n_chunk_items (blocks)
+  int n_rz;                     // partial sums of (r, z): nsub (envelope solves), n_chunk_items (blocks) or
+                                // n_dli_items (explicit inverses)
+  // explicit subdomain inverses (local-solve variant for small subdomains): X_s = A_s^{-1} dense row-major at
+  // dli_off[s] in dli (FP64, or FP32 for the lower-precision modes); items (subdomain, first row) in dli_item
+  const void* dli;
+  const long long* dli_off;
+  const int* dli_item;
+  int n_dli_items;
   const int* sub_sr;            // [nsub+1] first global super-row of each subdomain
   const int* fwd_run;           // [global super-row][sr][2]: coupling runs (first operand block, tiles)
   const int* bwd_run;
@@ -118,6 +127,13 @@ int launch_coarse(const BatchDev& B, int total, int km, void* stream);
 // up and set the error word), err[1] = 1 (the wait returned false)
 int launch_wait_selftest(int* err, long long limit, void* stream);
 int launch_bjac(const BatchDev& B, int total, int km, void* stream);
+// explicit-inverse local solves (kernels_dli.cu): slot K_DLI (FP64 inverses) or K_DLI + 1 (FP32)
+int launch_dli(const BatchDev& B, int slot, int total, int km, void* stream);
+// r zero on entry: column kk of r ([cb][ndof]) becomes unit vector c0 + kk of every subdomain
+int launch_unit_block(const int* sub_e0, int nsub, int np, int c0, int cb, long long ndof, double* r, void* stream);
+// X_s[i][c0 + kk] = z[kk][d0_s + i] into the explicit inverses (FP64 if fp64, else FP32); nmax = largest n_s
+int launch_dli_store(int fp64, const int* sub_e0, int nsub, int np, const long long* off, int c0, int cb,
+                     long long ndof, const double* z, void* X, int nmax, void* stream);
 // nonnested: some problem of the batch has a non-nested coarse space
 int launch_pupdate(const BatchDev& B, int total, int mode, int km, int nonnested, void* stream);
 // r_0 = R_0 r for non-nested coarse spaces: one CTA per coarse cell (prefix slot K_RNN)

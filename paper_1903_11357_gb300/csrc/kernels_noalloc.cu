@@ -1,8 +1,7 @@
 // Allocation-free entry point: y = A x together with the energy product x^T A x, for callers that must
-// not allocate device memory.  Such callers include code that runs while another runtime owns the
-// device allocator (a framework's caching allocator that must not be bypassed or fragmented), code that
-// runs inside a CUDA stream capture (cudaMalloc is not a capturable operation), and real-time loops that
-// forbid allocation after start-up.
+// not allocate device memory after start-up: code whose device memory belongs to another runtime's caching
+// allocator (which a cudaMalloc would bypass and fragment), and real-time loops whose allocation budget is
+// fixed when they start.
 //
 // The kernel is a variant of the system SpMV: one thread per (element, row) as in dgasm_system_spmv, plus
 // a deterministic reduction of x . (A x): every CTA writes its partial sum, and the last CTA (fenced
@@ -10,6 +9,7 @@
 // __device__ array of fixed size instead of memory allocated per call.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "common.h"
@@ -100,15 +100,43 @@ int scratch_address(void** out) {
 
 }  // namespace
 
+namespace {
+// [a, a + na) and [b, b + nb) overlap (byte ranges of two caller arrays)
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return a0 < b0 + nb && b0 < a0 + na;
+}
+}  // namespace
+
 extern "C" int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, double* y, double* xAx, void* stream) {
   using namespace dgasm;
   clear_error();
   if (!s || !x || !y || !xAx) return set_error(DGASM_EINVAL, "dgasm_system_spmv_dot_noalloc: NULL argument");
-  if (!s->d_vals.ptr)
+  const int ne = s->mesh->m.ne, np = s->np;
+  const size_t vbytes = sizeof(double) * (size_t)ne * np;
+  // x is read by every thread while y is written: the three arrays must not share memory
+  if (overlap(x, vbytes, y, vbytes) || overlap(xAx, sizeof(double), x, vbytes) || overlap(xAx, sizeof(double), y, vbytes))
+    return set_error(DGASM_EINVAL, "dgasm_system_spmv_dot_noalloc: x, y and xAx must not overlap");
+  const int *rowptr, *col;
+  const double* vals;
+  int sys_dev;
+  {
+    // the upload (dgasm_system_spmv, dgasm_setup) publishes these under the same lock; host-only, no allocation
+    std::lock_guard<std::mutex> lk(s->dev_mu);
+    rowptr = s->d_rowptr.as<int>();
+    col = s->d_col.as<int>();
+    vals = s->d_vals.as<double>();
+    sys_dev = s->dev;
+  }
+  if (!vals)
     return set_error(DGASM_EINVAL,
                      "dgasm_system_spmv_dot_noalloc: the matrix is not on the device yet; call dgasm_system_spmv "
                      "or dgasm_setup once first (they upload it)");
-  const int ne = s->mesh->m.ne, np = s->np;
+  int cur = -1;
+  DG_CUDA(cudaGetDevice(&cur));
+  if (cur != sys_dev)
+    return set_error(DGASM_EINVAL, "dgasm_system_spmv_dot_noalloc: the matrix lives on device %d, device %d is current",
+                     sys_dev, cur);
   const int epi = NT / np;
   const long long ctas = ((long long)ne + epi - 1) / epi;
   if (ctas > (long long)NOALLOC_MAX_CTAS)
@@ -120,8 +148,8 @@ extern "C" int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, 
   cudaStream_t st = (cudaStream_t)stream;
   // the counter must start at zero (a clear, not an allocation)
   DG_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned int), st));
-  k_spmv_dot_noalloc<<<(unsigned)ctas, NT, 0, st>>>(s->d_rowptr.as<int>(), s->d_col.as<int>(), s->d_vals.as<double>(),
-                                                    ne, np, s->np2s, x, y, xAx, (unsigned char*)scratch);
+  k_spmv_dot_noalloc<<<(unsigned)ctas, NT, 0, st>>>(rowptr, col, vals, ne, np, s->np2s, x, y, xAx,
+                                                    (unsigned char*)scratch);
   DG_CUDA(cudaGetLastError());
   return DGASM_OK;
 }

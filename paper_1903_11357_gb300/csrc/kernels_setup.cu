@@ -92,47 +92,59 @@ __global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, 
   using C = typename Compute<S>::type;
   __shared__ C a[T][T + 1];
   __shared__ C inv[T][T + 1];
-  __shared__ C rdj;
+  __shared__ C rdbuf[2];   // 1/sqrt(pivot) of step j in rdbuf[j & 1]
   __shared__ int bad;
   int s = tasks[blockIdx.x];
   long long ti = tile_index(E, s, K, K);
   S* tile = L + ti * TT;
-  int tid = threadIdx.x;
-  if (tid == 0) bad = -1;
+  const int tid = threadIdx.x;
   for (int t = tid; t < TT; t += blockDim.x) {
     int r = t / T, c = t % T;
     a[r][c] = (r >= c) ? (C)tile[t] : (C)0;
     inv[r][c] = (r == c) ? (C)1 : (C)0;
   }
   __syncthreads();
-  // Right-looking Cholesky of the tile, and in the same sweep the inverse X = inv(L) by forward
-  // elimination of L X = I: once column j of L is known, row j of X is final and the rows below it take
-  // their update from it.  Each step is parallel over the entries it touches (one warp per tile is
-  // slower: the FP64 pipe spends its slots on the lanes a triangular step leaves idle).
+  if (tid == 0) {
+    bad = -1;
+    C d = a[0][0];
+    if (!(d > (C)0)) { bad = 0; d = (C)1; }
+    rdbuf[0] = crsqrt<C>(d);
+  }
+  __syncthreads();
+  // Right-looking Cholesky of the tile, and in the same sweep X = inv(L) by forward elimination of L X = I,
+  // with one barrier per step.  Step j reads the pivot d = a_jj, column j of A and row j of X as the earlier
+  // steps left them (not yet divided by sqrt(d)); with rd = 1/sqrt(d), l_rj = a_rj rd and x_jc = x~_jc rd, so
+  //   a_rc -= u_r a_cj   (c > j, r >= c)      and      x_rc -= u_r x~_jc   (r > j, c <= j),    u_r = a_rj rd^2.
+  // Nothing writes column j of A or row j of X during step j; row j - 1 of X is scaled by its rd in step j,
+  // when nothing reads it any more (row T - 1 after the loop).  Eight threads share a row (u_r computed once
+  // and shuffled); the thread that updates a_(j+1)(j+1) forms the next pivot's rd.  L itself is not stored: the
+  // tile receives X = inv(L_KK), and only the pivots of A are read again.
+  const int r = tid >> 3, sub = tid & 7;
+  C rd_prev = (C)0;
   for (int j = 0; j < T; ++j) {
-    if (tid == 0) {
-      C d = a[j][j];
-      if (!(d > (C)0)) { if (bad < 0) bad = j; d = (C)1; }
-      const C rd = crsqrt<C>(d);
-      a[j][j] = d * rd;   // sqrt(d)
-      rdj = rd;
+    const C rd = rdbuf[j & 1];
+    C u = (C)0;
+    if (sub == 0) u = a[r][j] * (rd * rd);
+    u = __shfl_sync(0xffffffffu, u, (tid & 31) & ~7);
+#pragma unroll
+    for (int m = 0; m < T / 8; ++m) {
+      const int c = sub + 8 * m;
+      if (c > j && r >= c) {
+        a[r][c] -= u * a[c][j];
+        if (r == j + 1 && c == j + 1) {
+          C d = a[r][c];
+          if (!(d > (C)0)) { if (bad < 0) bad = j + 1; d = (C)1; }
+          rdbuf[(j + 1) & 1] = crsqrt<C>(d);
+        }
+      }
+      if (r > j && c <= j) inv[r][c] -= u * inv[j][c];
+      else if (j > 0 && r == j - 1 && c <= r) inv[r][c] *= rd_prev;
     }
-    __syncthreads();
-    const C rd = rdj;
-    // column j of L and row j of X (X_jc, c <= j)
-    if (tid < T) {
-      if (tid > j) a[tid][j] *= rd;
-      if (tid <= j) inv[j][tid] *= rd;
-    }
-    __syncthreads();
-    // trailing update of A (c > j, r >= c) and of the rows of X below j (r > j, c <= j)
-    for (int t = tid; t < TT; t += blockDim.x) {
-      const int r = t / T, c = t % T;
-      if (c > j && r >= c) a[r][c] -= a[r][j] * a[c][j];
-      else if (r > j && c <= j) inv[r][c] -= a[r][j] * inv[j][c];
-    }
+    rd_prev = rd;
     __syncthreads();
   }
+  for (int c = tid; c < T; c += blockDim.x) inv[T - 1][c] *= rd_prev;
+  __syncthreads();
   for (int t = tid; t < TT; t += blockDim.x) tile[t] = (S)inv[t / T][t % T];
   if (tid == 0 && bad >= 0) {
     // record the first failure: subdomain and pivot row
@@ -142,7 +154,9 @@ __global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, 
   }
 }
 
-// panel: L_IK = A_IK inv(L_KK)^T
+// panel: L_IK = A_IK inv(L_KK)^T, entry (r, c) = sum_{m <= c} A_rm X_cm (X = inv(L_KK), lower triangular).
+// Lane = row r; warp w computes columns w, w + 8, w + 16, w + 24, so the triangular loop length is the same
+// across a warp (no idle lanes) and the four columns of a warp balance the warps' work.
 template <typename S>
 __global__ void __launch_bounds__(256) k_chol_panel(EnvDev E, S* __restrict__ L, int K, const int* __restrict__ tasks) {
   using C = typename Compute<S>::type;
@@ -156,12 +170,19 @@ __global__ void __launch_bounds__(256) k_chol_panel(EnvDev E, S* __restrict__ L,
     A[t / T][t % T] = (C)P[t];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < TT; t += blockDim.x) {
-    int r = t / T, c = t % T;
-    C acc = (C)0;
-    for (int m = 0; m <= c; ++m) acc += A[r][m] * inv[c][m];
-    P[t] = (S)acc;
+  const int r = threadIdx.x & 31, w = threadIdx.x >> 5;
+  C acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = w + 8 * u;
+    acc[u] = (C)0;
+    for (int m = 0; m <= c; ++m) acc[u] += A[r][m] * inv[c][m];
   }
+  __syncthreads();   // every warp is done reading A: stage the result there for a coalesced store
+#pragma unroll
+  for (int u = 0; u < 4; ++u) A[r][w + 8 * u] = acc[u];
+  __syncthreads();
+  for (int t = threadIdx.x; t < TT; t += blockDim.x) P[t] = (S)A[t / T][t % T];
 }
 
 // trailing update: A_IJ -= L_IK L_JK^T

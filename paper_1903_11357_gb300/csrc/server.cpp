@@ -113,6 +113,8 @@ void dgasm_server_s::run() {
     std::vector<Request*> ok;
     for (Request* r : admitted) {
       int rc = prec_build(r->pc.get());
+      // the same local-solve variant a solve of this problem alone would take (measured once per shape)
+      if (rc >= 0) rc = tune_local_variant(r->pc.get(), r->nrhs, r->b, stream);
       if (rc < 0) {
         std::lock_guard<std::mutex> lk(mu);
         finish_request(r, rc, "setup failed");

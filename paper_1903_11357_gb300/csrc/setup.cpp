@@ -362,10 +362,109 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
   return DGASM_OK;
 }
 
+namespace dgasm {
+
+// explicit inverses: at most this many dofs per subdomain and this many bytes in all
+constexpr int DLI_MAX_N = 2048;
+constexpr size_t DLI_MAX_BYTES = size_t(1) << 30;
+constexpr int DLI_CB = 64;   // unit vectors per pass of the local-solve kernel
+
+bool dli_candidate(const dgasm_prec_s& pc) {
+  if (pc.blocks || pc.P.nsub < 1) return false;
+  const size_t eb = pc.precision == DGASM_FP64 ? 8 : 4;
+  size_t bytes = 0;
+  for (int s = 0; s < pc.P.nsub; ++s) {
+    const size_t n = (size_t)pc.P.env.ndof[s];
+    if (n > (size_t)DLI_MAX_N) return false;
+    bytes += n * n * eb;
+  }
+  return bytes <= DLI_MAX_BYTES;
+}
+
+// X_s = A_s^{-1} for every subdomain: the local-solve kernel (the sweeps with the envelope factors, in the
+// factor precision) applied to DLI_CB unit vectors per subdomain at a time, each result column stored into X_s
+int build_dli(dgasm_prec_s* pc) {
+  if (pc->dli.ptr) return DGASM_OK;
+  if (!dli_candidate(*pc)) return set_error(DGASM_EINVAL, "explicit local inverses: subdomains too large (at most %d "
+                                                          "dofs each and %zu bytes in all)", DLI_MAX_N, DLI_MAX_BYTES);
+  const Plan& P = pc->P;
+  const int nsub = P.nsub, np = P.np;
+  const long long ndof = (long long)P.ne * np;
+  const bool fp64 = pc->precision == DGASM_FP64;
+  const size_t eb = fp64 ? 8 : 4;
+  cudaStream_t st = pc->stream;
+  std::vector<long long> off(nsub + 1, 0);
+  std::vector<int> items;
+  int nmax = 0;
+  for (int s = 0; s < nsub; ++s) {
+    const int n = P.env.ndof[s];
+    nmax = std::max(nmax, n);
+    off[s + 1] = off[s] + (long long)n * n;
+    for (int r0 = 0; r0 < n; r0 += DLI_ROWS) { items.push_back(s); items.push_back(r0); }
+  }
+  DevBuf X, offs, item, r, z, misc, probs, prefix;
+  DG_TRY(X.alloc((size_t)off[nsub] * eb));
+  DG_TRY(upload(offs, off));
+  DG_TRY(upload(item, items));
+  DG_TRY(r.alloc(sizeof(double) * (size_t)DLI_CB * ndof));
+  DG_TRY(z.alloc(sizeof(double) * (size_t)DLI_CB * ndof));
+  // done flags [DLI_CB], error word, partial (r, z) [nsub][DLI_CB]
+  const size_t rz_off = (sizeof(int) * (DLI_CB + 2) + 15) & ~(size_t)15;
+  DG_TRY(misc.alloc(rz_off + sizeof(double) * (size_t)nsub * DLI_CB));
+  DG_CUDA(cudaMemsetAsync(misc.ptr, 0, misc.bytes, st));
+  const int chunks = DLI_CB / KC;
+  ProbDev D;
+  std::memset(&D, 0, sizeof(D));
+  D.ne = P.ne; D.np = np; D.np2s = pc->sys->np2s; D.ndof = (int)ndof; D.nsub = nsub; D.k = DLI_CB; D.kc = KC;
+  D.n_rhs_chunks = chunks; D.prec = pc->precision;
+  D.sub_e0 = pc->sub_e0.as<int>(); D.sub_trow = pc->env.sub_trow.as<int>(); D.trow_F = pc->env.trow_F.as<int>();
+  D.trow_ptr = pc->env.trow_ptr.as<long long>(); D.fwd_ptr = pc->env.fwd_ptr.as<long long>();
+  D.bwd_ptr = pc->env.bwd_ptr.as<long long>();
+  D.sr = P.env.sr;
+  D.sub_sr = pc->env.sub_sr.as<int>(); D.fwd_run = pc->env.fwd_run.as<int>(); D.bwd_run = pc->env.bwd_run.as<int>();
+  D.Lr = pc->Lr.ptr; D.Lc = pc->Lc.ptr; D.scale = pc->scale.as<double>();
+  D.fwd_total = (long long)P.env.fwd_src.size();
+  D.bwd_total = (long long)P.env.bwd_src.size();
+  D.r = r.as<double>(); D.z = z.as<double>();
+  D.done = (int*)misc.ptr;
+  D.part_rz = (double*)((char*)misc.ptr + rz_off);
+  DG_TRY(probs.alloc(sizeof(ProbDev)));
+  DG_CUDA(cudaMemcpyAsync(probs.ptr, &D, sizeof(ProbDev), cudaMemcpyHostToDevice, st));
+  std::vector<int> pre{0, nsub * chunks};
+  DG_TRY(upload(prefix, pre));
+  BatchDev B;
+  std::memset(&B, 0, sizeof(B));
+  B.probs = probs.as<ProbDev>();
+  B.nprob = 1;
+  B.err = (int*)misc.ptr + DLI_CB;
+  const int slot = K_NKINDS + 2 * pc->precision + 1;
+  B.prefix[slot] = prefix.as<int>();
+  for (int c0 = 0; c0 < nmax; c0 += DLI_CB) {
+    DG_CUDA(cudaMemsetAsync(r.ptr, 0, r.bytes, st));
+    DG_CUDA(launch_unit_block(pc->sub_e0.as<int>(), nsub, np, c0, DLI_CB, ndof, r.as<double>(), st));
+    DG_CUDA(launch_local(B, slot, nsub * chunks, local_smem_bytes(pc->precision, nmax, KC), st));
+    DG_CUDA(launch_dli_store(fp64 ? 1 : 0, pc->sub_e0.as<int>(), nsub, np, offs.as<long long>(), c0, DLI_CB, ndof,
+                             z.as<double>(), X.ptr, nmax, st));
+  }
+  int herr = 0;
+  DG_CUDA(cudaMemcpyAsync(&herr, B.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (herr) return set_error(DGASM_ECUDA, "a bounded wait while forming the explicit local inverses gave up");
+  pc->dli = std::move(X);
+  pc->dli_off = std::move(offs);
+  pc->dli_item = std::move(item);
+  pc->n_dli_items = (int)(items.size() / 2);
+  pc->dli_nmax = nmax;
+  return DGASM_OK;
+}
+
+}  // namespace dgasm
+
 size_t dgasm_prec_s::footprint() const {
   size_t b = perm.bytes + rowptr.bytes + col.bytes + vals.bytes + sub_e0.bytes + scale.bytes + Lr.bytes + Lc.bytes +
              grp_ptr.bytes + grp_elems.bytes + agg_int.bytes + r0t.bytes + A0inv.bytes + err.bytes + dinv.bytes +
-             r0t_ptr.bytes + r0t_col.bytes + r0t_elem.bytes + rT_ptr.bytes + rT_pair.bytes;
+             r0t_ptr.bytes + r0t_col.bytes + r0t_elem.bytes + rT_ptr.bytes + rT_pair.bytes + dli.bytes + dli_off.bytes +
+             dli_item.bytes;
   const EnvBufs* es[2] = {&env, &env0};
   for (const EnvBufs* e : es)
     b += e->ndof.bytes + e->sub_trow.bytes + e->trow_F.bytes + e->trow_ptr.bytes + e->diag_task.bytes +

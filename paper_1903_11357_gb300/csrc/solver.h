@@ -26,6 +26,7 @@ struct Workspace {
   DevBuf buf;
   int k = 0, maxit = 0;
   int n_chunk_items = 0, n_spmv_items = 0, n_coarse_items = 0;
+  int n_rz_cap = 0;   // partial (r, z) sums the buffer holds per right-hand side
   // per right-hand side: iterations of the first CG run when a residual replacement restarted it (-1:
   // none); kept with the problem, so it survives the engine being rebuilt for other batches
   std::vector<int> lanczos_len;
@@ -91,6 +92,13 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit);
 int prec_build(dgasm_prec_s* pc);
 // times one preconditioner application of b with each right-hand-side chunking and keeps the faster
 int tune_rhs_chunk(dgasm_prec_s* pc, int nrhs, const double* b, cudaStream_t stream);
+// local-solve variants: 1 = forward/backward sweeps with the envelope factors, 2 = explicit inverses
+enum LocalVariant { LV_TUNE = 0, LV_SWEEPS = 1, LV_INVERSE = 2 };
+bool dli_candidate(const dgasm_prec_s& pc);   // explicit inverses small enough to form and keep
+int build_dli(dgasm_prec_s* pc);              // forms them (once)
+// times the local-solve variants on b (when the preconditioner is a candidate and not yet tuned) and keeps
+// the faster; the caller holds pc->mu
+int tune_local_variant(dgasm_prec_s* pc, int nrhs, const double* b, cudaStream_t stream);
 // z = B r (the caller holds pc->mu)
 int apply_locked(dgasm_prec_s* pc, int nrhs, const double* r, double* z, cudaStream_t stream);
 
@@ -113,6 +121,9 @@ struct dgasm_prec_s {
   // KC, tuned by the first dgasm_solve with k > 1), else 1 or KC
   int rhs_chunk[dgasm::KMAX + 1] = {0};
   bool blocks = false;      // every subdomain is one element: local solves with explicit block inverses
+  int local_variant = dgasm::LV_TUNE;   // envelope problems: sweeps or explicit inverses (LocalVariant)
+  dgasm::DevBuf dli, dli_off, dli_item;  // explicit inverses, their offsets and the item table
+  int n_dli_items = 0, dli_nmax = 0;
   dgasm::DevBuf dinv;       // [ne][np][np] FP64, internal element order
   dgasm::EnvBufs env, env0;
   dgasm::Workspace ws;

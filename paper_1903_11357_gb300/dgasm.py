@@ -20,6 +20,9 @@ FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
 
 RHS_FN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+# device allocator hooks of dgasm_set_allocator: alloc(bytes, stream, user) -> pointer, free(ptr, stream, user)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 
 class SetupOpts(C.Structure):
@@ -93,6 +96,8 @@ def lib():
             "dgasm_nonnested_prolongation": [vp, vp, C.c_int, C.c_int, i64p, ip, ip, dp],
             "dgasm_selftest_plan": [vp, C.c_int, i64p, i64p],
             "dgasm_prec_get_rhs_chunk": [vp, C.c_int, ip],
+            "dgasm_prec_set_local_variant": [vp, C.c_int],
+            "dgasm_prec_get_local_variant": [vp, ip],
             "dgasm_prec_destroy": [vp],
             "dgasm_solve": [vp, C.c_int, vp, vp, C.POINTER(SolveOpts), C.POINTER(Stats)],
             "dgasm_solve_batch": [C.c_int, C.POINTER(vp), ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveOpts),
@@ -262,6 +267,17 @@ class System:
             raise ValueError("spmv takes one vector")
         check(lib().dgasm_system_spmv(self.h, _dev_ptr(x), _dev_ptr(y), _stream_ptr(stream)))
 
+    def spmv_dot_noalloc(self, x, y, out, stream=None):
+        """y = A x and out[0] = x^T A x with no device allocation (dgasm_system_spmv_dot_noalloc; asynchronous
+        on the stream).  The matrix must already be on the device (spmv or a Prec uploads it)."""
+        import torch
+        if _nvec(self.ndof, x, y) != 1 or x.dim() != 1:
+            raise ValueError("spmv_dot_noalloc takes one vector")
+        if not (isinstance(out, torch.Tensor) and out.numel() >= 1):
+            raise ValueError("out must hold at least one double")
+        check(lib().dgasm_system_spmv_dot_noalloc(self.h, _dev_ptr(x), _dev_ptr(y), _dev_ptr(out),
+                                                  _stream_ptr(stream)))
+
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.dgasm_system_destroy(self.h)
@@ -301,6 +317,19 @@ class Prec:
         v = C.c_int()
         check(lib().dgasm_prec_get_rhs_chunk(self.h, int(nrhs), C.byref(v)))
         return v.value
+
+    LOCAL_VARIANTS = {"tune": 0, "sweeps": 1, "inverse": 2}
+
+    def set_local_variant(self, variant):
+        """Local solves by the envelope sweeps ("sweeps"), by explicit subdomain inverses ("inverse", small
+        subdomains only), or "tune" to let the first solve measure both (dgasm_prec_set_local_variant)."""
+        v = self.LOCAL_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        check(lib().dgasm_prec_set_local_variant(self.h, v))
+
+    def local_variant(self):
+        v = C.c_int()
+        check(lib().dgasm_prec_get_local_variant(self.h, C.byref(v)))
+        return {0: "tune", 1: "sweeps", 2: "inverse"}[v.value]
 
     def apply(self, r, z, stream=None):
         k = _nvec(self.ndof, r, z)
@@ -422,7 +451,7 @@ def profile_enable(on=True, kinds=None):
     if not on:
         mask = 0
     elif kinds is None:
-        mask = 0xFF
+        mask = (1 << len(PROFILE_KINDS)) - 1
     else:
         mask = 0
         for k in kinds:
