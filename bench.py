@@ -34,12 +34,9 @@ N_ELEM, SEED, P_DEG, NSUB, NCOARSE, P_C, CONTRAST = 16384, 2, 3, 64, 256, 1, 1e4
 WORKLOAD = ("16384 Lloyd-relaxed Voronoi cells of (0,1)^2 (seed 2, 20 Lloyd steps), SIPG p=3 (163840 dofs), "
             "C_sigma=10, 64 RCB subdomains (~2560 dofs), 256 RCB agglomerates at p_c=1, rho=1e4 on a 4x4 "
             "checkerboard of subdomains; f = 2 pi^2 sin(pi x) sin(pi y); rtol 1e-8 from x0=0")
-# PCG iterations to 1e-8 on the headline workload: the library's FP64 solve takes 293, and the parity tests hold
-# the oracle's count to within one of the library's; too many to run the oracle to convergence in a bench step
-REF_ITERS = 293
 FP64_PEAK_FLOPS_PER_CLK = 152 * 2 * 2   # 152 SMs x 2 DFMA/clk (measured issue rate) x 2 flop
 # DRAM bytes (read + write) per stream tile of the FP64 local-solve kernel, from one ncu capture of the
-# 4096-cell case (profiles/local_solve_fp64_4096cells_p3.md); valid only for the kernel source it was taken on
+# 4096-cell case; valid only for the kernel source it was taken on
 LOCAL_TRAFFIC = {"sha256": "dd12d7c7069094093c9801a4ad85cb01dfb5fe167d8c84b1fbf30787c96a9b65",
                  "bytes_per_stream_tile": 8453}
 
@@ -120,6 +117,13 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def oracle_iters():
+    """The oracle's own PCG iteration count to 1e-8 on the headline workload, from its stored converged solve
+    (tests/golden, written by a script that calls only the oracle)."""
+    from tests.golden.make_oracle_solutions import load
+    return int(load("p3_c1e4")["iters"])
+
+
 def oracle_prep(m, rho):
     """Untimed preparation for the CPU baseline: the oracle's SIPG assembly and partitions, and the full
     coarse transfer (needed by the sampled PCG iterations)."""
@@ -135,11 +139,11 @@ def oracle_prep(m, rho):
             "R0T": R0T}
 
 
-def oracle_sample(prep, gpu_iters, sample_subdomains=4, sample_elems=1024, sample_iters=3):
-    """The CPU oracle timed on a bounded sample of the workload, scaled to one solve:
-    local Cholesky of `sample_subdomains` of the 64 subdomain matrices (x 64 / sample), the L2
-    prolongation on the first `sample_elems` elements (x ne / sample), the Galerkin product A_0 and its
-    Cholesky (full), and `sample_iters` PCG iterations (x the GPU's iteration count)."""
+def oracle_sample(prep, iters, sample_subdomains=4, sample_elems=1024, sample_iters=10):
+    """The CPU oracle timed on a bounded sample of the workload, scaled to one solve.  Setup: the dense
+    Cholesky of `sample_subdomains` of the 64 subdomain matrices (x 64 / sample), the L2 prolongation on the
+    first `sample_elems` elements (x ne / sample), the Galerkin product A_0 and its Cholesky (measured in
+    full).  Solve: `sample_iters` PCG iterations (x iters / sample_iters, iters = the oracle's own count)."""
     from oracle import pcg, schwarz
     from synth.voronoi import PolyMesh
     A, b, m, g, agg, dofs, R0T = (prep[k] for k in ("A", "b", "m", "g", "agg", "dofs", "R0T"))
@@ -162,15 +166,54 @@ def oracle_sample(prep, gpu_iters, sample_subdomains=4, sample_elems=1024, sampl
     t0 = time.perf_counter()
     pcg.pcg(A, b, S.apply, fixed_iters=sample_iters)
     t_iter = (time.perf_counter() - t0) / sample_iters
-    t_solve = t_local + t_r0t + t_a0 + t_iter * gpu_iters
+    t_setup = t_local + t_r0t + t_a0
+    t_solve = t_iter * iters
+    return {"setup_s": t_setup, "solve_s": t_solve, "seconds_per_solve": t_setup + t_solve,
+            "measured": f"A_0 product and Cholesky in full; {sample_subdomains}/{NSUB} subdomain Cholesky "
+                        f"factorisations, {sample_elems}/{ne} elements of the prolongation, {sample_iters} PCG "
+                        f"iterations",
+            "extrapolated": f"subdomain factorisations x{NSUB / sample_subdomains:g}, prolongation "
+                            f"x{ne / sample_elems:g}, PCG iterations x{iters / sample_iters:g} to the oracle's own "
+                            f"{iters} iterations; SIPG assembly untimed"}
+
+
+def cpu_worker(args):
+    """Runs oracle_sample on a pickled preparation (bench.py --cpu-worker FILE) and prints its JSON; started
+    as a fresh process so that the BLAS thread count set in its environment holds from the first import."""
+    import pickle
+    with open(args.cpu_worker, "rb") as f:
+        prep, iters = pickle.load(f)
+    print(json.dumps(oracle_sample(prep, iters)), flush=True)
+
+
+def cpu_baseline(m, rho):
+    """The oracle on this host at all cores (BLAS default) and at one thread, setup and solve separately."""
+    import pickle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "seconds_per_solve": t_solve,
-            "sample": (f"numpy/scipy oracle on this workload, scaled to one solve: dense Cholesky of "
-                       f"{sample_subdomains}/{NSUB} subdomain matrices (x{NSUB / sample_subdomains:g}), L2 prolongation "
-                       f"of {sample_elems}/{ne} elements (x{ne / sample_elems:g}), full A_0 product and Cholesky, "
-                       f"{sample_iters} PCG iterations (x{gpu_iters / sample_iters:g} for the {gpu_iters} of one solve); "
-                       f"assembly untimed; BLAS threads = library default on {cores} cores")}
+    iters = oracle_iters()
+    prep = oracle_prep(m, rho)
+    allc = oracle_sample(prep, iters)
+    one = None
+    with tempfile.NamedTemporaryFile(suffix=".pkl", delete=False) as f:
+        pickle.dump((prep, iters), f)
+        path = f.name
+    try:
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", path], env=env,
+                           capture_output=True, text=True, timeout=900)
+        for line in r.stdout.splitlines():
+            if line.startswith("{"):
+                one = json.loads(line)
+    finally:
+        os.unlink(path)
+    out = {"value": 1.0 / allc["seconds_per_solve"], "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "sample": ("numpy/scipy FP64 oracle on this workload, one solve (setup + solve) extrapolated from a sample: "
+                      + allc["measured"] + " measured; " + allc["extrapolated"] + "; BLAS threads = all cores"),
+           "setup_s": allc["setup_s"], "solve_s": allc["solve_s"], "oracle_iters": iters}
+    if one:
+        out["one_thread"] = {"value": 1.0 / one["seconds_per_solve"], "setup_s": one["setup_s"],
+                             "solve_s": one["solve_s"], "cores": 1}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -185,19 +228,24 @@ def run_reference(args, rank, world):
     sub = partition.subdomains(g.centroid, NSUB)
     rho = checker_per_subdomain(m, sub, CONTRAST)
     prep = oracle_prep(m, rho)
+    iters = oracle_iters()
     vals = []
     last = None
     for step in range(args.warmup + args.steps):
-        last = oracle_sample(prep, args.ref_iters, sample_subdomains=2, sample_elems=256, sample_iters=1)
+        last = oracle_sample(prep, iters, sample_subdomains=2, sample_elems=256, sample_iters=1)
         if step >= args.warmup:
             vals.append(last["seconds_per_solve"])
     t = statistics.mean(vals)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = ("numpy/scipy FP64 oracle, one solve per step extrapolated from a sample: " + last["measured"] +
+              " measured; " + last["extrapolated"] + "; BLAS threads = all cores")
     out = {"impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "solver": "CPU oracle (numpy/scipy FP64)"},
-           "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": last["cores"], "kind": "oracle",
-                            "sample": last["sample"]},
+           "config": {"workload": WORKLOAD, "precision": "fp64 (plain FP64 ASPCG)", "parallelism": f"replicas x{world}",
+                      "solver": "CPU oracle (numpy/scipy FP64)"},
+           "cpu_baseline": {"value": 1.0 / t, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+                            "setup_s": last["setup_s"], "solve_s": last["solve_s"], "oracle_iters": iters},
            "e2e": {"value": 1.0 / t, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -216,17 +264,17 @@ def _systems(specs, meshes, dg, torch, rhs_seed_offset=1):
     return out
 
 
-def run_batch(args):
+def batch_measure(steps, warmup):
     """48 independent problems (element counts log-uniform in 1024..16384, p in 1..4, N/256 subdomains,
-    N/64 agglomerates at p_c=1): setup of all 48 preconditioners with FP32 local factors and one batched
-    solve of all of them (FP64 outer PCG, one launch per kernel kind and iteration for the whole batch,
-    CUDA graphs), against the plain FP64 library mode, one problem at a time."""
+    N/64 agglomerates at p_c=1): setup of all 48 preconditioners and one batched solve of all of them (FP64
+    outer PCG; per iteration one persistent vector launch and one local-solve launch per kind for the whole
+    batch, CUDA graphs), with FP32 / BF16 / FP64 local factors, against the plain FP64 library mode, one
+    problem at a time (setup + solve each)."""
     from synth.workloads import build_meshes, problem_specs
     specs = problem_specs(48, 4)
     meshes = build_meshes(specs)
     import torch
     from paper_1903_11357_gb300 import dgasm as dg
-    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     probs = _systems(specs, meshes, dg, torch)
     nrhs = len(probs)
@@ -262,51 +310,66 @@ def run_batch(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1000.0 / steps, out
 
-    sampler = ClockSampler(0)
-    t_mix, (_, x_mix, st_mix) = timed(lambda: batched("fp32"), args.steps, args.warmup)
-    clocks = sampler.stop()
-    t_bf, (_, x_bf, st_bf) = timed(lambda: batched("bf16"), args.steps, 1)
-    t_b64, (_, x_b64, st_b64) = timed(lambda: batched("fp64"), args.steps, 1)
-    t_plain, (x_64, st_64) = timed(plain, args.steps, 1)
+    t_mix, (precs_mix, x_mix, st_mix) = timed(lambda: batched("fp32"), steps, warmup)
+    variants = {}
+    for P in precs_mix:
+        v = P.local_variant()
+        variants[v] = variants.get(v, 0) + 1
+    t_bf, (_, x_bf, st_bf) = timed(lambda: batched("bf16"), steps, 1)
+    t_b64, (_, x_b64, st_b64) = timed(lambda: batched("fp64"), steps, 1)
+    t_plain, (x_64, st_64) = timed(plain, steps, 1)
     rel = lambda xa: max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(xa, x_64))
     it = lambda sts: [int(s["iters"]) for s in sts]
+    return {
+        "problems": nrhs, "total_dofs": int(sum(S.ndof for _, S, _ in probs)),
+        "fp32_batched": {"solves_per_s": nrhs / t_mix, "ms_per_step": 1000.0 * t_mix,
+                         "max_rel_diff_vs_fp64": rel(x_mix), "iters_sum": sum(it(st_mix)),
+                         "max_true_relres": max(float(s["true_relres"]) for s in st_mix)},
+        "bf16_batched": {"solves_per_s": nrhs / t_bf, "ms_per_step": 1000.0 * t_bf,
+                         "max_rel_diff_vs_fp64": rel(x_bf), "iters_sum": sum(it(st_bf)),
+                         "max_true_relres": max(float(s["true_relres"]) for s in st_bf)},
+        "fp64_batched": {"solves_per_s": nrhs / t_b64, "ms_per_step": 1000.0 * t_b64, "iters_sum": sum(it(st_b64))},
+        "fp64_plain": {"solves_per_s": nrhs / t_plain, "ms_per_step": 1000.0 * t_plain, "iters_sum": sum(it(st_64)),
+                       "what": "FP64 local factors, one problem at a time (setup + solve each)"},
+        "speedup_mixed_batched_vs_fp64_plain": t_plain / t_mix,
+        "local_variant_counts_fp32": variants,
+        "iters_fp32_minus_fp64_max": max(a - c for a, c in zip(it(st_mix), it(st_64))),
+    }
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    r = batch_measure(args.steps, args.warmup)
+    clocks = sampler.stop()
+    t_mix = r["fp32_batched"]["ms_per_step"] / 1000.0
     out = {
-        "metric": METRIC, "value": nrhs / t_mix, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": r["problems"] / t_mix, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_mix, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 outer / f32 local", "data": "synthetic",
         "config": {"workload": "batch of 48 problems: Voronoi meshes (rng 4) with 1024..16384 cells log-uniform, "
                                "p in {1..4}, N/256 RCB subdomains, N/64 agglomerates at p_c=1, rho per subdomain "
                                "log-uniform in [1,1e3], rhs N(0,1) per dof, rtol 1e-8",
-                   "total_dofs": int(sum(S.ndof for _, S, _ in probs)),
-                   "step": "setup of 48 preconditioners + one batched solve of all 48"},
-        "fp64_plain": {"solves_per_s": nrhs / t_plain, "ms_per_step": 1000.0 * t_plain,
-                       "what": "FP64 local factors, one problem at a time (setup + solve each)"},
-        "fp64_batched": {"solves_per_s": nrhs / t_b64, "ms_per_step": 1000.0 * t_b64},
-        "bf16_batched": {"solves_per_s": nrhs / t_bf, "ms_per_step": 1000.0 * t_bf,
-                         "max_rel_diff_vs_fp64": rel(x_bf), "iters_sum": sum(it(st_bf))},
-        "speedup_mixed_batched_vs_fp64_plain": t_plain / t_mix,
-        "max_rel_diff_mixed_vs_fp64": rel(x_mix),
-        "max_true_relres_mixed": max(float(s["true_relres"]) for s in st_mix),
-        "iters_sum": {"fp32": sum(it(st_mix)), "fp64": sum(it(st_64))},
-        "iters_fp32_minus_fp64_max": max(a - c for a, c in zip(it(st_mix), it(st_64))),
-        "clocks": clocks,
+                   "total_dofs": r["total_dofs"], "step": "setup of 48 preconditioners + one batched solve of all 48"},
+        "batch": r, "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
 
 
-def run_serve(args):
+def serve_measure(n_req, fracs):
     """Poisson arrivals of solve requests (problem drawn from a pool of 16 problems shaped like the batch
     mix, 1..8 N(0,1) right-hand sides each) into the continuous-batching server; latency from arrival to
-    completion, p50 / p99, and right-hand sides completed per second, per arrival rate and precision."""
+    completion, p50 / p99, and right-hand sides completed per second.  Per precision (FP32 local factors,
+    and plain FP64): the saturation rate (all requests at once), then Poisson arrivals at each fraction
+    of it; fracs: {precision: [fractions]}."""
     from synth.workloads import build_meshes, problem_specs
     specs = problem_specs(16, 5)
     meshes = build_meshes(specs)
     import torch
     from paper_1903_11357_gb300 import dgasm as dg
-    torch.cuda.set_device(0)
     pool = _systems(specs, meshes, dg, torch)
     rng = np.random.default_rng(5)
-    n_req = max(16, args.requests)
 
     def make_request():
         s, S, _ = pool[int(rng.integers(len(pool)))]
@@ -348,20 +411,28 @@ def run_serve(args):
                 "p50_ms": 1000 * lat[len(lat) // 2], "p99_ms": 1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                 "mean_ms": 1000 * sum(lat) / len(lat), "rounds": stats["rounds"], "stalls": stats["stalls"]}
 
-    sampler = ClockSampler(0)
     res = {}
-    for precision in ("fp32", "fp64"):
+    for precision, fr in fracs.items():
         run(precision, [0.0] * 4)   # warm-up
         sat = run(precision, [0.0] * n_req)   # everything at once: saturation throughput
         rows = {"saturation_closed_batch": sat}
-        for frac in (0.5, 0.9):
+        for frac in fr:
             lam = frac * sat["rhs_per_s"] / 4.5   # requests/s: 4.5 right-hand sides per request on average
             gaps = np.random.default_rng(int(frac * 100)).exponential(1.0 / lam, size=n_req)
             arrivals = list(np.cumsum(gaps) - gaps[0])
-            rows[f"poisson_{frac:.1f}x_saturation"] = dict(run(precision, arrivals), rate_req_per_s=lam)
+            rows[f"poisson_{frac:.2f}x_saturation"] = dict(run(precision, arrivals), rate_req_per_s=lam)
         res[precision] = rows
+    return res
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    n_req = max(16, args.requests)
+    sampler = ClockSampler(0)
+    res = serve_measure(n_req, {"fp32": (0.5, 0.9), "fp64": (0.5, 0.9)})
     clocks = sampler.stop()
-    mixed = res["fp32"]["poisson_0.9x_saturation"]
+    mixed = res["fp32"]["poisson_0.90x_saturation"]
     out = {
         "metric": METRIC, "value": res["fp32"]["saturation_closed_batch"]["rhs_per_s"], "unit": "solves/s",
         "n_gpus": 1, "steps": n_req, "warmup": 4, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
@@ -377,26 +448,35 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
-def run_sweep(args):
+SWEEP_FIXTURE = {1.0: "p4_c1", 1e2: "p4_c1e2", 1e4: "p4_c1e4", 1e6: "p4_c1e6"}
+
+
+def sweep_measure(contrasts=(1.0, 1e2, 1e4, 1e6), precisions=("fp64", "fp32", "tf32", "bf16"), timed_reps=2):
     """Precision / contrast sweep: the 16384-cell mesh at p = 4 (245760 dofs, 64 subdomains, 256
     agglomerates), checkerboard contrast 1, 1e2, 1e4, 1e6; local factors in FP64, FP32, TF32, BF16 (FP64
-    outer PCG, residual and coarse solve).  Per case: iterations, true relative residual, relative
-    difference to the FP64 solution of the same case, and time to 1e-8 (setup + solve)."""
+    outer PCG, residual and coarse solve).  Per case: iterations, true relative residual, time to 1e-8
+    (setup + solve; the last of timed_reps solves), relative difference to the library's FP64 solution, and,
+    where the oracle's converged FP64 solve of the case is stored (tests/golden, written by a script that calls
+    only the oracle), the oracle's iteration count and the error against the oracle's solution at its 1000
+    sampled dofs (max |x - x_oracle| / max |x_oracle|)."""
     from synth.coeff import checker_per_subdomain
     from synth.voronoi import voronoi_mesh
     import torch
     from paper_1903_11357_gb300 import dgasm as dg
-    torch.cuda.set_device(0)
+    from tests.golden.make_oracle_solutions import load as load_oracle_solve, path_of
     stream = torch.cuda.current_stream()
     m = voronoi_mesh(N_ELEM, SEED)
     sub, _ = dg.Mesh.from_polymesh(m, np.ones(m.n_elem)).partition(NSUB, 0)
     rows = []
-    for contrast in (1.0, 1e2, 1e4, 1e6):
-        S = dg.System(dg.Mesh.from_polymesh(m, checker_per_subdomain(m, sub, contrast)), 4, 10.0, f=f_sin)
+    for contrast in contrasts:
+        S = dg.System(dg.Mesh.from_polymesh(m, checker_per_subdomain(m, sub, contrast)), 4, 10.0, f=f_sin,
+                      device=True, stream=stream)
         b = torch.tensor(S.rhs(), dtype=torch.float64, device="cuda")
+        fx = SWEEP_FIXTURE.get(contrast)
+        oref = load_oracle_solve(fx) if fx and os.path.exists(path_of(fx)) else None
         ref = None
-        for precision in ("fp64", "fp32", "tf32", "bf16"):
-            for _ in range(2):   # the second solve is timed
+        for precision in precisions:
+            for _ in range(timed_reps):   # the last solve is timed
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 P = dg.Prec(S, NSUB, NCOARSE, P_C, precision=precision, stream=stream)
@@ -404,13 +484,25 @@ def run_sweep(args):
                 rc, st = P.solve(b, x, rtol=1e-8, maxit=20000, stream=stream)
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
+                del P
             if precision == "fp64":
                 ref = x.clone()
-            rows.append({"contrast": contrast, "precision": precision, "rc": rc, "iters": st[0]["iters"],
-                         "true_relres": st[0]["true_relres"], "kappa": st[0]["kappa"],
-                         "rel_diff_vs_fp64": float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref)),
-                         "ms": 1000 * dt})
-            del P
+            row = {"contrast": contrast, "precision": precision, "rc": rc, "iters": st[0]["iters"],
+                   "true_relres": st[0]["true_relres"], "kappa": st[0]["kappa"], "ms": 1000 * dt,
+                   "rel_diff_vs_fp64": float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref)) if ref is not None
+                   else None}
+            if oref is not None:
+                xs = x[torch.tensor(oref["idx"], device="cuda")].cpu().numpy()
+                row["oracle_iters"] = int(oref["iters"])
+                row["err_vs_oracle_sampled"] = float(np.abs(xs - oref["x"]).max() / np.abs(oref["x"]).max())
+            rows.append(row)
+    return rows
+
+
+def run_sweep(args):
+    import torch
+    torch.cuda.set_device(0)
+    rows = sweep_measure()
     t = {r["precision"]: r["ms"] for r in rows if r["contrast"] == 1e4}
     out = {"metric": METRIC, "value": 1000.0 / t["fp32"], "unit": "solves/s", "n_gpus": 1, "steps": 1,
            "warmup": 1, "ms_per_step": t["fp32"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -533,26 +625,35 @@ def main():
     ap.add_argument("--impl", default="dgasm", choices=["dgasm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=REF_ITERS,
-                    help="PCG iterations one solve of the headline workload takes (the reference arm scales its "
-                         "sampled iteration by this count)")
+    ap.add_argument("--quick", action="store_true", help="headline solve only: no precision sweep, batch or serving "
+                                                         "sections, no CPU baseline")
     ap.add_argument("--elems", type=int, default=N_ELEM, help="smaller workloads for profiling runs")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"],
+                    help="local-factor precision of the timed step (profiling runs; the headline is fp64)")
     ap.add_argument("--nsub", type=int, default=NSUB)
     ap.add_argument("--ncoarse", type=int, default=NCOARSE)
     ap.add_argument("--degree", type=int, default=P_DEG)
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "batch", "serve", "sweep", "paper"],
-                    help="cfg2: the headline solve (default); batch: 48-problem batch; serve: Poisson "
-                         "arrivals into the server; sweep: precision / contrast sweep at p=4; paper: the paper's "
-                         "setting (subdomains = elements) over fine and coarse mesh sizes")
-    ap.add_argument("--requests", type=int, default=48, help="requests per arrival rate (serve)")
+                    help="cfg2: the headline solve (default, with compact sweep / batch / serving sections); batch: "
+                         "48-problem batch; serve: Poisson arrivals into the server; sweep: precision / contrast "
+                         "sweep at p=4; paper: the paper's setting (subdomains = elements) over fine and coarse "
+                         "mesh sizes")
+    ap.add_argument("--requests", type=int, default=200, help="requests per arrival rate (serving)")
+    ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args)
+        return
     if args.workload != "cfg2":
         {"batch": run_batch, "serve": run_serve, "sweep": run_sweep, "paper": run_paper}[args.workload](args)
         return
+    if args.precision != "fp64":
+        args.quick = True
     if (args.elems, args.nsub, args.ncoarse, args.degree) != (N_ELEM, NSUB, NCOARSE, P_DEG):
         N_ELEM, NSUB, NCOARSE, P_DEG = args.elems, args.nsub, args.ncoarse, args.degree
         WORKLOAD = (f"profiling case: {N_ELEM} Lloyd-Voronoi cells, p={P_DEG}, {NSUB} subdomains, {NCOARSE} "
                     f"agglomerates at p_c=1, checkerboard 1e4 (not the headline workload)")
+        args.quick = True
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -586,7 +687,7 @@ def main():
         asm["device_ms" if dev_asm else "host_ms"] = 1000.0 * dt
     asm.update({"cells": N_ELEM, "p": P_DEG, "host_threads": os.cpu_count(), "what": "block matrix only (no load vector)"})
 
-    def step(precision="fp64", keep=None):
+    def step(precision=args.precision, keep=None):
         P = dg.Prec(S, NSUB, NCOARSE, P_C, precision=precision, stream=stream)
         x = torch.zeros_like(b)
         rc, st = P.solve(b, x, rtol=1e-8, stream=stream)
@@ -605,13 +706,11 @@ def main():
         assert rc == 0, rc
     del P, x
     # per-kernel breakdown: one untimed step with every kind bracketed by events
-    breakdown = profiled_step(dg, step, barrier, "fp64")
+    breakdown = profiled_step(dg, step, barrier, args.precision)
     dom = max(breakdown, key=lambda k: breakdown[k]["total_ms"])
-    # timed region: only the dominant kernel kind is bracketed by events (its roofline below)
+    # timed region: no instrumentation; every step's preconditioner is kept until the region ends
     keep = []
     sampler = ClockSampler(local_rank)
-    dg.profile_read(reset=True)
-    dg.profile_enable(True, kinds=[dom])
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -627,8 +726,6 @@ def main():
         assert rc == 0, rc
     ev1.record(stream)
     barrier()
-    dg.profile_enable(False)
-    prof = dg.profile_read(reset=True)
     clocks = sampler.stop()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
     t_max = slowest_rank_seconds(elapsed, world, device="cuda")
@@ -636,9 +733,20 @@ def main():
     info = keep[0][0].info()
     sts = [s for _, _, s in per_step]
     iters = sts[-1]["iters"]
-    launches = sum(info_i["setup_launches"] for info_i in [P_.info() for P_, _ in keep]) + sum(s["launches"] for s in sts)
+    launches = sum(P_.info()["setup_launches"] for P_, _ in keep) + sum(s["launches"] for s in sts)
     x_fp64 = keep[-1][1].clone()
     del keep
+    # the dominant kernel's launch times, in a separate pass of the same steps with only that kind bracketed
+    dg.profile_read(reset=True)
+    dg.profile_enable(True, kinds=[dom])
+    barrier()
+    for _ in range(min(args.steps, 3)):
+        rc, _, P, x = step()
+        assert rc == 0, rc
+    barrier()
+    dg.profile_enable(False)
+    prof = dg.profile_read(reset=True)
+    del P, x
 
     # end to end through the C-ABI with host buffers (b copied in, x copied out inside the call), both in
     # pinned host memory allocated before the timed region
@@ -647,7 +755,7 @@ def main():
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        Pe = dg.Prec(S, NSUB, NCOARSE, P_C, precision="fp64", stream=stream)
+        Pe = dg.Prec(S, NSUB, NCOARSE, P_C, precision=args.precision, stream=stream)
         rc, _ = Pe.solve(b_pin, x_pin, rtol=1e-8, stream=stream, host_buffers=True)
         assert rc == 0
         del Pe
@@ -698,12 +806,69 @@ def main():
         res["tuned_kc"] = Px.rhs_chunk(8)
         return res
 
-    tuning = rhs_chunk_tuning() if rank == 0 else None
+    def local_variant_tuning():
+        """The small configuration (256 cells, p = 2, 4 subdomains of ~384 dofs, 16 agglomerates): local solves
+        by the envelope sweeps and by explicit subdomain inverses, each timed (setup excluded, median of 5
+        solves), and the tuner's pick."""
+        from synth.voronoi import voronoi_mesh
+        mm = voronoi_mesh(256, 1)
+        Sx = dg.System(dg.Mesh.from_polymesh(mm, np.ones(mm.n_elem)), 2, 10.0, f=f_sin)
+        bx = torch.tensor(Sx.rhs(), dtype=torch.float64, device="cuda")
+        res = {"case": "256 cells (seed 1), p=2, 4 subdomains, 16 agglomerates at p_c=1, FP64, rtol 1e-8"}
+        for variant in ("sweeps", "inverse"):
+            Px = dg.Prec(Sx, 4, 16, P_C, stream=stream)
+            Px.set_local_variant(variant)
+            ts = []
+            for _ in range(6):
+                xx = torch.zeros_like(bx)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, stx = Px.solve(bx, xx, rtol=1e-8, stream=stream)
+                torch.cuda.synchronize()
+                ts.append(1000.0 * (time.perf_counter() - t0))
+            res[f"solve_ms_{variant}"] = statistics.median(ts[1:])
+            res[f"iters_{variant}"] = stx[0]["iters"]
+        Px = dg.Prec(Sx, 4, 16, P_C, stream=stream)
+        Px.solve(bx, torch.zeros_like(bx), rtol=1e-8, stream=stream)
+        res["tuned"] = Px.local_variant()
+        return res
 
-    mixed = mixed_tf32 = None
+    tuning = rhs_chunk_tuning() if rank == 0 else None
+    variant_tuning = local_variant_tuning() if rank == 0 else None
+
+    mixed = mixed_tf32 = mixed_bf16 = None
     if not args.no_mixed:
         mixed = run_mixed("fp32", "fp32 local factors, fp64 outer")
         mixed_tf32 = run_mixed("tf32", "fp32 local factors with tensor-core (split TF32) trailing updates, fp64 outer")
+        mixed_bf16 = run_mixed("bf16", "bf16 local factor streams (fp32 factorisation and accumulation), fp64 outer")
+
+    # the precision (p = 4), batching and serving configurations, compact (rank 0 only)
+    extras = {}
+    if rank == 0 and not args.quick:
+        t0 = time.perf_counter()
+        extras["precision_sweep"] = {
+            "workload": "16384-cell mesh (seed 2) at p=4 (245760 dofs), 64 subdomains, 256 agglomerates p_c=1, "
+                        "checkerboard contrast 1..1e6, local factors per row, fp64 outer PCG; error against the "
+                        "oracle's converged FP64 solve at 1000 sampled dofs",
+            "rows": sweep_measure(timed_reps=2)}
+        extras["precision_sweep"]["seconds"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        bm = batch_measure(1, 1)
+        bm["workload"] = ("48 problems: Voronoi meshes (rng 4) with 1024..16384 cells log-uniform, p in {1..4}, N/256 "
+                          "subdomains, N/64 agglomerates p_c=1, rho per subdomain log-uniform in [1,1e3], N(0,1) rhs; "
+                          "step = setup of all 48 + one batched solve")
+        bm["seconds"] = time.perf_counter() - t0
+        extras["batch"] = bm
+        t0 = time.perf_counter()
+        sv = serve_measure(args.requests, {"fp32": (0.5, 0.75, 0.9), "fp64": (0.9,)})
+        extras["serving"] = {
+            "workload": f"pool of 16 problems (rng 5) shaped like the batch mix, 1..8 N(0,1) rhs per request, "
+                        f"{args.requests} requests per rate: all at once (saturation), then Poisson arrivals at "
+                        f"fractions of the saturation rate; budget 96 GiB, 24 slots",
+            "fp32": sv["fp32"], "fp64": sv["fp64"],
+            "saturation_speedup_mixed_vs_fp64": sv["fp32"]["saturation_closed_batch"]["rhs_per_s"] /
+                                                sv["fp64"]["saturation_closed_batch"]["rhs_per_s"],
+            "seconds": time.perf_counter() - t0}
 
     if rank != 0:
         if world > 1:
@@ -712,7 +877,8 @@ def main():
     peaks = read_peaks()
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = FP64_PEAK_FLOPS_PER_CLK * sm_max * 1e6 / 1e12
-    # roofline of the dominant kernel (largest device time in the breakdown step), timed in the timed region
+    # roofline of the dominant kernel (largest device time in the breakdown step), its launches timed in a
+    # separate pass of the same steps
     dom_ms, dom_n = prof[dom]
     avg_s = dom_ms / 1000.0 / max(dom_n, 1)
     tiles = info["stream_tiles"]
@@ -734,12 +900,22 @@ def main():
             "traffic": local_traffic(tiles) if dom == "local" else None, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
             "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
             "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (issue rate measured by an FMA probe)"}
+    if dom == "local" and args.precision != "fp64":
+        # lower-precision local factors: the sweeps stream 1024 entries of 4 (FP32) or 2 (BF16) bytes per tile
+        eb = 2 if args.precision == "bf16" else 4
+        bytes_ = tiles * 1024 * eb + ndof * 8 * 3
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": bytes_ / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": bytes_ / avg_s / 1e9 / hbm, "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
+                "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": 2 * tiles * 1024,
+                "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
     out = {
         "metric": METRIC, "value": world * args.steps / t_max, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64 (plain FP64 ASPCG)", "parallelism": f"replicas x{world}",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (plain FP64 ASPCG)" if args.precision == "fp64" else
+                   f"{args.precision} local factors, fp64 outer (profiling run)", "parallelism": f"replicas x{world}",
                    "l2": "working set > L2 (matrix 92 MB + local factors + Krylov vectors per step), no flush"},
         "time_to_1e8_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "mean": sum(lat) / len(lat)},
@@ -749,17 +925,19 @@ def main():
         "gpu_launches": int(launches),
         "assembly": asm,
         "rhs_chunk_tuning": tuning,
+        "local_variant_tuning": variant_tuning,
         "kernels_one_step": breakdown,
         "roofline": roof,
         "e2e": {"value": world * args.steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": ndof * 8,
                 "d2h_bytes_per_step": ndof * 8, "host_memory": "pinned"},
         "mixed_fp32": mixed,
         "mixed_tf32": mixed_tf32,
+        "mixed_bf16": mixed_bf16,
         "clocks": clocks,
     }
-    if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_sample(oracle_prep(m, rho), iters)
-        out["cpu_baseline"].pop("seconds_per_solve", None)
+    out.update(extras)
+    if world == 1 and not args.no_cpu_baseline and not args.quick:
+        out["cpu_baseline"] = cpu_baseline(m, rho)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
