@@ -3,11 +3,13 @@
 // dgasm_submit plans the request on the caller's thread (partition, ordering, envelope: host work)
 // and estimates its device footprint (factors, coarse operator, Krylov state).  A scheduler thread
 // admits queued requests in arrival order while a slot is free and the footprint fits in the memory
-// budget next to the admitted ones, builds their preconditioners on the device, and runs rounds of
-// ROUND_ITERS batched PCG iterations over all admitted requests together (one launch per kernel for
-// the whole batch).  Finished requests are retired between rounds, their memory returned, and
-// queued requests join the next round.  Each problem's arithmetic and reduction order are independent
-// of the batch it runs in, so results are bitwise identical alone and in the mix.
+// budget next to the admitted ones, and runs rounds of ROUND_ITERS batched PCG iterations over the
+// active requests together (one launch per kernel for the whole batch).  A setup thread builds the
+// preconditioners of admitted requests and runs their initial step on a stream of its own, so that
+// this device work overlaps the rounds of the requests already active; a request joins the active
+// batch at the first round after its setup completes.  Finished requests are retired between rounds
+// and their memory returned.  Each problem's arithmetic and reduction order are independent of the
+// batch it runs in, so results are bitwise identical alone and in the mix.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -54,21 +56,26 @@ struct dgasm_server_s {
   size_t budget = 0;
   int max_slots = 1;
   int device = 0;
-  cudaStream_t stream = nullptr, own_stream = nullptr;
+  cudaStream_t stream = nullptr, own_stream = nullptr, setup_stream = nullptr;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_setup;
   std::deque<Request*> queue;
+  std::deque<Request*> setup_queue;   // admitted, waiting for their device setup
+  std::vector<Request*> ready;        // set up and initialised, joining the batch at the next round
+  int in_setup = 0;                   // admitted requests not active yet
+  bool stop_setup = false;
   std::vector<Request*> active;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
   uint64_t next_ticket = 1;
   bool stop = false;
   size_t in_use = 0;
   int64_t n_done = 0, rounds = 0, stalls = 0;
-  std::thread th;
+  std::thread th, setup_th;
   std::unique_ptr<Engine> engine, engine_aux;
   bool active_changed = true;
 
   void run();
+  void setup_run();
   void finish_request(Request* r, int rc, const char* msg);
 };
 
@@ -84,19 +91,57 @@ void dgasm_server_s::finish_request(Request* r, int rc, const char* msg) {
   cv_done.notify_all();
 }
 
+// setup thread: device setup (preconditioner, local-solve variant) and initial step of admitted requests,
+// one at a time, on setup_stream
+void dgasm_server_s::setup_run() {
+  cudaSetDevice(device);
+  Engine eng;
+  while (true) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_setup.wait(lk, [&] { return stop_setup || !setup_queue.empty(); });
+      if (setup_queue.empty()) break;
+      r = setup_queue.front();
+      setup_queue.pop_front();
+    }
+    dgasm_prec_s* pc = r->pc.get();
+    int rc = prec_build(pc);
+    // the same local-solve variant a solve of this problem alone would take (measured once per shape)
+    if (rc >= 0) rc = tune_local_variant(pc, r->nrhs, r->b, setup_stream);
+    const dgasm_solve_opts* o = &r->o;
+    if (rc >= 0) rc = eng.build(1, &pc, &r->nrhs, &r->b, &r->x, &o, setup_stream, -1);
+    if (rc >= 0) rc = eng.reset_state();
+    if (rc >= 0) rc = eng.init();
+    if (rc >= 0 && cudaStreamSynchronize(setup_stream) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "init");
+    std::lock_guard<std::mutex> lk(mu);
+    if (rc < 0) {
+      --in_setup;
+      finish_request(r, rc, "setup failed");
+      r->pc.reset();
+    } else {
+      ready.push_back(r);
+    }
+    cv_work.notify_all();
+  }
+}
+
 void dgasm_server_s::run() {
   cudaSetDevice(device);
   engine.reset(new Engine());
   engine_aux.reset(new Engine());
-  std::vector<Request*> admitted;
   while (true) {
-    admitted.clear();
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stop || !active.empty() || !queue.empty(); });
-      if (stop && active.empty() && queue.empty()) break;
+      // admissible: a queued request, a free slot and room in the budget for the first in line
+      auto admissible = [&] {
+        return !stop && !queue.empty() && (int)(active.size() + in_setup) < max_slots &&
+               in_use + queue.front()->bytes <= budget;
+      };
+      cv_work.wait(lk, [&] { return stop || !active.empty() || !ready.empty() || admissible(); });
+      if (stop && active.empty() && queue.empty() && ready.empty() && in_setup == 0) break;
       // admission in arrival order while a slot is free and the footprint fits
-      while (!stop && !queue.empty() && (int)(active.size() + admitted.size()) < max_slots) {
+      while (!stop && !queue.empty() && (int)(active.size() + in_setup) < max_slots) {
         Request* r = queue.front();
         if (in_use + r->bytes > budget) {
           ++stalls;
@@ -106,50 +151,23 @@ void dgasm_server_s::run() {
         in_use += r->bytes;
         r->state = Q_RUNNING;
         r->t_admit = std::chrono::steady_clock::now();
-        admitted.push_back(r);
+        setup_queue.push_back(r);
+        ++in_setup;
+        cv_setup.notify_one();
       }
-    }
-    // device setup of the admitted requests, then their initial step as one batch
-    std::vector<Request*> ok;
-    for (Request* r : admitted) {
-      int rc = prec_build(r->pc.get());
-      // the same local-solve variant a solve of this problem alone would take (measured once per shape)
-      if (rc >= 0) rc = tune_local_variant(r->pc.get(), r->nrhs, r->b, stream);
-      if (rc < 0) {
-        std::lock_guard<std::mutex> lk(mu);
-        finish_request(r, rc, "setup failed");
-        r->pc.reset();
+      // requests whose setup completed join this round
+      for (Request* r : ready) {
+        active.push_back(r);
+        --in_setup;
+        active_changed = true;
+      }
+      ready.clear();
+      if (active.empty()) {
+        // nothing to iterate yet: wait for a setup to complete (or shut down when nothing is left)
+        if (stop && queue.empty() && in_setup == 0) break;
+        cv_work.wait(lk, [&] { return !ready.empty() || (stop && in_setup == 0) || admissible(); });
         continue;
       }
-      ok.push_back(r);
-    }
-    if (!ok.empty()) {
-      std::vector<dgasm_prec_s*> pcs;
-      std::vector<int> nr;
-      std::vector<const double*> bs;
-      std::vector<double*> xs;
-      std::vector<const dgasm_solve_opts*> os;
-      for (Request* r : ok) {
-        pcs.push_back(r->pc.get());
-        nr.push_back(r->nrhs);
-        bs.push_back(r->b);
-        xs.push_back(r->x);
-        os.push_back(&r->o);
-      }
-      int rc = engine_aux->build((int)ok.size(), pcs.data(), nr.data(), bs.data(), xs.data(), os.data(), stream, -1);
-      if (rc >= 0) rc = engine_aux->reset_state();
-      if (rc >= 0) rc = engine_aux->init();
-      if (rc >= 0) rc = (int)cudaStreamSynchronize(stream) == 0 ? DGASM_OK : cuda_error(cudaGetLastError(), "init");
-      std::lock_guard<std::mutex> lk(mu);
-      for (Request* r : ok) {
-        if (rc < 0) {
-          finish_request(r, rc, "initial step failed");
-          r->pc.reset();
-        } else {
-          active.push_back(r);
-        }
-      }
-      active_changed = true;
     }
     if (active.empty()) continue;
     // one round of batched iterations over every admitted request
@@ -285,8 +303,10 @@ extern "C" int dgasm_server_create(size_t hbm_budget, int max_slots, void* strea
     DG_CUDA(cudaStreamCreateWithFlags(&sv->own_stream, cudaStreamNonBlocking));
     sv->stream = sv->own_stream;
   }
+  DG_CUDA(cudaStreamCreateWithFlags(&sv->setup_stream, cudaStreamNonBlocking));
   dgasm_server_s* raw = sv.get();
   sv->th = std::thread([raw] { raw->run(); });
+  sv->setup_th = std::thread([raw] { raw->setup_run(); });
   *out = sv.release();
   return DGASM_OK;
 }
@@ -311,7 +331,7 @@ extern "C" int dgasm_submit(dgasm_server_t sv, dgasm_system_t sys, const dgasm_s
     r->agg.assign(so->agg_of_elem, so->agg_of_elem + ne);
     r->so.agg_of_elem = r->agg.data();
   }
-  r->so.stream = sv->stream;
+  r->so.stream = sv->setup_stream;   // the preconditioner is built by the setup thread
   r->nrhs = nrhs;
   r->b = b;
   r->x = x;
@@ -412,6 +432,13 @@ extern "C" int dgasm_server_destroy(dgasm_server_t sv) {
     sv->cv_work.notify_all();
   }
   if (sv->th.joinable()) sv->th.join();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop_setup = true;
+    sv->cv_setup.notify_all();
+  }
+  if (sv->setup_th.joinable()) sv->setup_th.join();
+  if (sv->setup_stream) cudaStreamDestroy(sv->setup_stream);
   if (sv->own_stream) cudaStreamDestroy(sv->own_stream);
   delete sv;
   return DGASM_OK;
