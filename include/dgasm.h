@@ -170,6 +170,10 @@ int dgasm_selftest_bounded_wait(double limit_ms, int* gave_up, double* elapsed_m
  * same layout; tile row 0 is unchanged).  Synchronous.  DGASM_EINVAL for bad arguments, DGASM_ETIMEOUT if
  * the kernel's bounded wait on the MMA completion gave up, DGASM_ECUDA on a CUDA error. */
 int dgasm_selftest_tc_update(int n, const float* tiles, float* out);
+/* The same step with the BF16 mode's kernel: tcgen05.mma of kind::f16 on BF16 operands, each FP32 entry split
+ * in three BF16 parts (hi, mid, lo) and six products accumulated in FP32 in tensor memory.  Arguments, layout
+ * and errors as dgasm_selftest_tc_update. */
+int dgasm_selftest_tc_update_bf16(int n, const float* tiles, float* out);
 
 /* ---- Two-level Schwarz preconditioner (Sec. 3: local solvers, coarse solver, Eq. R0T, Eq. A0) --- */
 typedef struct {
@@ -256,6 +260,8 @@ typedef struct {
   double plan_ms;         /* host part of dgasm_setup: partition, ordering, envelopes, task lists */
   double setup_ms;        /* wall time of dgasm_setup */
   int setup_launches;     /* kernels launched by dgasm_setup */
+  int tc_fallback;        /* TF32 / BF16 modes: 1 if the tensor-core factorisation met a non-positive pivot and
+                             the local factors were computed again with the FP32 CUDA-core updates */
 } dgasm_prec_info_t;
 int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info);
 int dgasm_prec_destroy(dgasm_prec_t pc);

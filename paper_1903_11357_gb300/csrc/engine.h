@@ -162,11 +162,12 @@ int launch_extract_rows(int prec, const EnvDev& E, const int* sub_e0, const int*
 int launch_chol_diag(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, int* err, void* stream);
 int launch_chol_panel(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, void* stream);
 int launch_chol_update(int prec, const EnvDev& E, void* L, int K, const int* tasks, int n, void* stream);
-// the trailing update of step K on the tensor cores (tcgen05, TF32 operands split in two, FP32 accumulation);
-// tasks: n quadruples (pstart, n, mb, nb) of Envelope::tc_task, panel_task: all (s, I) pairs; err[3]
-// (bounded wait on the MMA completion gave up) is set on timeout
+// the trailing update of step K on the tensor cores (tcgen05, FP32 accumulation in tensor memory; bf16 = 0:
+// kind::tf32 with operands split in two, 1: kind::f16 with BF16 operands split in three); tasks: n quadruples
+// (pstart, n, mb, nb) of Envelope::tc_task, panel_task: all (s, I) pairs; err[3] (bounded wait on the MMA
+// completion gave up) is set on timeout
 int launch_chol_update_tc(const EnvDev& E, float* L, int K, const int* panel_task, const int* tasks, int n, int* err,
-                          void* stream);
+                          void* stream, int bf16);
 int launch_to_colmajor(int prec, const void* Lr, void* Lc, long long ntiles, void* stream);
 int launch_to_bf16(const float* src, void* dst, long long n, void* stream);
 // dst tile t = src tile idx[t] (same element layout), for the backward-ordered copy of a factor

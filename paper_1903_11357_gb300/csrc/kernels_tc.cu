@@ -1,6 +1,6 @@
 // Trailing update of the tile Cholesky factorisation of the subdomain matrices A_i (Sec. 3, local
 // solvers: A_i is the principal submatrix of A on the subdomain's dofs) on the 5th-generation tensor cores,
-// used by the TF32 precision mode.
+// used by the TF32 precision mode (kind::tf32) and the BF16 precision mode (kind::f16 with BF16 operands).
 //
 // Step K of the right-looking tile Cholesky updates C_IJ -= L_IK L_JK^T for every pair I >= J of the tile
 // rows S(s, K) below the diagonal tile that reach column K.  Per (subdomain, K) this is the lower triangle
@@ -15,12 +15,18 @@
 // so the factor stays as accurate as the FP32 mode's and the subdomain Cholesky stays positive definite at
 // the coefficient contrasts the method targets.
 //
+// BF16 keeps 8 mantissa bits, so the BF16 mode splits each FP32 operand three ways, v = hi + mid + lo with
+// hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid), and accumulates the six products down to the
+// order of FP32 rounding, lo*hi + hi*lo + mid*mid + mid*hi + hi*mid + hi*hi (six BF16 MMAs per K = 16 step):
+// BF16 tensor-core products with FP32 accumulation in tensor memory at FP32-level accuracy.
+//
 // Operands are staged by the CTA's threads into shared memory in the canonical K-major layout without
-// swizzling: core matrices of 8 rows x 16 bytes (4 TF32 entries), 128 contiguous bytes each; the 8 core
+// swizzling: core matrices of 8 rows x 16 bytes (4 TF32 or 8 BF16 entries), 128 contiguous bytes each; the core
 // matrices of an 8-row group follow each other along K (leading-dimension offset 128 B) and row groups are
-// 1024 B apart (stride-dimension offset).  One thread issues the MMAs and commits them to an mbarrier; the
+// 1024 B (TF32) or 512 B (BF16) apart (stride-dimension offset).  One thread issues the MMAs and commits them to an mbarrier; the
 // wait on it is bounded, and on timeout the kernel sets the error word, skips its stores, waits once more
 // (bounded) and frees its tensor memory before returning.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -37,9 +43,11 @@ constexpr int TT = T * T;
 constexpr int MBT = 4;                       // row tiles per block: M = 128
 constexpr int NBT = 8;                       // column tiles per block: N <= 256
 constexpr int TC_THREADS = 128;              // 4 warps: one per row tile (tensor-memory lane quarter)
-constexpr int A_BYTES = MBT * TT * 4;        // one split part of A: 16 KB
-constexpr int B_BYTES = NBT * TT * 4;        // one split part of B: 32 KB
-constexpr int TC_SMEM = 2 * A_BYTES + 2 * B_BYTES + 1024;   // + alignment slack
+// bytes of one split part of A (MBT row tiles) and of B (NBT row tiles): TF32 4 bytes, BF16 2 bytes an entry;
+// TF32 splits in two parts, BF16 in three
+template <bool BF> constexpr int a_bytes() { return MBT * TT * (BF ? 2 : 4); }
+template <bool BF> constexpr int b_bytes() { return NBT * TT * (BF ? 2 : 4); }
+template <bool BF> constexpr int tc_smem() { return (BF ? 3 : 2) * (a_bytes<BF>() + b_bytes<BF>()) + 1024; }
 constexpr unsigned TMEM_COLS = 256;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // about one second at the GB300 clock
 
@@ -56,16 +64,38 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+// byte offset of entry (row, k) in the canonical K-major layout of a 32-column BF16 operand: core matrices of
+// 8 rows x 8 entries, four along K per 8-row group (512 B a group)
+__device__ __forceinline__ unsigned canon_off_bf16(int row, int k) {
+  return (unsigned)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
 // shared-memory matrix descriptor: start address, leading-dimension byte offset 128 (next core matrix along
-// K), stride-dimension byte offset 1024 (next 8-row group), descriptor version 1, no swizzle
-__device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
+// K), stride-dimension byte offset sbo (next 8-row group: 1024 B for TF32, 512 B for BF16), descriptor
+// version 1, no swizzle
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned sbo = 1024) {
   return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)(128 >> 4) << 16) |
-         ((unsigned long long)(1024 >> 4) << 32) | (1ull << 46);
+         ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
 }
 
 // instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, N and M
 __host__ __device__ constexpr unsigned tf32_idesc(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+// instruction descriptor of kind::f16 with BF16 operands: D FP32, A and B BF16 (the same type), both K-major
+__host__ __device__ constexpr unsigned bf16_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned dtmem, unsigned long long adesc, unsigned long long bdesc, unsigned idesc,
+                                         int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(unsigned dtmem, unsigned long long adesc, unsigned long long bdesc, unsigned idesc,
@@ -148,6 +178,45 @@ __device__ __forceinline__ void stage(const float* __restrict__ L, const long lo
   }
 }
 
+// the BF16 three-way split of `ntile` tiles into p0 (hi), p1 (mid), p2 (lo), zero rows up to ROWS
+__device__ __forceinline__ unsigned pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+template <int ROWS>
+__device__ __forceinline__ void stage_bf16(const float* __restrict__ L, const long long* base, int ntile,
+                                           unsigned char* p0, unsigned char* p1, unsigned char* p2) {
+  constexpr int NV = ROWS * (T / 4) / TC_THREADS;   // float4 per thread
+  float4 v[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const int i = threadIdx.x + j * TC_THREADS;
+    const int row = i >> 3, kc = i & 7, t = row >> 5, r = row & 31;
+    v[j] = t < ntile ? __ldg(reinterpret_cast<const float4*>(L + base[t] * TT + r * T + 4 * kc))
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const int i = threadIdx.x + j * TC_THREADS;
+    const int row = i >> 3, kc = i & 7;
+    const float x[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+    float h[4], m[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      h[q] = __bfloat162float(__float2bfloat16_rn(x[q]));
+      const float r1 = x[q] - h[q];
+      m[q] = __bfloat162float(__float2bfloat16_rn(r1));
+      l[q] = r1 - m[q];   // rounded to BF16 by the packing below
+    }
+    const unsigned o = canon_off_bf16(row, 4 * kc);
+    *reinterpret_cast<uint2*>(p0 + o) = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+    *reinterpret_cast<uint2*>(p1 + o) = make_uint2(pack_bf16x2(m[0], m[1]), pack_bf16x2(m[2], m[3]));
+    *reinterpret_cast<uint2*>(p2 + o) = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+  }
+}
+
+template <bool BF>
 __global__ void __launch_bounds__(TC_THREADS) k_chol_update_tc(EnvDev E, float* __restrict__ L, int K,
                                                                const int* __restrict__ panel,
                                                                const int* __restrict__ tasks, int* __restrict__ err) {
@@ -155,11 +224,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_update_tc(EnvDev E, float* 
   __shared__ __align__(8) unsigned long long done_bar;
   __shared__ unsigned tmem_base;
   __shared__ long long a_base[MBT], b_base[NBT], c_base[MBT][NBT];
+  constexpr int AB = a_bytes<BF>(), BB = b_bytes<BF>(), NPART = BF ? 3 : 2;
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<size_t>(smem_raw) + 1023) & ~(size_t)1023);
-  unsigned char* a_hi = sm;
-  unsigned char* a_lo = sm + A_BYTES;
-  unsigned char* b_hi = sm + 2 * A_BYTES;
-  unsigned char* b_lo = sm + 2 * A_BYTES + B_BYTES;
+  unsigned char* a_p[3] = {sm, sm + AB, sm + 2 * AB};   // split parts of A (hi, lo / hi, mid, lo)
+  unsigned char* b_p[3] = {sm + NPART * AB, sm + NPART * AB + BB, sm + NPART * AB + 2 * BB};
   const int pstart = tasks[4 * blockIdx.x], n = tasks[4 * blockIdx.x + 1];
   const int mb = tasks[4 * blockIdx.x + 2], nb = tasks[4 * blockIdx.x + 3];
   const int s = panel[2 * pstart];
@@ -195,9 +263,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_update_tc(EnvDev E, float* 
                        : -1;
   }
   __syncthreads();
-  stage<MBT * T>(L, a_base, na, a_hi, a_lo);
-  if (nbt > 4) stage<NBT * T>(L, b_base, nbt, b_hi, b_lo);
-  else stage<4 * T>(L, b_base, nbt, b_hi, b_lo);
+  if constexpr (BF) {
+    stage_bf16<MBT * T>(L, a_base, na, a_p[0], a_p[1], a_p[2]);
+    if (nbt > 4) stage_bf16<NBT * T>(L, b_base, nbt, b_p[0], b_p[1], b_p[2]);
+    else stage_bf16<4 * T>(L, b_base, nbt, b_p[0], b_p[1], b_p[2]);
+  } else {
+    stage<MBT * T>(L, a_base, na, a_p[0], a_p[1]);
+    if (nbt > 4) stage<NBT * T>(L, b_base, nbt, b_p[0], b_p[1]);
+    else stage<4 * T>(L, b_base, nbt, b_p[0], b_p[1]);
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy stores -> tensor-core reads
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -206,17 +280,32 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_update_tc(EnvDev E, float* 
   const unsigned bar = smem_u32(&done_bar);
 
   if (threadIdx.x == 0) {
-    const unsigned idesc = tf32_idesc(MBT * T, N);
-    const unsigned ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-    const unsigned as[3] = {al, ah, ah}, bs[3] = {bh, bl, bh};   // lo*hi, hi*lo, then hi*hi
     int acc = 0;
+    if constexpr (BF) {
+      const unsigned idesc = bf16_idesc(MBT * T, N);
+      const unsigned a0s = smem_u32(a_p[0]), a1s = smem_u32(a_p[1]), a2s = smem_u32(a_p[2]);
+      const unsigned b0s = smem_u32(b_p[0]), b1s = smem_u32(b_p[1]), b2s = smem_u32(b_p[2]);
+      // lo*hi, hi*lo, mid*mid, mid*hi, hi*mid, then hi*hi (the small terms first)
+      const unsigned as[6] = {a2s, a0s, a1s, a1s, a0s, a0s}, bs[6] = {b0s, b2s, b1s, b0s, b1s, b0s};
 #pragma unroll
-    for (int pass = 0; pass < 3; ++pass)
+      for (int pass = 0; pass < 6; ++pass)
 #pragma unroll
-      for (int ks = 0; ks < T / 8; ++ks) {   // K = 8 per MMA: two core matrices (256 B) along K
-        mma_tf32(tmem, smem_desc(as[pass] + 256 * ks), smem_desc(bs[pass] + 256 * ks), idesc, acc);
-        acc = 1;
-      }
+        for (int ks = 0; ks < T / 16; ++ks) {   // K = 16 per MMA: two core matrices (256 B) along K
+          mma_bf16(tmem, smem_desc(as[pass] + 256 * ks, 512), smem_desc(bs[pass] + 256 * ks, 512), idesc, acc);
+          acc = 1;
+        }
+    } else {
+      const unsigned idesc = tf32_idesc(MBT * T, N);
+      const unsigned ah = smem_u32(a_p[0]), al = smem_u32(a_p[1]), bh = smem_u32(b_p[0]), bl = smem_u32(b_p[1]);
+      const unsigned as[3] = {al, ah, ah}, bs[3] = {bh, bl, bh};   // lo*hi, hi*lo, then hi*hi
+#pragma unroll
+      for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+        for (int ks = 0; ks < T / 8; ++ks) {   // K = 8 per MMA: two core matrices (256 B) along K
+          mma_tf32(tmem, smem_desc(as[pass] + 256 * ks), smem_desc(bs[pass] + 256 * ks), idesc, acc);
+          acc = 1;
+        }
+    }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
   }
   const bool ok = mbar_wait_bounded(bar, 0);
@@ -253,8 +342,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_chol_update_tc(EnvDev E, float* 
 
 }  // namespace
 
-int launch_chol_update_tc(const EnvDev& E, float* L, int K, const int* panel_task, const int* tasks, int n, int* err,
-                          void* stream) {
+namespace {
+template <bool BF>
+int launch_tc(const EnvDev& E, float* L, int K, const int* panel_task, const int* tasks, int n, int* err, void* stream) {
   if (n <= 0) return 0;
   {
     static std::mutex mu;
@@ -263,13 +353,20 @@ int launch_chol_update_tc(const EnvDev& E, float* L, int K, const int* panel_tas
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (!done.count(dev)) {
-      cudaError_t e = cudaFuncSetAttribute(k_chol_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+      cudaError_t e = cudaFuncSetAttribute(k_chol_update_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<BF>());
       if (e != cudaSuccess) return (int)e;
       done.insert(dev);
     }
   }
-  k_chol_update_tc<<<n, TC_THREADS, TC_SMEM, (cudaStream_t)stream>>>(E, L, K, panel_task, tasks, err);
+  k_chol_update_tc<BF><<<n, TC_THREADS, tc_smem<BF>(), (cudaStream_t)stream>>>(E, L, K, panel_task, tasks, err);
   return (int)cudaGetLastError();
+}
+}  // namespace
+
+int launch_chol_update_tc(const EnvDev& E, float* L, int K, const int* panel_task, const int* tasks, int n, int* err,
+                          void* stream, int bf16) {
+  return bf16 ? launch_tc<true>(E, L, K, panel_task, tasks, n, err, stream)
+              : launch_tc<false>(E, L, K, panel_task, tasks, n, err, stream);
 }
 
 }  // namespace dgasm

@@ -69,9 +69,9 @@ int factor_env(int prec, const Envelope& E, EnvBufs& D, void* Lr, int* err, cuda
     if (ev) ev->end(id, st);
     if (rc) return cuda_error(rc, "tile Cholesky panel step");
     id = ev && nu ? ev->begin(PK_CHOL_UPDATE, st) : -1;
-    if (prec == DGASM_TF32)   // tensor cores (split TF32 products, FP32 accumulation)
+    if (prec == DGASM_TF32 || prec == DGASM_BF16)   // tensor cores (split TF32 or BF16 products, FP32 accumulation)
       rc = launch_chol_update_tc(D.dev, (float*)Lr, K, D.panel_task.as<int>(), D.tc_task.as<int>() + 4 * (size_t)E.tc_off[K],
-                                 E.tc_off[K + 1] - E.tc_off[K], err, st);
+                                 E.tc_off[K + 1] - E.tc_off[K], err, st, prec == DGASM_BF16 ? 1 : 0);
     else
       rc = launch_chol_update(fp, D.dev, Lr, K, D.upd_task.as<int>() + 3 * (size_t)E.upd_off[K], nu, st);
     if (ev) ev->end(id, st);
@@ -212,6 +212,23 @@ int prec_build(dgasm_prec_s* pc) {
                                 P.nsub, ne, st));
     nl += 1;
     DG_TRY(factor_env(fprec, P.env, pc->env, Lf.ptr, pc->err.as<int>(), st, ev, &nl));
+    if (fprec == DGASM_TF32 || fprec == DGASM_BF16) {
+      // breakdown of the tensor-core factorisation (a non-positive pivot): factorise again from A_i with the
+      // FP32 CUDA-core updates
+      int herr[3];
+      DG_CUDA(cudaMemcpyAsync(herr, pc->err.ptr, sizeof(herr), cudaMemcpyDeviceToHost, st));
+      DG_CUDA(cudaStreamSynchronize(st));
+      if (herr[0]) {
+        const int err0[3] = {0, -1, -1};
+        DG_CUDA(cudaMemcpyAsync(pc->err.ptr, err0, sizeof(err0), cudaMemcpyHostToDevice, st));
+        DG_CUDA(cudaMemsetAsync(Lf.ptr, 0, Lf.bytes, st));
+        DG_CUDA(launch_extract_rows(1, pc->env.dev, pc->sub_e0.as<int>(), pc->rowptr.as<int>(), pc->col.as<int>(),
+                                    pc->vals.as<double>(), np, np2s, pc->scale.as<double>(), Lf.ptr, P.nsub, ne, st));
+        DG_TRY(factor_env(DGASM_FP32, P.env, pc->env, Lf.ptr, pc->err.as<int>(), st, ev, &nl));
+        pc->tc_fallback = 1;
+        nl += 1;
+      }
+    }
     // super-row inverse blocks, then the forward (column-major) and backward (row-major) solve streams
     DG_TRY(build_streams(fprec, P.env, pc->env, Lf, pc->Lc, pc->Lr, st, &nl));
   }
@@ -504,6 +521,7 @@ extern "C" int dgasm_prec_info(dgasm_prec_t pc, dgasm_prec_info_t* info) {
   info->plan_ms = pc->plan_ms;
   info->setup_ms = pc->setup_ms;
   info->setup_launches = pc->setup_launches;
+  info->tc_fallback = pc->tc_fallback;
   return DGASM_OK;
 }
 
@@ -514,7 +532,8 @@ extern "C" int dgasm_prec_destroy(dgasm_prec_t pc) {
 
 // One trailing-update step on the tensor cores for a dense lower tile matrix (Sec. 3, local solvers: the
 // update C_IJ -= L_I0 L_J0^T of step 0 of the tile Cholesky), for tests of the tcgen05 kernel.
-extern "C" int dgasm_selftest_tc_update(int n, const float* tiles, float* out) {
+namespace {
+int selftest_tc(int n, const float* tiles, float* out, int bf16) {
   using namespace dgasm;
   clear_error();
   if (n < 1 || n > 64 || !tiles || !out) return set_error(DGASM_EINVAL, "dgasm_selftest_tc_update: need 1 <= n <= 64 and buffers");
@@ -531,7 +550,7 @@ extern "C" int dgasm_selftest_tc_update(int n, const float* tiles, float* out) {
   DG_CUDA(cudaMemcpy(L.ptr, tiles, bytes, cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemset(err.ptr, 0, 4 * sizeof(int)));
   int rc = launch_chol_update_tc(D.dev, L.as<float>(), 0, D.panel_task.as<int>(), D.tc_task.as<int>() + 4 * (size_t)E.tc_off[0],
-                                 E.tc_off[1] - E.tc_off[0], err.as<int>(), nullptr);
+                                 E.tc_off[1] - E.tc_off[0], err.as<int>(), nullptr, bf16);
   if (rc) return cuda_error(rc, "tensor-core update self-test launch");
   DG_CUDA(cudaDeviceSynchronize());
   int h[4];
@@ -540,4 +559,9 @@ extern "C" int dgasm_selftest_tc_update(int n, const float* tiles, float* out) {
   DG_CUDA(cudaMemcpy(out, L.ptr, bytes, cudaMemcpyDeviceToHost));
   return DGASM_OK;
 }
+}  // namespace
+
+extern "C" int dgasm_selftest_tc_update(int n, const float* tiles, float* out) { return selftest_tc(n, tiles, out, 0); }
+
+extern "C" int dgasm_selftest_tc_update_bf16(int n, const float* tiles, float* out) { return selftest_tc(n, tiles, out, 1); }
 

@@ -124,6 +124,7 @@ struct dgasm_prec_s {
   int local_variant = dgasm::LV_TUNE;   // envelope problems: sweeps or explicit inverses (LocalVariant)
   dgasm::DevBuf dli, dli_off, dli_item;  // explicit inverses, their offsets and the item table
   int n_dli_items = 0, dli_nmax = 0;
+  int tc_fallback = 0;      // 1: the tensor-core factorisation broke down and was redone with FP32 CUDA cores
   dgasm::DevBuf dinv;       // [ne][np][np] FP64, internal element order
   dgasm::EnvBufs env, env0;
   dgasm::Workspace ws;

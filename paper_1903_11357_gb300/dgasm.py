@@ -50,7 +50,7 @@ class PrecInfo(C.Structure):
                 ("local_dofs", C.c_int64), ("local_tiles", C.c_int64), ("stream_tiles", C.c_int64),
                 ("factor_flops", C.c_int64),
                 ("nnzb", C.c_int64), ("plan_ms", C.c_double), ("setup_ms", C.c_double),
-                ("setup_launches", C.c_int)]
+                ("setup_launches", C.c_int), ("tc_fallback", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -108,6 +108,7 @@ def lib():
             "dgasm_profile_enable": [C.c_int],
             "dgasm_selftest_bounded_wait": [C.c_double, C.POINTER(C.c_int), dp],
             "dgasm_selftest_tc_update": [C.c_int, vp, vp],
+            "dgasm_selftest_tc_update_bf16": [C.c_int, vp, vp],
             "dgasm_profile_read": [C.c_int, dp, i64p, C.c_int],
             "dgasm_server_create": [C.c_size_t, C.c_int, vp, C.POINTER(vp)],
             "dgasm_submit": [vp, vp, C.POINTER(SetupOpts), C.c_int, vp, vp, C.POINTER(SolveOpts),
@@ -428,17 +429,18 @@ def selftest_plan(system: "System", nsub: int):
     return v.value, n.value
 
 
-def selftest_tc_update(tiles):
+def selftest_tc_update(tiles, kind="tf32"):
     """One tensor-core trailing-update step (C_IJ -= L_I0 L_J0^T, 1 <= J <= I <= n) on a dense lower tile
     matrix: `tiles` is a float32 array of shape ((n+1)(n+2)/2, 32, 32), tile (I, J) at I(I+1)/2 + J; returns
-    the updated array."""
+    the updated array.  kind: "tf32" (the TF32 mode's kernel) or "bf16" (the BF16 mode's)."""
     t = np.ascontiguousarray(tiles, dtype=np.float32)
     m = t.shape[0]
     n = int(round((-3 + np.sqrt(1 + 8 * m)) / 2))
     if t.shape[1:] != (32, 32) or (n + 1) * (n + 2) // 2 != m:
         raise ValueError("tiles must have shape ((n+1)(n+2)/2, 32, 32)")
     out = np.empty_like(t)
-    check(lib().dgasm_selftest_tc_update(n, t.ctypes.data, out.ctypes.data))
+    fn = lib().dgasm_selftest_tc_update_bf16 if kind == "bf16" else lib().dgasm_selftest_tc_update
+    check(fn(n, t.ctypes.data, out.ctypes.data))
     return out
 
 

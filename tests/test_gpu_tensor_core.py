@@ -1,11 +1,13 @@
-"""The TF32 precision mode: trailing updates of the local tile Cholesky (Sec. 3, local solvers) on the tensor
-cores (tcgen05, split TF32 operands, FP32 accumulation).
+"""The TF32 and BF16 precision modes: trailing updates of the local tile Cholesky (Sec. 3, local solvers) on the
+tensor cores (tcgen05; split TF32 operands, or BF16 operands split in three, FP32 accumulation).
 
 The kernel itself is pinned against a plain float64 numpy product of the same float32 tiles.  Split TF32
 (v = hi + lo, three MMAs per k-step) keeps about 21 bits of each product, and the tensor cores accumulate the
 32 products of a k-loop in FP32, so an entry's error is bounded by about 32 * 2^-22 of the sum of the absolute
 products; the test allows 2^-16 of (|C| + sum |products|).  A single-pass TF32 product (2^-11) or any layout
-mistake fails it.  The mode as a whole is checked against the library's FP64 and FP32 modes: its
+mistake fails it.  The BF16 kernel splits each FP32 entry exactly into three BF16 parts (8 bits each) and keeps
+the six products down to the order 2^-16 of the part sizes, so its products carry about 23 bits: the same bound
+holds, and a single BF16 pass (2^-8) or a two-part split (2^-15 with the FP32 accumulation) fails it.  The mode as a whole is checked against the library's FP64 and FP32 modes: its
 preconditioner may differ from FP64's by a few times FP32's difference (at most 20 times), and its solves
 reach the 1e-8 true residual within two iterations of FP32's.
 """
@@ -31,10 +33,11 @@ def tid(I, J):
     return I * (I + 1) // 2 + J
 
 
+@pytest.mark.parametrize("kind", ["tf32", "bf16"])
 @pytest.mark.parametrize("n", [1, 4, 5, 9, 13])
-def test_tc_update_matches_float64_product(n):
+def test_tc_update_matches_float64_product(n, kind):
     t = lower_tiles(n, 100 + n)
-    out = dg.selftest_tc_update(t)
+    out = dg.selftest_tc_update(t, kind=kind)
     for I in range(n + 1):
         for J in range(I + 1):
             k = tid(I, J)
@@ -89,5 +92,25 @@ def test_tf32_mode_apply_and_solve_track_fp32():
     rc, st, x = res["tf32"]
     assert rc == 0 and st["converged"] and st["true_relres"] <= 1e-8
     assert abs(st["iters"] - res["fp32"][1]["iters"]) <= 2
+    x64 = res["fp64"][2]
+    assert np.linalg.norm(x - x64) <= 1e-6 * np.linalg.norm(x64)
+
+
+def test_bf16_mode_factorises_on_the_tensor_cores_and_solves():
+    """BF16 mode: the trailing updates on the tensor cores with BF16 operands (three-part split), the solve
+    streams in BF16; the outer FP64 PCG reaches the 1e-8 true residual within 10 % of FP32's iterations and its
+    solution agrees with FP64's to 1e-6."""
+    res = {}
+    for prec in ("fp64", "fp32", "bf16"):
+        S, P = _case(prec)   # P of the last mode (bf16) is kept
+        b = torch.tensor(S.rhs(), dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(b)
+        rc, st = P.solve(b, x, rtol=1e-8)
+        torch.cuda.synchronize()
+        res[prec] = (rc, st[0], x.cpu().numpy())
+    rc, st, x = res["bf16"]
+    assert rc == 0 and st["converged"] and st["true_relres"] <= 1e-8
+    assert P.info()["tc_fallback"] == 0   # the tensor-core factorisation held
+    assert st["iters"] <= 1.1 * res["fp32"][1]["iters"] + 1
     x64 = res["fp64"][2]
     assert np.linalg.norm(x - x64) <= 1e-6 * np.linalg.norm(x64)
