@@ -220,7 +220,49 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
   // non-nested coarse spaces restrict in their own kernel (an element meets several coarse cells)
   const bool restrict_ = nq > 0 && P.r0t_ptr == nullptr;
   const bool fused_r0 = restrict_ && nq == NQ1;
-  for (int base = 0; base < nd && any; base += UPD_THREADS) {
+  if (mode == MODE_ITER) {
+    // the CG update, two dofs per thread and pass, every load of both issued before the stores; each thread
+    // still accumulates its dofs t, t + UPD_THREADS, t + 2 UPD_THREADS, ... in that order
+    for (int t0 = threadIdx.x; t0 < nd && any; t0 += 2 * UPD_THREADS) {
+      long long dv[2];
+      bool ok[2];
+      double w2[2][NQ1];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = t0 + h * UPD_THREADS;
+        ok[h] = t < nd;
+        const int tt = ok[h] ? t : t0;
+        dv[h] = (long long)P.grp_elems[g0 + tt / np] * np + tt % np;
+#pragma unroll
+        for (int c = 0; c < NQ1; ++c) w2[h][c] = fused_r0 ? P.r0t[dv[h] * NQ1 + c] : 0.0;
+      }
+#pragma unroll
+      for (int kk = 0; kk < KM; ++kk) {
+        if (!act[kk]) continue;
+        double xv[2], pv[2], qv[2], rv0[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long long o = kk * (long long)P.ndof + dv[h];
+          xv[h] = P.x[o];
+          pv[h] = P.p[o];
+          qv[h] = P.q[o];
+          rv0[h] = P.r[o];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!ok[h]) continue;
+          const long long o = kk * (long long)P.ndof + dv[h];
+          P.x[o] = fma(alpha[kk], pv[h], xv[h]);
+          const double rv = fma(-alpha[kk], qv[h], rv0[h]);
+          P.r[o] = rv;
+          prr[kk] = fma(rv, rv, prr[kk]);
+#pragma unroll
+          for (int c = 0; c < NQ1; ++c) pr0[kk][c] = fma(w2[h][c], rv, pr0[kk][c]);
+        }
+      }
+    }
+  }
+  for (int base = 0; base < nd && any && mode != MODE_ITER; base += UPD_THREADS) {
     const int t = base + threadIdx.x;
     if (t >= nd) break;
     const int e = P.grp_elems[g0 + t / np], a = t % np;
