@@ -40,7 +40,7 @@ int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
   o_vec = take(sizeof(double) * 6 * k * ndof);
   o_coarse = take(sizeof(double) * 2 * k * std::max(n0, 1));
-  o_scal = take(sizeof(double) * 5 * k);
+  o_scal = take(sizeof(double) * 6 * k);
   o_int = take(sizeof(int) * 3 * k);
   o_hist = take(sizeof(double) * 2 * (size_t)k * maxit);
   o_ppq = take(sizeof(double) * (size_t)n_spmv_items * k);
@@ -99,7 +99,7 @@ void Workspace::fill(const dgasm_prec_s& pc, ProbDev& D, int kk, const double* b
   double* c = (double*)(base + o_coarse);
   D.r0 = c; D.z0 = c + (size_t)k * std::max(pc.n0, 1);
   double* s = (double*)(base + o_scal);
-  D.bnorm = s; D.gamma = s + k; D.alpha = s + 2 * k; D.relres = s + 3 * k; D.true_rr = s + 4 * k;
+  D.bnorm = s; D.gamma = s + k; D.alpha = s + 2 * k; D.relres = s + 3 * k; D.true_rr = s + 4 * k; D.gamma1 = s + 5 * k;
   int* iv = (int*)(base + o_int);
   D.done = iv; D.iters = iv + k; D.status = iv + 2 * k;
   double* h = (double*)(base + o_hist);
@@ -233,7 +233,7 @@ int Engine::spmv(int operand, EventPairs* ev) {
   return DGASM_OK;
 }
 
-int Engine::precond(int mode, EventPairs* ev) {
+int Engine::precond(int mode, EventPairs* ev, int wslot) {
   const int n = nprob;
   if (tot_rnn)   // non-nested coarse spaces: r_0 = R_0 r before the coarse solve forks off
     DG_CUDA(timed_launch(PK_UPDATE, stream, ev, launches, [&] { return launch_restrict_nn(B, tot_rnn, km, stream); }));
@@ -255,7 +255,7 @@ int Engine::precond(int mode, EventPairs* ev) {
     if (tot) DG_CUDA(timed_launch(PK_LOCAL, stream, ev, launches, [&] { return launch_dli(B, slot, tot, km, stream); }));
   }
   DG_CUDA(cudaStreamWaitEvent(stream, ev_join, 0));
-  DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, km, tot_rnn > 0, stream); }));
+  DG_CUDA(timed_launch(PK_PUPDATE, stream, ev, launches, [&] { return launch_pupdate(B, tot_spmv, mode, km, tot_rnn > 0, wslot, stream); }));
   return DGASM_OK;
 }
 
@@ -263,9 +263,9 @@ int Engine::init(bool x0) {
   init_ev.reset();
   for (int i = 0; i < nprob; ++i) pcs[i]->ws.lanczos_len.assign(pcs[i]->ws.k, -1);
   if (!x0) {
-    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT, km, stream); }));
+    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT, km, 0, stream); }));
   } else {
-    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT_X0, km, stream); }));
+    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_INIT_X0, km, 0, stream); }));
     // a zero right-hand side has the solution 0 whatever the initial guess
     for (int i = 0; i < nprob; ++i) {
       const ProbDev& D = hp[i];
@@ -277,9 +277,9 @@ int Engine::init(bool x0) {
         if (bn[kk] == 0.0) DG_CUDA(cudaMemsetAsync(D.x + (size_t)kk * D.ndof, 0, sizeof(double) * D.ndof, stream));
     }
     DG_TRY(spmv(1, &init_ev));
-    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_RESTART, km, stream); }));
+    DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_RESTART, km, 0, stream); }));
   }
-  DG_TRY(precond(MODE_INIT, &init_ev));
+  DG_TRY(precond(MODE_INIT, &init_ev, 0));
   return DGASM_OK;
 }
 
@@ -314,8 +314,8 @@ int Engine::restart(int* count) {
   h_remaining[0] = *count;
   h_remaining[1] = 0;
   DG_CUDA(cudaMemcpyAsync(d_remaining, h_remaining, 2 * sizeof(int), cudaMemcpyHostToDevice, stream));
-  DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_RESTART, km, stream); }));
-  DG_TRY(precond(MODE_INIT, &init_ev));
+  DG_CUDA(timed_launch(PK_UPDATE, stream, &init_ev, launches, [&] { return launch_update(B, tot_grp, MODE_RESTART, km, 0, stream); }));
+  DG_TRY(precond(MODE_INIT, &init_ev, 0));
   return DGASM_OK;
 }
 
@@ -328,11 +328,15 @@ int Engine::iterate(int max_iters, int* ran) {
     DG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     const long long before = launches;
     int rc = 0;
+    // gamma alternates between two slots: the p update of iteration it reads slot it % 2 and writes the other,
+    // the x/r update of iteration it reads slot it % 2 (CHUNK is even, and the initial p update writes slot 0)
+    static_assert(CHUNK % 2 == 0, "the gamma slots must line up from one graph launch to the next");
     for (int it = 0; it < CHUNK && rc == 0; ++it) {
+      const int gs = it & 1;
       rc = spmv(0, &graph_ev);
-      if (!rc) rc = timed_launch(PK_UPDATE, stream, &graph_ev, launches, [&] { return launch_update(B, tot_grp, MODE_ITER, km, stream); });
+      if (!rc) rc = timed_launch(PK_UPDATE, stream, &graph_ev, launches, [&] { return launch_update(B, tot_grp, MODE_ITER, km, gs, stream); });
       if (!rc) {
-        int r3 = precond(MODE_ITER, &graph_ev);
+        int r3 = precond(MODE_ITER, &graph_ev, gs ^ 1);
         if (r3 < 0) rc = r3;
       }
     }

@@ -92,6 +92,7 @@ struct ProbDev {
   double *r0, *z0;    // [k][n0]
   // per right-hand side scalars
   double *bnorm, *gamma, *alpha, *relres, *true_rr;
+  double* gamma1;     // second slot of gamma: the p update of an iteration reads one slot and writes the other
   int *done, *iters, *status;
   double *alpha_hist, *beta_hist;  // [k][maxit]
   // deterministic partial sums
@@ -119,7 +120,8 @@ enum UpdateMode { MODE_INIT = 0, MODE_ITER = 1, MODE_RESTART = 2, MODE_INIT_X0 =
 // km: 1 when every problem of the batch has one right-hand side, else KMAX
 int launch_spmv(const BatchDev& B, int p, int total, int operand /*0: q = A p, 1: q = A x, true residual*/, int km,
                 void* stream);
-int launch_update(const BatchDev& B, int total, int mode, int km, void* stream);
+// gslot: the gamma slot (0 or 1) the ITER mode reads for alpha = gamma / (p, q)
+int launch_update(const BatchDev& B, int total, int mode, int km, int gslot, void* stream);
 int launch_local(const BatchDev& B, int slot, int total, int smem_bytes, void* stream);
 int launch_coarse(const BatchDev& B, int total, int km, void* stream);
 // element-block local solves z_e = inv(A_ee) r_e with the partial (r, z) per chunk item
@@ -134,8 +136,9 @@ int launch_unit_block(const int* sub_e0, int nsub, int np, int c0, int cb, long 
 // X_s[i][c0 + kk] = z[kk][d0_s + i] into the explicit inverses (FP64 if fp64, else FP32); nmax = largest n_s
 int launch_dli_store(int fp64, const int* sub_e0, int nsub, int np, const long long* off, int c0, int cb,
                      long long ndof, const double* z, void* X, int nmax, void* stream);
-// nonnested: some problem of the batch has a non-nested coarse space
-int launch_pupdate(const BatchDev& B, int total, int mode, int km, int nonnested, void* stream);
+// nonnested: some problem of the batch has a non-nested coarse space; wslot: the gamma slot this launch writes
+// (the ITER mode reads the other one for beta)
+int launch_pupdate(const BatchDev& B, int total, int mode, int km, int nonnested, int wslot, void* stream);
 // r_0 = R_0 r for non-nested coarse spaces: one CTA per coarse cell (prefix slot K_RNN)
 int launch_restrict_nn(const BatchDev& B, int total, int km, void* stream);
 int launch_finish(const BatchDev& B, int total, int operand /*0: x, 1: p*/, void* stream);

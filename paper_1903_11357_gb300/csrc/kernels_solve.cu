@@ -77,6 +77,46 @@ __device__ __forceinline__ double warp_sum_strided(const double* v, int n, int s
   return warp_sum(s);
 }
 
+// Sums of the per-item partials v[i * k + kk] (i < n) for every kk < k, formed by the whole CTA in a fixed
+// order (thread-strided sums, a fixed shuffle tree in each warp, then the warps in order) and returned in
+// out[0..k) (shared) to every thread.  Every CTA that calls it on the same partials gets the same bits, so a
+// scalar such as alpha = gamma / (p, q) is formed where it is used instead of by a last CTA of the kernel
+// that produced the partials.
+template <int KM, int NTB>
+__device__ void block_sum_items(const double* __restrict__ v, int n, int k, double (*red)[KMAX], double* out) {
+  constexpr int U = KM == 1 ? 8 : 1;   // loads in flight per thread and pass
+  double s[KM];
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk) s[kk] = 0.0;
+  for (int i0 = threadIdx.x; i0 < n; i0 += U * NTB) {
+    double t[U][KM];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * NTB;
+#pragma unroll
+      for (int kk = 0; kk < KM; ++kk) t[u][kk] = (i < n && kk < k) ? v[(long long)i * k + kk] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int kk = 0; kk < KM; ++kk) s[kk] += t[u][kk];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk) {
+    if (kk >= k) break;
+    const double t = warp_sum(s[kk]);
+    if (lane == 0) red[w][kk] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double t = 0.0;
+    for (int ww = 0; ww < NTB / 32; ++ww) t += red[ww][threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
 // returns true in the last CTA of this kernel for problem P (all CTAs must call it exactly once)
 __device__ bool last_block(unsigned int* counter, unsigned int n_items, int* flag_smem) {
   __threadfence();
@@ -164,31 +204,23 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv(BatchDev B, int operand, 
   if (any) spmv_rows<NP, KM>(P, item, operand, act, part);
   block_sum_k<KM, SW>(part, k, red, tot);
   if (threadIdx.x < k) P.part_pq[(long long)item * k + threadIdx.x] = tot[threadIdx.x];
+  // q = A p: the x/r update that follows sums the (p, q) partials itself (alpha in every CTA), so this
+  // kernel ends without a last-CTA step
+  if (operand == 0) return;
   if (!last_block(&P.counters[C_SPMV], P.n_spmv_items, &lastf)) return;
   for (int kk = threadIdx.x >> 5; kk < k; kk += SW) {
     if (!act[kk]) continue;
     const double s = warp_sum_strided(P.part_pq + kk, P.n_spmv_items, k);
-    if ((threadIdx.x & 31) != 0) continue;
-    if (operand == 1) {
-      P.true_rr[kk] = P.bnorm[kk] > 0.0 ? sqrt(s) / P.bnorm[kk] : 0.0;
-      continue;
-    }
-    double alpha = P.gamma[kk] / s;
-    if (!(s > 0.0) || !finite_d(alpha)) {
-      P.status[kk] = DGASM_ENAN;
-      P.done[kk] = 3;
-      atomicSub(P.remaining, 1);
-      alpha = 0.0;
-    }
-    P.alpha[kk] = alpha;
+    if ((threadIdx.x & 31) == 0) P.true_rr[kk] = P.bnorm[kk] > 0.0 ? sqrt(s) / P.bnorm[kk] : 0.0;
   }
 }
 
 // ---- x/r update (or initial residual) with partial ||r||^2 and the coarse restriction ----------
 template <int KM>
-__global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
+__global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode, int gslot) {
   __shared__ double red4[UPD_NW][KMAX][4];
   __shared__ double red[UPD_NW * KMAX];
+  __shared__ double red8[UPD_NW][KMAX];
   __shared__ double tot[KMAX];
   __shared__ int lastf;
   __shared__ __align__(16) ProbDev Ps;
@@ -203,10 +235,38 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
     act[kk] = kk < k && P.done[kk] == 0;
     any |= act[kk];
   }
+  // alpha = gamma / (p, q) from the SpMV's partial sums, formed identically in every CTA; a right-hand side
+  // whose (p, q) is not positive or whose alpha is not finite is left alone here and failed by the last CTA
   double alpha[KM];
+  bool bad[KM];
 #pragma unroll
-  for (int kk = 0; kk < KM; ++kk) alpha[kk] = (mode == MODE_ITER && act[kk]) ? P.alpha[kk] : 0.0;
+  for (int kk = 0; kk < KM; ++kk) {
+    alpha[kk] = 0.0;
+    bad[kk] = false;
+  }
+  // loads that do not depend on the sums below are issued before them
   const int g0 = P.grp_ptr[g], g1 = P.grp_ptr[g + 1];
+  double gam[KM];
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk) gam[kk] = (mode == MODE_ITER && kk < k) ? (gslot ? P.gamma1 : P.gamma)[kk] : 0.0;
+  if (mode == MODE_ITER) {
+    block_sum_items<KM, UPD_THREADS>(P.part_pq, P.n_spmv_items, k, red8, tot);
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) {
+      if (!act[kk]) continue;
+      const double spq = tot[kk];
+      const double a = gam[kk] / spq;
+      if (!(spq > 0.0) || !finite_d(a)) {
+        bad[kk] = true;
+        act[kk] = false;
+      } else {
+        alpha[kk] = a;
+      }
+    }
+    any = false;
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) any |= act[kk];
+  }
   const int nd = (g1 - g0) * np;
   // one pass: x/r update, ||r||^2 and, for q = 1 (nq = 3), the restriction r_0[J] = sum R0T^T r
   constexpr int NQ1 = 3;
@@ -221,27 +281,33 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
   const bool restrict_ = nq > 0 && P.r0t_ptr == nullptr;
   const bool fused_r0 = restrict_ && nq == NQ1;
   if (mode == MODE_ITER) {
-    // the CG update, two dofs per thread and pass, every load of both issued before the stores; each thread
-    // still accumulates its dofs t, t + UPD_THREADS, t + 2 UPD_THREADS, ... in that order
-    for (int t0 = threadIdx.x; t0 < nd && any; t0 += 2 * UPD_THREADS) {
-      long long dv[2];
-      bool ok[2];
-      double w2[2][NQ1];
+    // the CG update, H dofs per thread and pass (all index loads, then all data loads of the pass, issued
+    // before the stores); each thread still accumulates its dofs t, t + UPD_THREADS, t + 2 UPD_THREADS, ...
+    // in that order
+    constexpr int H = KM == 1 ? 4 : 2;
+    for (int t0 = threadIdx.x; t0 < nd && any; t0 += H * UPD_THREADS) {
+      long long dv[H];
+      bool ok[H];
+      double w2[H][NQ1];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < H; ++h) {
         const int t = t0 + h * UPD_THREADS;
         ok[h] = t < nd;
-        const int tt = ok[h] ? t : t0;
-        dv[h] = (long long)P.grp_elems[g0 + tt / np] * np + tt % np;
+        dv[h] = P.grp_elems[g0 + (ok[h] ? t : t0) / np];
+      }
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const int tt = ok[h] ? t0 + h * UPD_THREADS : t0;
+        dv[h] = dv[h] * np + tt % np;
 #pragma unroll
         for (int c = 0; c < NQ1; ++c) w2[h][c] = fused_r0 ? P.r0t[dv[h] * NQ1 + c] : 0.0;
       }
 #pragma unroll
       for (int kk = 0; kk < KM; ++kk) {
         if (!act[kk]) continue;
-        double xv[2], pv[2], qv[2], rv0[2];
+        double xv[H], pv[H], qv[H], rv0[H];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < H; ++h) {
           const long long o = kk * (long long)P.ndof + dv[h];
           xv[h] = P.x[o];
           pv[h] = P.p[o];
@@ -249,7 +315,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
           rv0[h] = P.r[o];
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < H; ++h) {
           if (!ok[h]) continue;
           const long long o = kk * (long long)P.ndof + dv[h];
           P.x[o] = fma(alpha[kk], pv[h], xv[h]);
@@ -338,6 +404,15 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
   if (!last_block(&P.counters[C_GRP], P.ngrp, &lastf)) return;
   if ((threadIdx.x >> 5) < k) {
     const int kk = threadIdx.x >> 5;
+    if (bad[kk]) {
+      if ((threadIdx.x & 31) == 0) {
+        P.alpha[kk] = 0.0;
+        P.status[kk] = DGASM_ENAN;
+        P.done[kk] = 3;
+        atomicSub(P.remaining, 1);
+      }
+      return;
+    }
     if (!act[kk]) return;
     const double s = warp_sum_strided(P.part_rr + kk, P.ngrp, k);
     if ((threadIdx.x & 31) != 0) return;
@@ -374,7 +449,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode) {
     const int it = P.iters[kk] + 1;
     P.iters[kk] = it;
     P.relres[kk] = rel;
-    if (it <= P.maxit) P.alpha_hist[(long long)kk * P.maxit + it - 1] = P.alpha[kk];
+    P.alpha[kk] = alpha[kk];
+    if (it <= P.maxit) P.alpha_hist[(long long)kk * P.maxit + it - 1] = alpha[kk];
     int newdone = 0;
     if (!finite_d(rel)) { P.status[kk] = DGASM_ENAN; newdone = 3; }
     else if (P.fixed_iters > 0) { if (it >= P.fixed_iters) newdone = 1; }
@@ -488,10 +564,9 @@ __global__ void __launch_bounds__(NTHREADS) k_bjac(BatchDev B) {
 // NN: the batch holds a non-nested coarse space (prolongation over (element, coarse cell) pairs); the
 // instantiation without it keeps the agglomerate path lean
 template <int KM, bool NN>
-__global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
+__global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode, int wslot) {
   __shared__ double beta_s[KMAX];
   __shared__ double gnew_s[KMAX];
-  __shared__ int lastf;
   __shared__ __align__(16) ProbDev Ps;
   const int pi = find_prob(B.prefix[K_SPMV], B.nprob, blockIdx.x);
   const ProbDev& P = stage_prob(B.probs + pi, &Ps);
@@ -504,6 +579,40 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
     act[kk] = kk < k && P.done[kk] == 0;
     any |= act[kk];
   }
+  // the element's data first (none of it depends on beta): z, the old p and, for coarse degree 1 with
+  // agglomerates, z + R_0^T z_0 itself
+  constexpr int NQ1 = 3;
+  const int e_begin = item * P.epi;
+  const int nel = min(P.epi, P.ne - e_begin);
+  const int t = threadIdx.x;
+  const bool mine = any && t < nel * np;
+  const bool nn = NN && nq > 0 && P.r0t_ptr != nullptr;
+  const bool fast = !nn && nq == NQ1;
+  const int e = e_begin + (mine ? t / np : 0), a = mine ? t % np : 0;
+  const long long d = (long long)e * np + a;
+  double zv[KM], pv[KM];
+#pragma unroll
+  for (int kk = 0; kk < KM; ++kk) {
+    zv[kk] = pv[kk] = 0.0;
+    if (mine && kk < k) {
+      const long long o = kk * (long long)P.ndof + d;
+      zv[kk] = P.z[o];
+      pv[kk] = P.p[o];
+    }
+  }
+  if (mine && fast) {
+    const int J = P.agg_int[e];
+    double R[NQ1];
+#pragma unroll
+    for (int c = 0; c < NQ1; ++c) R[c] = P.r0t[d * NQ1 + c];
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) {
+      if (kk >= k) break;
+      const double* z0 = P.z0 + (long long)kk * P.n0 + J * NQ1;
+#pragma unroll
+      for (int c = 0; c < NQ1; ++c) zv[kk] = fma(R[c], z0[c], zv[kk]);
+    }
+  }
   if ((threadIdx.x >> 5) < k) {
     const int kk = threadIdx.x >> 5;
     double g = 0.0;
@@ -513,41 +622,34 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
     }
     if ((threadIdx.x & 31) == 0) {
       gnew_s[kk] = g;
-      beta_s[kk] = (mode == MODE_INIT || !act[kk]) ? 0.0 : g / P.gamma[kk];
+      beta_s[kk] = (mode == MODE_INIT || !act[kk]) ? 0.0 : g / (wslot ? P.gamma : P.gamma1)[kk];
     }
   }
   __syncthreads();
-  if (any) {
-    const int e_begin = item * P.epi;
-    const int nel = min(P.epi, P.ne - e_begin);
-    const int t = threadIdx.x;
-    if (t < nel * np) {
-      const int e = e_begin + t / np, a = t % np;
-      const long long d = (long long)e * np + a;
-      const bool nn = NN && nq > 0 && P.r0t_ptr != nullptr;
-      const int J = nq > 0 && !nn ? P.agg_int[e] : 0;
+  if (mine) {
 #pragma unroll
-      for (int kk = 0; kk < KM; ++kk) {
-        if (!act[kk]) continue;
-        const long long o = kk * (long long)P.ndof + d;
-        double zv = P.z[o];
-        if (nn) {
-          // non-nested: every coarse cell that meets the element, in ascending order
-          for (int t = P.r0t_ptr[e]; t < P.r0t_ptr[e + 1]; ++t) {
-            const double* R = P.r0t + ((long long)t * np + a) * nq;
-            const double* z0 = P.z0 + (long long)kk * P.n0 + (long long)P.r0t_col[t] * nq;
-            for (int c = 0; c < nq; ++c) zv = fma(R[c], z0[c], zv);
-          }
-        } else if (nq > 0) {
-          const double* R = P.r0t + d * nq;
-          const double* z0 = P.z0 + (long long)kk * P.n0 + J * nq;
-          for (int c = 0; c < nq; ++c) zv = fma(R[c], z0[c], zv);
+    for (int kk = 0; kk < KM; ++kk) {
+      if (!act[kk]) continue;
+      const long long o = kk * (long long)P.ndof + d;
+      double z = zv[kk];
+      if (nn) {
+        // non-nested: every coarse cell that meets the element, in ascending order
+        for (int u = P.r0t_ptr[e]; u < P.r0t_ptr[e + 1]; ++u) {
+          const double* R = P.r0t + ((long long)u * np + a) * nq;
+          const double* z0 = P.z0 + (long long)kk * P.n0 + (long long)P.r0t_col[u] * nq;
+          for (int c = 0; c < nq; ++c) z = fma(R[c], z0[c], z);
         }
-        P.p[o] = (mode == MODE_INIT) ? zv : fma(beta_s[kk], P.p[o], zv);
+      } else if (nq > 0 && !fast) {
+        const double* R = P.r0t + d * nq;
+        const double* z0 = P.z0 + (long long)kk * P.n0 + P.agg_int[e] * nq;
+        for (int c = 0; c < nq; ++c) z = fma(R[c], z0[c], z);
       }
+      P.p[o] = (mode == MODE_INIT) ? z : fma(beta_s[kk], pv[kk], z);
     }
   }
-  if (!last_block(&P.counters[C_PUPD], P.n_chunk_items, &lastf)) return;
+  // the new gamma goes to the other slot, so no CTA of this launch can read it in place of the old one: the
+  // first item records it (every item formed the same sum) and no last-CTA step is needed
+  if (item != 0) return;
   if (threadIdx.x < k) {
     const int kk = threadIdx.x;
     if (!act[kk]) return;
@@ -556,7 +658,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pupdate(BatchDev B, int mode) {
       const int it = P.iters[kk];
       if (it >= 1 && it <= P.maxit) P.beta_hist[(long long)kk * P.maxit + it - 1] = beta_s[kk];
     }
-    P.gamma[kk] = g;
+    (wslot ? P.gamma1 : P.gamma)[kk] = g;
     if (!finite_d(g) || !(g > 0.0)) {
       P.status[kk] = DGASM_ENAN;
       P.done[kk] = 3;
@@ -663,9 +765,9 @@ int launch_spmv(const BatchDev& B, int p, int total, int operand, int km, void* 
                  : launch_spmv_k<KMAX>(B, p, total, operand, (cudaStream_t)st);
 }
 
-int launch_update(const BatchDev& B, int total, int mode, int km, void* st) {
-  if (km == 1) k_update<1><<<total, UPD_THREADS, 0, (cudaStream_t)st>>>(B, mode);
-  else k_update<KMAX><<<total, UPD_THREADS, 0, (cudaStream_t)st>>>(B, mode);
+int launch_update(const BatchDev& B, int total, int mode, int km, int gslot, void* st) {
+  if (km == 1) k_update<1><<<total, UPD_THREADS, 0, (cudaStream_t)st>>>(B, mode, gslot);
+  else k_update<KMAX><<<total, UPD_THREADS, 0, (cudaStream_t)st>>>(B, mode, gslot);
   return (int)cudaGetLastError();
 }
 
@@ -681,14 +783,14 @@ int launch_bjac(const BatchDev& B, int total, int km, void* st) {
   return (int)cudaGetLastError();
 }
 
-int launch_pupdate(const BatchDev& B, int total, int mode, int km, int nonnested, void* st) {
+int launch_pupdate(const BatchDev& B, int total, int mode, int km, int nonnested, int wslot, void* st) {
   cudaStream_t s = (cudaStream_t)st;
   if (nonnested) {
-    if (km == 1) k_pupdate<1, true><<<total, NTHREADS, 0, s>>>(B, mode);
-    else k_pupdate<KMAX, true><<<total, NTHREADS, 0, s>>>(B, mode);
+    if (km == 1) k_pupdate<1, true><<<total, NTHREADS, 0, s>>>(B, mode, wslot);
+    else k_pupdate<KMAX, true><<<total, NTHREADS, 0, s>>>(B, mode, wslot);
   } else {
-    if (km == 1) k_pupdate<1, false><<<total, NTHREADS, 0, s>>>(B, mode);
-    else k_pupdate<KMAX, false><<<total, NTHREADS, 0, s>>>(B, mode);
+    if (km == 1) k_pupdate<1, false><<<total, NTHREADS, 0, s>>>(B, mode, wslot);
+    else k_pupdate<KMAX, false><<<total, NTHREADS, 0, s>>>(B, mode, wslot);
   }
   return (int)cudaGetLastError();
 }

@@ -81,7 +81,7 @@ struct Engine {
   // per problem: 1 when all its right-hand sides are done; not_done_rhs counts the open ones
   int read_done(std::vector<int>& done, int* not_done_rhs);
  private:
-  int precond(int mode, EventPairs* ev);
+  int precond(int mode, EventPairs* ev, int wslot);   // wslot: the gamma slot the p update writes
   int spmv(int operand, EventPairs* ev);
 };
 
