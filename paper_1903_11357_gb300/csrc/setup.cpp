@@ -83,9 +83,10 @@ int factor_env(int prec, const Envelope& E, EnvBufs& D, void* Lr, int* err, cuda
 
 // From the factored tile pool Lf (row-major, diagonal tiles inverted): the super-row inverse blocks,
 // then the forward stream (column-major tiles) and the backward stream (row-major tiles) in the order
-// the triangular solves consume them.  Lf is released.
+// the triangular solves consume them.  Asynchronous on st: Lf and the temporaries go to `keep`, released
+// by the caller after the setup's final synchronisation.
 int build_streams(int fprec, const Envelope& E, EnvBufs& D, DevBuf& Lf, DevBuf& Lc, DevBuf& Lr, cudaStream_t st,
-                  int* nl) {
+                  int* nl, SetupTemps& keep) {
   const int fp = fprec == DGASM_FP64 ? 0 : 1;
   const size_t eb = fact_elem_bytes(fprec);
   const long long nf = (long long)E.fwd_src.size(), nb = (long long)E.bwd_src.size();
@@ -104,13 +105,14 @@ int build_streams(int fprec, const Envelope& E, EnvBufs& D, DevBuf& Lf, DevBuf& 
     DG_CUDA(launch_to_bf16(Sf.as<float>(), Lc.ptr, nf * TILE * TILE, st));
     DG_CUDA(launch_to_bf16(Sb.as<float>(), Lr.ptr, nb * TILE * TILE, st));
     *nl += 2;
-    DG_CUDA(cudaStreamSynchronize(st));
+    keep.add(std::move(Sf));
+    keep.add(std::move(Sb));
   } else {
-    DG_CUDA(cudaStreamSynchronize(st));
     Lc = std::move(Sf);
     Lr = std::move(Sb);
   }
-  Lf.reset();
+  keep.add(std::move(X));
+  keep.add(std::move(Lf));
   return DGASM_OK;
 }
 
@@ -166,14 +168,24 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
   return b;
 }
 
+// The coarse space (R_0^T, A_0 = R_0 A R_0^T, its factor and inverse) does not depend on the local factors:
+// it is issued on the side stream and runs beside the local factorisation.  Nothing is freed and no stream is
+// synchronised until all device work of the setup has been issued (a cudaFree waits for the whole device).
 int prec_build(dgasm_prec_s* pc) {
   dgasm_system_s* s = pc->sys;
   Plan& P = pc->P;
   EventPairs* ev = profiling() ? &pc->setup_ev : nullptr;
   if (ev) ev->reset();
   int nl = 0;
-  cudaStream_t st = pc->stream;
+  cudaStream_t st = pc->stream, cs = pc->side;
   const int ne = P.ne, np = P.np, np2s = s->np2s;
+  SetupTemps keep;
+  DevBuf Lf;  // factorisation pool (row-major)
+  // on every return, the work issued on both streams finishes before keep and Lf are freed
+  struct Drain {
+    cudaStream_t a, b;
+    ~Drain() { cudaStreamSynchronize(a); cudaStreamSynchronize(b); }
+  } drain{st, cs};
   // plan arrays
   DG_TRY(upload(pc->perm, P.perm));
   DG_TRY(upload(pc->rowptr, P.rowptr));
@@ -193,8 +205,10 @@ int prec_build(dgasm_prec_s* pc) {
   nl += 2;
   DG_TRY(pc->scale.alloc(sizeof(double) * (size_t)ne * np));
   DG_CUDA(launch_scale(pc->rowptr.as<int>(), pc->col.as<int>(), pc->vals.as<double>(), ne, np, np2s, pc->scale.as<double>(), st));
-  // local factors
+  DG_CUDA(cudaEventRecord(pc->ev_fork, st));   // the permuted matrix is ready for the coarse stream
+  // local factors (stream st)
   pc->blocks = P.nsub == P.ne;
+  const int fprec = pc->precision;
   if (pc->blocks) {
     // every subdomain is one element: explicit FP64 inverses of the diagonal blocks
     DG_TRY(pc->dinv.alloc(sizeof(double) * (size_t)ne * np * np));
@@ -202,9 +216,7 @@ int prec_build(dgasm_prec_s* pc) {
                                 pc->dinv.as<double>(), pc->err.as<int>(), st));
     nl += 1;
   } else {
-    const int fprec = pc->precision;
     const size_t ftiles = (size_t)P.env.ntiles * TILE * TILE;
-    DevBuf Lf;  // factorisation pool (row-major)
     DG_TRY(Lf.alloc(ftiles * fact_elem_bytes(fprec)));
     DG_CUDA(cudaMemsetAsync(Lf.ptr, 0, Lf.bytes, st));
     DG_CUDA(launch_extract_rows(fprec == DGASM_FP64 ? 0 : 1, pc->env.dev, pc->sub_e0.as<int>(), pc->rowptr.as<int>(),
@@ -212,6 +224,61 @@ int prec_build(dgasm_prec_s* pc) {
                                 P.nsub, ne, st));
     nl += 1;
     DG_TRY(factor_env(fprec, P.env, pc->env, Lf.ptr, pc->err.as<int>(), st, ev, &nl));
+  }
+  // coarse space: R_0^T, A_0 = R_0 A R_0^T, FP64 factor and explicit inverse (stream cs)
+  int* coarse_err = nullptr;   // error word of the coarse inverse's bounded waits
+  if (pc->n0 > 0) {
+    DG_CUDA(cudaStreamWaitEvent(cs, pc->ev_fork, 0));
+    const int n0 = pc->n0, q = P.q, nq = P.nq, mq = (s->p + q + 2) / 2;
+    std::vector<double> gt, gw;
+    gauss_legendre01(mq, gt, gw);
+    DevBuf d_gt, d_gw, d_aggbox;
+    DG_TRY(upload(d_gt, gt));
+    DG_TRY(upload(d_gw, gw));
+    DG_TRY(upload(d_aggbox, P.agg_bbox));
+    DevBuf A0;
+    DG_TRY(A0.alloc(sizeof(double) * (size_t)n0 * n0));
+    if (P.nonnested) {
+      // R_0^T pairs from the plan; A_0 accumulated row block by row block on the device
+      DG_TRY(upload(pc->r0t, pc->nn.blocks));
+      DG_TRY(upload(pc->r0t_ptr, pc->nn.ptr));
+      DG_TRY(upload(pc->r0t_col, pc->nn.col));
+      DG_TRY(upload(pc->r0t_elem, pc->nn.elem));
+      DG_TRY(upload(pc->rT_ptr, pc->nn.tptr));
+      DG_TRY(upload(pc->rT_pair, pc->nn.tpair));
+      DG_CUDA(cudaMemsetAsync(A0.ptr, 0, A0.bytes, cs));
+      DG_CUDA(launch_galerkin_nn(pc->rowptr.as<int>(), pc->col.as<int>(), pc->vals.as<double>(), np, np2s, nq,
+                                 pc->r0t_ptr.as<int>(), pc->r0t_col.as<int>(), pc->r0t_elem.as<int>(), pc->r0t.as<double>(),
+                                 pc->rT_ptr.as<int>(), pc->rT_pair.as<int>(), P.nagg, n0, A0.as<double>(), cs));
+    } else {
+      DG_TRY(pc->r0t.alloc(sizeof(double) * (size_t)ne * np * nq));
+      DG_CUDA(launch_r0t(pc->perm.as<int>(), s->d_bbox.as<double>(), pc->agg_int.as<int>(), d_aggbox.as<double>(), ne,
+                         s->p, q, d_gt.as<double>(), d_gw.as<double>(), mq, pc->r0t.as<double>(), cs));
+      DevBuf W;
+      DG_TRY(W.alloc(sizeof(double) * P.col.size() * (size_t)nq * nq));
+      DG_CUDA(launch_galerkin(pc->grp_ptr.as<int>(), pc->grp_elems.as<int>(), pc->agg_int.as<int>(), pc->rowptr.as<int>(),
+                              pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), ne, (long long)P.col.size(),
+                              P.nagg, np, np2s, nq, W.as<double>(), A0.as<double>(), cs));
+      keep.add(std::move(W));
+    }
+    DG_TRY(upload_env(P.env0, pc->env0));
+    DevBuf scale0, Lr0, Lc0, Lb0;
+    DG_TRY(scale0.alloc(sizeof(double) * n0));
+    const size_t t0 = (size_t)P.env0.ntiles * TILE * TILE;
+    DG_TRY(Lr0.alloc(sizeof(double) * t0));
+    DG_CUDA(cudaMemsetAsync(Lr0.ptr, 0, Lr0.bytes, cs));
+    DG_CUDA(launch_coarse_extract(A0.as<double>(), n0, scale0.as<double>(), pc->env0.dev, Lr0.as<double>(), cs));
+    nl += 4;
+    DG_TRY(factor_env(DGASM_FP64, P.env0, pc->env0, Lr0.ptr, pc->err.as<int>() + 4, cs, ev, &nl));
+    DG_TRY(build_streams(DGASM_FP64, P.env0, pc->env0, Lr0, Lc0, Lb0, cs, &nl, keep));
+    // A_0^{-1} = columns of the local-solve kernel applied to the identity
+    DG_TRY(pc->A0inv.alloc(sizeof(double) * (size_t)n0 * n0));
+    DG_TRY(pc->coarse_inverse(scale0, Lb0, Lc0, cs, keep, &coarse_err));
+    nl += 3;
+    for (DevBuf* b : {&d_gt, &d_gw, &d_aggbox, &A0, &scale0, &Lb0, &Lc0}) keep.add(std::move(*b));
+    pc->nn = R0TPairs{};
+  }
+  if (!pc->blocks) {
     if (fprec == DGASM_TF32 || fprec == DGASM_BF16) {
       // breakdown of the tensor-core factorisation (a non-positive pivot): factorise again from A_i with the
       // FP32 CUDA-core updates
@@ -230,64 +297,22 @@ int prec_build(dgasm_prec_s* pc) {
       }
     }
     // super-row inverse blocks, then the forward (column-major) and backward (row-major) solve streams
-    DG_TRY(build_streams(fprec, P.env, pc->env, Lf, pc->Lc, pc->Lr, st, &nl));
+    DG_TRY(build_streams(fprec, P.env, pc->env, Lf, pc->Lc, pc->Lr, st, &nl, keep));
   }
-  // coarse space: R_0^T, A_0 = R_0 A R_0^T, FP64 factor and explicit inverse
   if (pc->n0 > 0) {
-    const int n0 = pc->n0, q = P.q, nq = P.nq, mq = (s->p + q + 2) / 2;
-    std::vector<double> gt, gw;
-    gauss_legendre01(mq, gt, gw);
-    DevBuf d_gt, d_gw, d_aggbox;
-    DG_TRY(upload(d_gt, gt));
-    DG_TRY(upload(d_gw, gw));
-    DG_TRY(upload(d_aggbox, P.agg_bbox));
-    DevBuf A0;
-    DG_TRY(A0.alloc(sizeof(double) * (size_t)n0 * n0));
-    if (P.nonnested) {
-      // R_0^T pairs from the plan; A_0 accumulated row block by row block on the device
-      DG_TRY(upload(pc->r0t, pc->nn.blocks));
-      DG_TRY(upload(pc->r0t_ptr, pc->nn.ptr));
-      DG_TRY(upload(pc->r0t_col, pc->nn.col));
-      DG_TRY(upload(pc->r0t_elem, pc->nn.elem));
-      DG_TRY(upload(pc->rT_ptr, pc->nn.tptr));
-      DG_TRY(upload(pc->rT_pair, pc->nn.tpair));
-      DG_CUDA(cudaMemsetAsync(A0.ptr, 0, A0.bytes, st));
-      DG_CUDA(launch_galerkin_nn(pc->rowptr.as<int>(), pc->col.as<int>(), pc->vals.as<double>(), np, np2s, nq,
-                                 pc->r0t_ptr.as<int>(), pc->r0t_col.as<int>(), pc->r0t_elem.as<int>(), pc->r0t.as<double>(),
-                                 pc->rT_ptr.as<int>(), pc->rT_pair.as<int>(), P.nagg, n0, A0.as<double>(), st));
-      pc->nn = R0TPairs{};
-    } else {
-      DG_TRY(pc->r0t.alloc(sizeof(double) * (size_t)ne * np * nq));
-      DG_CUDA(launch_r0t(pc->perm.as<int>(), s->d_bbox.as<double>(), pc->agg_int.as<int>(), d_aggbox.as<double>(), ne,
-                         s->p, q, d_gt.as<double>(), d_gw.as<double>(), mq, pc->r0t.as<double>(), st));
-      DevBuf W;
-      DG_TRY(W.alloc(sizeof(double) * P.col.size() * (size_t)nq * nq));
-      DG_CUDA(launch_galerkin(pc->grp_ptr.as<int>(), pc->grp_elems.as<int>(), pc->agg_int.as<int>(), pc->rowptr.as<int>(),
-                              pc->col.as<int>(), pc->vals.as<double>(), pc->r0t.as<double>(), ne, (long long)P.col.size(),
-                              P.nagg, np, np2s, nq, W.as<double>(), A0.as<double>(), st));
-    }
-    DG_TRY(upload_env(P.env0, pc->env0));
-    DevBuf scale0, Lr0, Lc0, Lb0;
-    DG_TRY(scale0.alloc(sizeof(double) * n0));
-    const size_t t0 = (size_t)P.env0.ntiles * TILE * TILE;
-    DG_TRY(Lr0.alloc(sizeof(double) * t0));
-    DG_CUDA(cudaMemsetAsync(Lr0.ptr, 0, Lr0.bytes, st));
-    DG_CUDA(launch_coarse_extract(A0.as<double>(), n0, scale0.as<double>(), pc->env0.dev, Lr0.as<double>(), st));
-    nl += 4;
-    DG_TRY(factor_env(DGASM_FP64, P.env0, pc->env0, Lr0.ptr, pc->err.as<int>() + 4, st, ev, &nl));
-    DG_TRY(build_streams(DGASM_FP64, P.env0, pc->env0, Lr0, Lc0, Lb0, st, &nl));
-    // A_0^{-1} = columns of the local-solve kernel applied to the identity
-    DG_TRY(pc->A0inv.alloc(sizeof(double) * (size_t)n0 * n0));
-    DG_TRY(pc->coarse_inverse(scale0, Lb0, Lc0));
-    nl += 3;
+    DG_CUDA(cudaEventRecord(pc->ev_join, cs));
+    DG_CUDA(cudaStreamWaitEvent(st, pc->ev_join, 0));
   }
   // check factorisation errors
   int herr[8];
+  int cerr = 0;
   DG_CUDA(cudaMemcpyAsync(herr, pc->err.ptr, sizeof(herr), cudaMemcpyDeviceToHost, st));
+  if (coarse_err) DG_CUDA(cudaMemcpyAsync(&cerr, coarse_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   DG_CUDA(cudaStreamSynchronize(st));
   if (herr[0]) return set_error(DGASM_ENOTSPD, "non-positive pivot in the Cholesky factor of subdomain %d at row %d", herr[1], herr[2]);
   if (herr[4]) return set_error(DGASM_ENOTSPD, "non-positive pivot in the Cholesky factor of the coarse operator A_0");
   if (herr[3]) return set_error(DGASM_ETIMEOUT, "a tensor-core trailing update did not complete within its wait limit");
+  if (cerr) return set_error(DGASM_ECUDA, "a bounded wait in the coarse inverse gave up (error word set)");
   if (ev) ev->accumulate();
   pc->setup_launches = nl;
   pc->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - pc->t_start).count();
@@ -331,9 +356,9 @@ dgasm_prec_s::~dgasm_prec_s() {
   if (ev_join) cudaEventDestroy(ev_join);
 }
 
-int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
+// asynchronous on st; its temporaries go to `keep`, and *err_word is the device word its bounded waits set
+int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0, cudaStream_t st, SetupTemps& keep, int** err_word) {
   const int n0 = this->n0;
-  cudaStream_t st = stream;
   // a one-subdomain problem with n0 right-hand sides: the unit vectors
   DevBuf ident, sub_e0c, misc, probs, prefix;
   DG_TRY(ident.alloc(sizeof(double) * (size_t)n0 * n0));
@@ -372,10 +397,8 @@ int dgasm_prec_s::coarse_inverse(DevBuf& scale0, DevBuf& Lr0, DevBuf& Lc0) {
   const int slot = K_NKINDS + 2 * DGASM_FP64 + 1;
   B.prefix[slot] = prefix.as<int>();
   DG_CUDA(launch_local(B, slot, chunks, local_smem_bytes(DGASM_FP64, n0, KC), st));
-  int herr = 0;
-  DG_CUDA(cudaMemcpyAsync(&herr, B.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  DG_CUDA(cudaStreamSynchronize(st));
-  if (herr) return set_error(DGASM_ECUDA, "a bounded wait in the coarse inverse gave up (error word set)");
+  *err_word = B.err;
+  for (DevBuf* b : {&ident, &sub_e0c, &misc, &probs, &prefix}) keep.add(std::move(*b));
   return DGASM_OK;
 }
 

@@ -15,6 +15,13 @@
 
 namespace dgasm {
 
+// Device buffers of a setup whose work may still be in flight, released together after the setup's final
+// synchronisation (freeing one earlier would wait for the whole device).
+struct SetupTemps {
+  std::vector<DevBuf> bufs;
+  void add(DevBuf&& b) { bufs.push_back(std::move(b)); }
+};
+
 struct EnvBufs {
   DevBuf ndof, sub_trow, trow_F, trow_ptr, diag_task, panel_task, upd_task, tc_task, bwd_src, fwd_src, fwd_ptr, bwd_ptr,
       dinv_task, dinv_ptr, sub_sr, fwd_run, bwd_run;
@@ -132,7 +139,8 @@ struct dgasm_prec_s {
   std::unique_ptr<dgasm::Engine> engine;  // reused by dgasm_solve
   std::mutex mu;
   int init_streams(void* user_stream);
-  int coarse_inverse(dgasm::DevBuf& scale0, dgasm::DevBuf& Lr0, dgasm::DevBuf& Lc0);
+  int coarse_inverse(dgasm::DevBuf& scale0, dgasm::DevBuf& Lr0, dgasm::DevBuf& Lc0, cudaStream_t st,
+                     dgasm::SetupTemps& keep, int** err_word);
   size_t footprint() const;
   ~dgasm_prec_s();
 };
