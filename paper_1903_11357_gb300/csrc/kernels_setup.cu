@@ -119,26 +119,41 @@ __global__ void __launch_bounds__(256) k_chol_diag(EnvDev E, S* __restrict__ L, 
   // when nothing reads it any more (row T - 1 after the loop).  Eight threads share a row (u_r computed once
   // and shuffled); the thread that updates a_(j+1)(j+1) forms the next pivot's rd.  L itself is not stored: the
   // tile receives X = inv(L_KK), and only the pivots of A are read again.
-  const int r = tid >> 3, sub = tid & 7;
+  // The FP64 pipe spends its slots on a warp instruction whatever its active lanes, so work that a whole warp
+  // (rows 4w .. 4w + 3) or a whole column group m of a warp would skip is branched around, not predicated.
+  const int r = tid >> 3, sub = tid & 7, w = tid >> 5, rlo = 4 * w, rhi = 4 * w + 3;
   C rd_prev = (C)0;
   for (int j = 0; j < T; ++j) {
     const C rd = rdbuf[j & 1];
-    C u = (C)0;
-    if (sub == 0) u = a[r][j] * (rd * rd);
-    u = __shfl_sync(0xffffffffu, u, (tid & 31) & ~7);
+    if (j <= rhi + 1) {   // some row of this warp changes in step j (rows above j - 1 are final)
+      const bool upd = rhi > j;   // a row of this warp lies below the pivot
+      C u = (C)0;
+      if (upd) {
+        if (sub == 0) u = a[r][j] * (rd * rd);
+        u = __shfl_sync(0xffffffffu, u, (tid & 31) & ~7);
+      }
 #pragma unroll
-    for (int m = 0; m < T / 8; ++m) {
-      const int c = sub + 8 * m;
-      if (c > j && r >= c) {
-        a[r][c] -= u * a[c][j];
-        if (r == j + 1 && c == j + 1) {
-          C d = a[r][c];
-          if (!(d > (C)0)) { if (bad < 0) bad = j + 1; d = (C)1; }
-          rdbuf[(j + 1) & 1] = crsqrt<C>(d);
+      for (int m = 0; m < T / 8; ++m) {
+        const int c = sub + 8 * m;
+        // column group m of this warp: entries (r, c) with c > j, r >= c exist; entries c <= j < r exist;
+        // row j - 1 of X is in this warp
+        if (upd && max(8 * m, j + 1) <= min(8 * m + 7, rhi)) {
+          if (c > j && r >= c) {
+            a[r][c] -= u * a[c][j];
+            if (r == j + 1 && c == j + 1) {
+              C d = a[r][c];
+              if (!(d > (C)0)) { if (bad < 0) bad = j + 1; d = (C)1; }
+              rdbuf[(j + 1) & 1] = crsqrt<C>(d);
+            }
+          }
+        }
+        if (upd && 8 * m <= j) {
+          if (r > j && c <= j) inv[r][c] -= u * inv[j][c];
+          else if (j > 0 && r == j - 1 && c <= r) inv[r][c] *= rd_prev;
+        } else if (j > 0 && j - 1 >= rlo && j - 1 <= rhi && 8 * m <= j - 1) {
+          if (r == j - 1 && c <= r) inv[r][c] *= rd_prev;
         }
       }
-      if (r > j && c <= j) inv[r][c] -= u * inv[j][c];
-      else if (j > 0 && r == j - 1 && c <= r) inv[r][c] *= rd_prev;
     }
     rd_prev = rd;
     __syncthreads();
@@ -200,6 +215,21 @@ __global__ void __launch_bounds__(256) k_chol_update(EnvDev E, S* __restrict__ L
     Y[t / T][t % T] = (C)Lj[t];
   }
   __syncthreads();
+  if (I == J) {
+    // a diagonal target: only its lower triangle is read again, so its 528 entries r >= c (enumerated row by
+    // row) are spread over the threads and whole warps go idle instead of predicated-off lanes
+    constexpr int NLT = T * (T + 1) / 2;
+    for (int e = threadIdx.x; e < NLT; e += blockDim.x) {
+      int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+      if (r * (r + 1) / 2 > e) --r;
+      if ((r + 1) * (r + 2) / 2 <= e) ++r;
+      const int c = e - r * (r + 1) / 2;
+      C acc = 0;
+      for (int m = 0; m < T; ++m) acc += X[r][m] * Y[c][m];
+      Cij[r * T + c] = (S)((C)Cij[r * T + c] - acc);
+    }
+    return;
+  }
   // each thread owns 4 entries of one column c: rows r0, r0+8, r0+16, r0+24
   int c = threadIdx.x % T, r0 = threadIdx.x / T;
   C acc[4] = {0, 0, 0, 0};
