@@ -34,7 +34,9 @@ N_ELEM, SEED, P_DEG, NSUB, NCOARSE, P_C, CONTRAST = 16384, 2, 3, 64, 256, 1, 1e4
 WORKLOAD = ("16384 Lloyd-relaxed Voronoi cells of (0,1)^2 (seed 2, 20 Lloyd steps), SIPG p=3 (163840 dofs), "
             "C_sigma=10, 64 RCB subdomains (~2560 dofs), 256 RCB agglomerates at p_c=1, rho=1e4 on a 4x4 "
             "checkerboard of subdomains; f = 2 pi^2 sin(pi x) sin(pi y); rtol 1e-8 from x0=0")
-FP64_PEAK_FLOPS_PER_CLK = 152 * 2 * 2   # 152 SMs x 2 DFMA/clk (measured issue rate) x 2 flop
+# nominal FP64 issue rate (1/64 of the FP32 rate): 2 FMA per clock per SM; the roofline uses the rate the
+# library's probe measures (dgasm_probe_fp64: about 1.68 FMA per clock per SM with every sub-partition busy)
+FP64_NOMINAL_FMA_PER_CLK_SM = 2.0
 # DRAM bytes (read + write) per stream tile of the FP64 local-solve kernel, from one ncu capture of the
 # headline workload's launch (615.8 MB for 74087 tiles); valid only for the kernel source it was taken on
 LOCAL_TRAFFIC = {"sha256": "dd12d7c7069094093c9801a4ad85cb01dfb5fe167d8c84b1fbf30787c96a9b65",
@@ -876,7 +878,10 @@ def main():
         return
     peaks = read_peaks()
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = FP64_PEAK_FLOPS_PER_CLK * sm_max * 1e6 / 1e12
+    # FP64 peak: SMs x the measured FMA issue rate per SM and clock x 2 flop x the maximum SM clock
+    nsm, fma_clk_sm, probe_tflops = dg.probe_fp64()
+    fp64_peak = nsm * fma_clk_sm * 2 * sm_max * 1e6 / 1e12
+    fp64_nominal = nsm * FP64_NOMINAL_FMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
     # roofline of the dominant kernel (largest device time in the breakdown step), its launches timed in a
     # separate pass of the same steps
     dom_ms, dom_n = prof[dom]
@@ -899,7 +904,10 @@ def main():
             "peak": fp64_peak, "unit": "TFLOP/s", "frac": (flops / avg_s / 1e12 / fp64_peak) if flops else None,
             "traffic": local_traffic(tiles) if dom == "local" else None, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
             "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
-            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (issue rate measured by an FMA probe)"}
+            "peak_source": (f"FP64: {nsm} SMs x {fma_clk_sm:.3f} FMA/clk/SM (dgasm_probe_fp64, measured in this run) x 2 "
+                            f"flop x max SM clock {sm_max:.0f} MHz; the probe itself ran at {probe_tflops:.3f} TFLOP/s"),
+            "peak_nominal_2_fma_per_clk": fp64_nominal,
+            "frac_vs_nominal": (flops / avg_s / 1e12 / fp64_nominal) if flops else None}
     if dom == "local" and args.precision != "fp64":
         # lower-precision local factors: the sweeps stream 1024 entries of 4 (FP32) or 2 (BF16) bytes per tile
         eb = 2 if args.precision == "bf16" else 4

@@ -152,6 +152,13 @@ int dgasm_system_destroy(dgasm_system_t s);
  * Asynchronous on the stream; y is bitwise identical to dgasm_system_spmv's. */
 int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, double* y, double* xAx, void* stream);
 
+/* FP64 FMA issue-rate probe (the paper has no counterpart; measurement support for the roofline of the FP64
+ * kernels).  Runs one CTA of 512 threads per SM on the current device, each thread 8 independent FP64 FMA
+ * chains, and reports *nsm (SM count), *fma_per_clk_per_sm (FMA per clock per SM, median SM, from the CTAs'
+ * clock64 cycles) and *tflops (the GPU-wide FP64 FMA rate at the clock the launch ran at, from CUDA events).
+ * Synchronous (default stream); allocates a few KB.  Errors: DGASM_EINVAL (NULL argument), DGASM_ECUDA. */
+int dgasm_probe_fp64(int* nsm, double* fma_per_clk_per_sm, double* tflops);
+
 /* ---- Failure detection self-test (no counterpart in the paper) --------------------------------------
  * Every wait inside the library's kernels (ring slots, the CTA pair's exchange) is bounded: past its limit
  * it sets the batch error word, stops waiting and lets the kernel return, and the host reports

@@ -119,6 +119,7 @@ def lib():
             "dgasm_server_stats": [vp, i64p, i64p, i64p, i64p],
             "dgasm_server_destroy": [vp],
             "dgasm_system_spmv_dot_noalloc": [vp, vp, vp, vp, vp],
+            "dgasm_probe_fp64": [ip, dp, dp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -540,3 +541,12 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def probe_fp64():
+    """FP64 FMA issue rate of the current device (dgasm_probe_fp64): (SM count, FMA per clock per SM, TFLOP/s)."""
+    n = C.c_int()
+    r = C.c_double()
+    t = C.c_double()
+    check(lib().dgasm_probe_fp64(C.byref(n), C.byref(r), C.byref(t)))
+    return n.value, r.value, t.value
