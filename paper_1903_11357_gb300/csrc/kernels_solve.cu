@@ -77,46 +77,6 @@ __device__ __forceinline__ double warp_sum_strided(const double* v, int n, int s
   return warp_sum(s);
 }
 
-// Sums of the per-item partials v[i * k + kk] (i < n) for every kk < k, formed by the whole CTA in a fixed
-// order (thread-strided sums, a fixed shuffle tree in each warp, then the warps in order) and returned in
-// out[0..k) (shared) to every thread.  Every CTA that calls it on the same partials gets the same bits, so a
-// scalar such as alpha = gamma / (p, q) is formed where it is used instead of by a last CTA of the kernel
-// that produced the partials.
-template <int KM, int NTB>
-__device__ void block_sum_items(const double* __restrict__ v, int n, int k, double (*red)[KMAX], double* out) {
-  constexpr int U = KM == 1 ? 8 : 1;   // loads in flight per thread and pass
-  double s[KM];
-#pragma unroll
-  for (int kk = 0; kk < KM; ++kk) s[kk] = 0.0;
-  for (int i0 = threadIdx.x; i0 < n; i0 += U * NTB) {
-    double t[U][KM];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * NTB;
-#pragma unroll
-      for (int kk = 0; kk < KM; ++kk) t[u][kk] = (i < n && kk < k) ? v[(long long)i * k + kk] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int kk = 0; kk < KM; ++kk) s[kk] += t[u][kk];
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int kk = 0; kk < KM; ++kk) {
-    if (kk >= k) break;
-    const double t = warp_sum(s[kk]);
-    if (lane == 0) red[w][kk] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < k) {
-    double t = 0.0;
-    for (int ww = 0; ww < NTB / 32; ++ww) t += red[ww][threadIdx.x];
-    out[threadIdx.x] = t;
-  }
-  __syncthreads();
-}
-
 // returns true in the last CTA of this kernel for problem P (all CTAs must call it exactly once)
 __device__ bool last_block(unsigned int* counter, unsigned int n_items, int* flag_smem) {
   __threadfence();
@@ -218,10 +178,11 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv(BatchDev B, int operand, 
 // ---- x/r update (or initial residual) with partial ||r||^2 and the coarse restriction ----------
 template <int KM>
 __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode, int gslot) {
-  __shared__ double red4[UPD_NW][KMAX][4];
   __shared__ double red[UPD_NW * KMAX];
-  __shared__ double red8[UPD_NW][KMAX];
   __shared__ double tot[KMAX];
+  __shared__ double alpha_s[KMAX];
+  __shared__ int bad_s[KMAX];
+  __shared__ double colbuf[4][UPD_THREADS];   // per-thread values of up to four sums at a time
   __shared__ int lastf;
   __shared__ __align__(16) ProbDev Ps;
   const int pi = find_prob(B.prefix[K_GRP], B.nprob, blockIdx.x);
@@ -246,21 +207,40 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode, in
   }
   // loads that do not depend on the sums below are issued before them
   const int g0 = P.grp_ptr[g], g1 = P.grp_ptr[g + 1];
-  double gam[KM];
-#pragma unroll
-  for (int kk = 0; kk < KM; ++kk) gam[kk] = (mode == MODE_ITER && kk < k) ? (gslot ? P.gamma1 : P.gamma)[kk] : 0.0;
+  // FP64 instructions are scarce on this part (each warp instruction costs the pipe the same whatever its
+  // active lanes), so one warp per right-hand side sums the (p, q) partials and one lane divides
   if (mode == MODE_ITER) {
-    block_sum_items<KM, UPD_THREADS>(P.part_pq, P.n_spmv_items, k, red8, tot);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n = P.n_spmv_items;
+    for (int kk = wid; kk < k; kk += UPD_NW) {
+      double sum = 0.0;
+      for (int i0 = lane; i0 < n; i0 += 8 * 32) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + 32 * u;
+          v[u] = i < n ? P.part_pq[(long long)i * k + kk] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum += v[u];
+      }
+      sum = warp_sum(sum);
+      if (lane == 0) {
+        const double a = (gslot ? P.gamma1 : P.gamma)[kk] / sum;
+        const int b = !(sum > 0.0) || !finite_d(a);
+        alpha_s[kk] = b ? 0.0 : a;
+        bad_s[kk] = b;
+      }
+    }
+    __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < KM; ++kk) {
       if (!act[kk]) continue;
-      const double spq = tot[kk];
-      const double a = gam[kk] / spq;
-      if (!(spq > 0.0) || !finite_d(a)) {
+      if (bad_s[kk]) {
         bad[kk] = true;
         act[kk] = false;
       } else {
-        alpha[kk] = a;
+        alpha[kk] = alpha_s[kk];
       }
     }
     any = false;
@@ -360,26 +340,37 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(BatchDev B, int mode, in
       for (int c = 0; c < NQ1; ++c) pr0[kk][c] = fma(w[c], rv, pr0[kk][c]);
     }
   }
-  // CTA reduction of ||r||^2 and the three restriction components (fixed shuffle tree + warp order)
+  // CTA sums of ||r||^2 and the three restriction components: each thread's values go through shared
+  // memory and one warp per sum adds them (lane-strided, then a fixed shuffle tree), four sums at a time
   {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nv = fused_r0 ? 1 + NQ1 : 1;
+    const int nsum = k * nv;
+    for (int c0 = 0; c0 < nsum; c0 += 4) {
 #pragma unroll
-    for (int kk = 0; kk < KM; ++kk) {
-      if (kk >= k) break;
-      for (int c = 0; c < nv; ++c) {
-        double v = c == 0 ? prr[kk] : pr0[kk][c - 1];
-        v = warp_sum(v);
-        if (lane == 0) red4[wid][kk][c] = v;
+      for (int j = 0; j < 4; ++j) {
+        const int cc = c0 + j;
+        if (cc >= nsum) break;
+        const int kk = cc / nv, c = cc % nv;
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < KM; ++q)
+          if (q == kk) v = c == 0 ? prr[q] : pr0[q][c == 1 ? 0 : (c == 2 ? 1 : 2)];
+        colbuf[j][threadIdx.x] = v;
       }
-    }
-    __syncthreads();
-    if (threadIdx.x < k * nv) {
-      const int kk = threadIdx.x / nv, c = threadIdx.x % nv;
-      double v = 0.0;
-      for (int ww = 0; ww < UPD_NW; ++ww) v += red4[ww][kk][c];
-      if (c == 0) P.part_rr[(long long)g * k + kk] = v;
-      else if (act[kk]) P.r0[(long long)kk * P.n0 + g * nq + c - 1] = v;
+      __syncthreads();
+      if (wid < 4 && c0 + wid < nsum) {
+        double v = 0.0;
+#pragma unroll
+        for (int i = 0; i < UPD_THREADS / 32; ++i) v += colbuf[wid][lane + 32 * i];
+        v = warp_sum(v);
+        if (lane == 0) {
+          const int cc = c0 + wid, kk = cc / nv, c = cc % nv;
+          if (c == 0) P.part_rr[(long long)g * k + kk] = v;
+          else if (act[kk]) P.r0[(long long)kk * P.n0 + g * nq + c - 1] = v;
+        }
+      }
+      __syncthreads();
     }
   }
   if (restrict_ && !fused_r0 && any) {
