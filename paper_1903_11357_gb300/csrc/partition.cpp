@@ -5,43 +5,56 @@
 #include <utility>
 
 #include "common.h"
+#include "hostpool.h"
 #include "plan.h"
 
 namespace dgasm {
 
-static void rcb_rec(const double* cx, const double* cy, std::vector<int>& elems, size_t lo, size_t hi, int k,
-                    std::vector<int>& part_of, int& next_part, std::vector<std::pair<double, int>>& keys) {
-  if (k <= 1) {
-    for (size_t i = lo; i < hi; ++i) part_of[elems[i]] = next_part;
-    ++next_part;
-    return;
-  }
-  double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-  for (size_t i = lo; i < hi; ++i) {
-    int e = elems[i];
-    xmin = std::min(xmin, cx[e]); xmax = std::max(xmax, cx[e]);
-    ymin = std::min(ymin, cy[e]); ymax = std::max(ymax, cy[e]);
-  }
-  const double* c = (xmax - xmin >= ymax - ymin) ? cx : cy;
-  int kl = k / 2;
-  size_t n = hi - lo;
-  size_t nl = (n * (size_t)kl) / (size_t)k;
-  // the first nl elements in the (coordinate, element id) order: a strict total order, so selecting them
-  // with nth_element gives exactly the set a full sort would (the keys sit side by side for the selection)
-  if (nl > 0 && nl < n) {
-    keys.resize(n);
-    for (size_t i = 0; i < n; ++i) keys[i] = {c[elems[lo + i]], elems[lo + i]};
-    std::nth_element(keys.begin(), keys.begin() + nl, keys.end());
-    for (size_t i = 0; i < n; ++i) elems[lo + i] = keys[i].second;
-  }
-  rcb_rec(cx, cy, elems, lo, lo + nl, kl, part_of, next_part, keys);
-  rcb_rec(cx, cy, elems, lo + nl, hi, k - kl, part_of, next_part, keys);
-}
-
+// Recursive coordinate bisection, level by level: every segment of a level (a range of elems with its part
+// count k and first part number) is split independently (the longer side of its centroids' bounding box, the
+// first floor(n floor(k/2) / k) elements in (coordinate, element id) order to the left), so the segments of a
+// level run in parallel and the parts do not depend on the threads.
 void rcb_parts(const MeshData& m, std::vector<int> elems, int k, std::vector<int>& part_of, int first_part) {
-  int next = first_part;
-  std::vector<std::pair<double, int>> keys;
-  rcb_rec(m.cx.data(), m.cy.data(), elems, 0, elems.size(), k, part_of, next, keys);
+  struct Seg {
+    size_t lo, hi;
+    int k, first;
+  };
+  const double *cx = m.cx.data(), *cy = m.cy.data();
+  std::vector<Seg> level{{0, elems.size(), k, first_part}}, next;
+  while (!level.empty()) {
+    next.assign(2 * level.size(), Seg{0, 0, 0, 0});
+    parallel_for((int)level.size(), [&](int si) {
+      const Seg g = level[si];
+      if (g.k <= 1) {
+        for (size_t i = g.lo; i < g.hi; ++i) part_of[elems[i]] = g.first;
+        return;
+      }
+      double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+      for (size_t i = g.lo; i < g.hi; ++i) {
+        const int e = elems[i];
+        xmin = std::min(xmin, cx[e]); xmax = std::max(xmax, cx[e]);
+        ymin = std::min(ymin, cy[e]); ymax = std::max(ymax, cy[e]);
+      }
+      const double* c = (xmax - xmin >= ymax - ymin) ? cx : cy;
+      const int kl = g.k / 2;
+      const size_t n = g.hi - g.lo;
+      const size_t nl = (n * (size_t)kl) / (size_t)g.k;
+      // the first nl elements in the (coordinate, element id) order: a strict total order, so selecting them
+      // with nth_element gives exactly the set a full sort would (the keys sit side by side for the selection)
+      if (nl > 0 && nl < n) {
+        thread_local std::vector<std::pair<double, int>> keys;
+        keys.resize(n);
+        for (size_t i = 0; i < n; ++i) keys[i] = {c[elems[g.lo + i]], elems[g.lo + i]};
+        std::nth_element(keys.begin(), keys.begin() + nl, keys.end());
+        for (size_t i = 0; i < n; ++i) elems[g.lo + i] = keys[i].second;
+      }
+      next[2 * si] = Seg{g.lo, g.lo + nl, kl, g.first};
+      next[2 * si + 1] = Seg{g.lo + nl, g.hi, g.k - kl, g.first + kl};
+    });
+    level.clear();
+    for (const Seg& g : next)
+      if (g.k > 0) level.push_back(g);
+  }
 }
 
 int compute_partition(const MeshData& m, int nsub, int ncoarse, std::vector<int>& sub, std::vector<int>* agg) {
@@ -57,14 +70,17 @@ int compute_partition(const MeshData& m, int nsub, int ncoarse, std::vector<int>
     if (ncoarse >= nsub) {
       std::vector<std::vector<int>> members(nsub);
       for (int e = 0; e < ne; ++e) members[sub[e]].push_back(e);
-      int next = 0;
       for (int i = 0; i < nsub; ++i) {
-        int ci = (int)(((long long)(i + 1) * ncoarse) / nsub - ((long long)i * ncoarse) / nsub);
+        const int ci = (int)(((long long)(i + 1) * ncoarse) / nsub - ((long long)i * ncoarse) / nsub);
         if (ci < 1 || (size_t)ci > members[i].size())
           return set_error(DGASM_EINVAL, "subdomain %d cannot hold %d agglomerates", i, ci);
-        rcb_parts(m, members[i], ci, *agg, next);
-        next += ci;
       }
+      // subdomain i's agglomerates are numbered from floor(i ncoarse / nsub) on
+      parallel_for(nsub, [&](int i) {
+        const int first = (int)(((long long)i * ncoarse) / nsub);
+        const int ci = (int)(((long long)(i + 1) * ncoarse) / nsub) - first;
+        rcb_parts(m, members[i], ci, *agg, first);
+      });
     } else {
       rcb_parts(m, all, ncoarse, *agg, 0);
     }

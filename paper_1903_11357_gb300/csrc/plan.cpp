@@ -12,6 +12,7 @@
 #include <tuple>
 
 #include "engine.h"
+#include "hostpool.h"
 #include "plan.h"
 
 namespace dgasm {
@@ -105,49 +106,64 @@ void Envelope::build(const std::vector<std::vector<int>>& first_col, int sr_) {
     bwd_ptr[s + 1] = (long long)bwd_src.size();
   }
   ndinv = dinv_ptr.back();
-  diag_off.assign(max_nbt + 1, 0);
-  panel_off.assign(max_nbt + 1, 0);
-  upd_off.assign(max_nbt + 1, 0);
-  diag_task.clear();
-  panel_task.clear();
-  upd_task.clear();
-  tc_off.assign(max_nbt + 1, 0);
-  tc_task.clear();
-  diag_task.reserve((size_t)nsub * max_nbt);
-  panel_task.reserve((size_t)ntiles * 2);
-  upd_task.reserve((size_t)ntiles * 3 * 8);
-  std::vector<int> S;
-  for (int K = 0; K < max_nbt; ++K) {
+  // Cholesky task lists by step K; the steps are independent, so each is built on its own (in parallel) and
+  // the lists are then laid end to end in step order (panel indices in the tensor-core groups shifted to the
+  // step's place), which gives the same arrays as building them one step after the other
+  struct StepTasks {
+    std::vector<int> diag, panel, tc, upd;
+  };
+  std::vector<StepTasks> steps(max_nbt);
+  parallel_for(max_nbt, [&](int K) {
+    StepTasks& T = steps[K];
+    std::vector<int> S;
     for (int s = 0; s < nsub; ++s) {
-      int nbt = (int)Fs[s].size();
+      const int nbt = (int)Fs[s].size();
       if (K >= nbt) continue;
-      diag_task.push_back(s);
+      T.diag.push_back(s);
       S.clear();
       for (int I = K + 1; I < nbt; ++I)
         if (Fs[s][I] <= K) S.push_back(I);
-      const int pstart = (int)(panel_task.size() / 2), n = (int)S.size();
-      for (int I : S) { panel_task.push_back(s); panel_task.push_back(I); }
+      const int pstart = (int)(T.panel.size() / 2), n = (int)S.size();   // within the step
+      for (int I : S) { T.panel.push_back(s); T.panel.push_back(I); }
       for (int mb = 0; 4 * mb < n; ++mb) {
         const int bmax = std::min(n, 4 * mb + 4);   // column tiles J <= the block's last row tile
         for (int nb = 0; 8 * nb < bmax; ++nb) {
-          tc_task.push_back(pstart);
-          tc_task.push_back(n);
-          tc_task.push_back(mb);
-          tc_task.push_back(nb);
+          T.tc.push_back(pstart);
+          T.tc.push_back(n);
+          T.tc.push_back(mb);
+          T.tc.push_back(nb);
         }
       }
       for (size_t a = 0; a < S.size(); ++a)
         for (size_t b = 0; b <= a; ++b) {
-          upd_task.push_back(s);
-          upd_task.push_back(S[a]);
-          upd_task.push_back(S[b]);
+          T.upd.push_back(s);
+          T.upd.push_back(S[a]);
+          T.upd.push_back(S[b]);
         }
     }
-    diag_off[K + 1] = (int)diag_task.size();
-    panel_off[K + 1] = (int)(panel_task.size() / 2);
-    upd_off[K + 1] = (int)(upd_task.size() / 3);
-    tc_off[K + 1] = (int)(tc_task.size() / 4);
+  });
+  diag_off.assign(max_nbt + 1, 0);
+  panel_off.assign(max_nbt + 1, 0);
+  upd_off.assign(max_nbt + 1, 0);
+  tc_off.assign(max_nbt + 1, 0);
+  for (int K = 0; K < max_nbt; ++K) {
+    diag_off[K + 1] = diag_off[K] + (int)steps[K].diag.size();
+    panel_off[K + 1] = panel_off[K] + (int)(steps[K].panel.size() / 2);
+    upd_off[K + 1] = upd_off[K] + (int)(steps[K].upd.size() / 3);
+    tc_off[K + 1] = tc_off[K] + (int)(steps[K].tc.size() / 4);
   }
+  diag_task.assign((size_t)diag_off[max_nbt], 0);
+  panel_task.assign(2 * (size_t)panel_off[max_nbt], 0);
+  upd_task.assign(3 * (size_t)upd_off[max_nbt], 0);
+  tc_task.assign(4 * (size_t)tc_off[max_nbt], 0);
+  parallel_for(max_nbt, [&](int K) {
+    const StepTasks& T = steps[K];
+    std::copy(T.diag.begin(), T.diag.end(), diag_task.begin() + diag_off[K]);
+    std::copy(T.panel.begin(), T.panel.end(), panel_task.begin() + 2 * (size_t)panel_off[K]);
+    std::copy(T.upd.begin(), T.upd.end(), upd_task.begin() + 3 * (size_t)upd_off[K]);
+    int* tc = tc_task.data() + 4 * (size_t)tc_off[K];
+    for (size_t i = 0; i < T.tc.size(); ++i) tc[i] = T.tc[i] + (i % 4 == 0 ? panel_off[K] : 0);
+  });
 }
 
 namespace {
@@ -254,14 +270,16 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
     if (ncoarse >= nsub) {
       std::vector<std::vector<int>> members(nsub);
       for (int e = 0; e < ne; ++e) members[P.sub_of[e]].push_back(e);
-      int next = 0;
       for (int i = 0; i < nsub; ++i) {
-        int ci = (int)(((long long)(i + 1) * ncoarse) / nsub - ((long long)i * ncoarse) / nsub);
+        const int ci = (int)(((long long)(i + 1) * ncoarse) / nsub - ((long long)i * ncoarse) / nsub);
         if (ci < 1 || (size_t)ci > members[i].size())
           return set_error(DGASM_EINVAL, "subdomain %d cannot hold %d agglomerates", i, ci);
-        rcb_parts(m, members[i], ci, P.agg_of, next);
-        next += ci;
       }
+      // subdomain i's agglomerates are numbered from floor(i ncoarse / nsub) on
+      parallel_for(nsub, [&](int i) {
+        const int first = (int)(((long long)i * ncoarse) / nsub);
+        rcb_parts(m, members[i], (int)(((long long)(i + 1) * ncoarse) / nsub) - first, P.agg_of, first);
+      });
     } else {
       std::vector<int> all(ne);
       std::iota(all.begin(), all.end(), 0);
@@ -281,16 +299,11 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   for (int e = 0; e < ne; ++e) members[P.sub_of[e]].push_back(e);
   // RCM of each subdomain, in parallel (subdomains are independent; results do not depend on threads)
   std::vector<std::vector<int>> ords(nsub);
-  {
-    const unsigned nt = std::max(1u, std::min({16u, std::thread::hardware_concurrency(), (unsigned)nsub}));
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t)
-      th.emplace_back([&, t]() {
-        std::vector<int> loc(ne, 0);
-        for (int s = (int)t; s < nsub; s += (int)nt) ords[s] = rcm_order(members[s], sys.rowptr, sys.col, P.sub_of, s, loc);
-      });
-    for (auto& x : th) x.join();
-  }
+  parallel_for(nsub, [&](int s) {
+    thread_local std::vector<int> loc;   // rcm_order writes the entries it reads
+    if ((int)loc.size() < ne) loc.resize(ne);
+    ords[s] = rcm_order(members[s], sys.rowptr, sys.col, P.sub_of, s, loc);
+  });
   P.perm.clear();
   P.perm.reserve(ne);
   P.sub_e0.assign(nsub + 1, 0);
@@ -305,23 +318,32 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
   for (int i = 0; i < ne; ++i) P.rowptr[i + 1] = P.rowptr[i] + (sys.rowptr[P.perm[i] + 1] - sys.rowptr[P.perm[i]]);
   P.col.resize(P.rowptr[ne]);
   P.src_blk.resize(P.rowptr[ne]);
-  for (int i = 0; i < ne; ++i) {
-    const int e = P.perm[i], base = P.rowptr[i];
-    int n = 0;
-    for (int k = sys.rowptr[e]; k < sys.rowptr[e + 1]; ++k, ++n) {
-      const int c = P.iperm[sys.col[k]];
-      int j = n;
-      for (; j > 0 && P.col[base + j - 1] > c; --j) {
-        P.col[base + j] = P.col[base + j - 1];
-        P.src_blk[base + j] = P.src_blk[base + j - 1];
+  {
+    const int *srp = sys.rowptr.data(), *sc = sys.col.data(), *ip = P.iperm.data(), *rp = P.rowptr.data(),
+              *pm = P.perm.data();
+    int* pc = P.col.data();
+    long long* ps = P.src_blk.data();
+    constexpr int RB = 512;   // internal rows per task
+    parallel_for((ne + RB - 1) / RB, [&](int b) {
+      for (int i = b * RB; i < std::min(ne, (b + 1) * RB); ++i) {
+        const int e = pm[i], base = rp[i];
+        int n = 0;
+        for (int k = srp[e]; k < srp[e + 1]; ++k, ++n) {
+          const int c = ip[sc[k]];
+          int j = n;
+          for (; j > 0 && pc[base + j - 1] > c; --j) {
+            pc[base + j] = pc[base + j - 1];
+            ps[base + j] = ps[base + j - 1];
+          }
+          pc[base + j] = c;
+          ps[base + j] = k;
+        }
       }
-      P.col[base + j] = c;
-      P.src_blk[base + j] = k;
-    }
+    });
   }
   // envelopes: first column of each local dof row
   std::vector<std::vector<int>> fc(nsub);
-  for (int s = 0; s < nsub; ++s) {
+  parallel_for(nsub, [&](int s) {
     int e0 = P.sub_e0[s], e1 = P.sub_e0[s + 1];
     fc[s].resize((size_t)(e1 - e0) * np);
     for (int i = e0; i < e1; ++i) {
@@ -332,7 +354,7 @@ int build_plan(const dgasm_system_s& sys, int nsub, int ncoarse, int q, const in
       }
       for (int a = 0; a < np; ++a) fc[s][(size_t)(i - e0) * np + a] = first * np;
     }
-  }
+  });
   P.env.build(fc, sr);
   // groups and coarse data
   P.agg_int.assign(ne, -1);
