@@ -269,8 +269,8 @@ def _systems(specs, meshes, dg, torch, rhs_seed_offset=1):
 def batch_measure(steps, warmup):
     """48 independent problems (element counts log-uniform in 1024..16384, p in 1..4, N/256 subdomains,
     N/64 agglomerates at p_c=1): setup of all 48 preconditioners and one batched solve of all of them (FP64
-    outer PCG; per iteration one persistent vector launch and one local-solve launch per kind for the whole
-    batch, CUDA graphs), with FP32 / BF16 / FP64 local factors, against the plain FP64 library mode, one
+    outer PCG; per iteration one launch per kernel kind for the whole batch, replayed from CUDA graphs), with
+    FP32 / BF16 / FP64 local factors, against the plain FP64 library mode, one
     problem at a time (setup + solve each)."""
     from synth.workloads import build_meshes, problem_specs
     specs = problem_specs(48, 4)
