@@ -225,3 +225,36 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         dg.lib()
     with pytest.raises(RuntimeError, match="missing"):
         dg.Mesh.from_polymesh(mesh(32, 1), np.ones(32))
+
+
+def test_partitions_and_plans_from_concurrent_threads_match_serial():
+    """The host plan's loops run on one shared worker pool: partitions computed from several threads at once
+    (ctypes releases the interpreter lock during each call) equal the serial ones, and plans built
+    concurrently pass their self-check."""
+    import threading
+    n = 3000
+    m = mesh(n, 11)
+    M = dg.Mesh.from_polymesh(m, np.ones(n))
+    cases = [(64, 256), (16, 64), (7, 30), (5, 3)]
+    ref = {c: M.partition(*c) for c in cases}
+    S = dg.System(M, 2, 10.0)
+    got, checks, errors = {}, {}, []
+
+    def work(i):
+        try:
+            c = cases[i % len(cases)]
+            for _ in range(3):
+                got[(i, c)] = M.partition(*c)
+            checks[i] = dg.selftest_plan(S, c[0])
+        except Exception as e:   # reported below
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(8)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    for (i, c), (sub, agg) in got.items():
+        assert np.array_equal(sub, ref[c][0]) and np.array_equal(agg, ref[c][1]), (i, c)
+    assert all(v == 0 and k > 0 for v, k in checks.values()), checks
