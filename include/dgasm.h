@@ -152,6 +152,14 @@ int dgasm_system_destroy(dgasm_system_t s);
  * Asynchronous on the stream; y is bitwise identical to dgasm_system_spmv's. */
 int dgasm_system_spmv_dot_noalloc(dgasm_system_t s, const double* x, double* y, double* xAx, void* stream);
 
+/* Form of the FP32 and BF16 local-solve launches (no paper counterpart; a scheduling choice of this library,
+ * process-wide): 0 (the default) runs each subdomain item on a cluster of two CTAs while all of a launch's
+ * items fit on the GPU at once, and on one CTA per item beyond that; 1 one CTA wherever its shared memory holds
+ * two ring slots next to the subdomain's vectors (else a pair); 2 always a pair.  Both forms add the same
+ * products in the same order, so results do not depend on it (FP64 local solves always use pairs).  Takes
+ * effect for solves and applications started after the call.  Errors: DGASM_EINVAL for another value. */
+int dgasm_set_local_cta_form(int form);
+
 /* FP64 FMA issue-rate probe (the paper has no counterpart; measurement support for the roofline of the FP64
  * kernels).  Runs one CTA of 512 threads per SM on the current device, each thread 8 independent FP64 FMA
  * chains, and reports *nsm (SM count), *fma_per_clk_per_sm (FMA per clock per SM, median SM, from the CTAs'

@@ -22,6 +22,11 @@
 // interleaved, one vector load per tile; lane = the other tile index), so the FP64 work is spread evenly
 // over both SMs' sub-partitions and a warp only ever needs its own entries of each solution block.
 //
+// FP32 and BF16 launches have a second form for launches with more pairs than the GPU holds at once: one CTA
+// of 16 consumer warps per item, whose slots carry the same runs of both halves (the half-0 tiles, then the
+// half-1 tiles) and whose warps 8..15 take the lines of the pair's rank 1.  A block entry is then (sum of warps
+// 0..7) + (sum of warps 8..15), the pair's (rank 0 sum) + (rank 1 sum), so both forms give the same bits.
+//
 // Reductions.  The warps' partial sums of a block entry are added in a fixed order inside each CTA; the
 // entries the peer owns are sent to it with st.async, which counts its bytes on the peer's exchange
 // mbarrier, and each entry's total is (rank 0 sum) + (rank 1 sum).  The result therefore does not depend
@@ -31,10 +36,12 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <set>
 #include <utility>
 
+#include "common.h"
 #include "engine.h"
 
 namespace dgasm {
@@ -44,9 +51,7 @@ namespace {
 constexpr int T = 32;
 constexpr int TT = T * T;
 constexpr int HT = TT / 2;             // half tile: 16 lines of 32
-constexpr int NCW = 8;                 // consumer warps
-constexpr int NCT = NCW * 32;          // consumer threads
-constexpr int NTH = NCT + 32;          // + producer warp
+constexpr int NCW_PAIR = 8;            // consumer warps of each CTA of a pair (a CTA alone has twice as many)
 constexpr int LW = 2;                  // tile lines per consumer warp
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds at the GB300 clock
 
@@ -156,7 +161,9 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory"); }
+// named barrier 1 over the n consumer threads (the producer warp never joins it)
+template <int N>
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -206,23 +213,31 @@ __device__ __forceinline__ float2 ld_pair2(const float* p) { return *reinterpret
 // tiles per ring slot: 32 KB of half tiles (the cost of a bulk copy is mostly per operation)
 template <typename S> __host__ __device__ constexpr int slot_tiles() { return (32 * 1024) / (int)(HT * sizeof(S)); }
 
-template <typename S, typename C, int KCT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
-    k_local(BatchDev B, int slot, int ring_off, int nstage) {
+// PAIR: a cluster of two CTAs per item, CTA rank h holding lines 16h .. 16h + 15 of every tile.  Otherwise one
+// CTA of 16 consumer warps per item does the work of both: its warp 8h + w takes the lines of warp w of rank h,
+// its ring slots hold the same tiles of both halves, and it adds the two halves' partial sums in the pair's
+// order, so both forms give the same bits (the engine takes the one CTA form when a launch's pairs would not all
+// be resident at once: it needs no exchange and half the SMs per item).
+template <typename S, typename C, int KCT, bool PAIR>
+__device__ __forceinline__ void local_body(const BatchDev& B, int slot, int ring_off, int nstage) {
   using VS = typename Pair<S>::V;
+  constexpr int NCW = PAIR ? NCW_PAIR : 2 * NCW_PAIR;   // consumer warps
+  constexpr int NCT = NCW * 32;
   constexpr int SR = 8;                   // tile rows per super-row: super_row() of every precision
-  constexpr int NX = SR * 16 * KCT;       // entries exchanged per reduction (each direction)
+  constexpr int YL = PAIR ? 16 : 32;      // lines of every tile this CTA holds (its half, or all)
+  constexpr int NX = SR * 16 * KCT;       // entries exchanged per reduction (each direction, PAIR)
   constexpr int NE = SR * KCT * T;        // entries summed per reduction in each CTA
   constexpr bool TWO = sizeof(C) == 4;    // two accumulation chains (FP32: cover the FMA latency)
-  constexpr int CH = slot_tiles<S>();     // tiles per ring slot
+  constexpr int CH = slot_tiles<S>();     // tiles per ring slot and half
+  constexpr int SLOT = (PAIR ? 1 : 2) * CH * HT;   // elements of a ring slot
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[NCW + 1][KCT];
   __shared__ double peer_rz[KCT];
   __shared__ int abort_flag, xdead;
   __shared__ __align__(8) unsigned long long xbar[2];   // the peer's partial sums have landed
-  const unsigned rank = cluster_rank(), peer = rank ^ 1u;
+  const unsigned rank = PAIR ? cluster_rank() : 0u, peer = rank ^ 1u;
   const int* prefix = B.prefix[slot];
-  const int item = blockIdx.x >> 1;
+  const int item = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int pi = find_prob(prefix, B.nprob, item);
   const ProbDev& P = B.probs[pi];
   const int li = item - prefix[pi];
@@ -236,7 +251,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     act[j] = j < kc && P.done[k0 + j] == 0;
     any |= act[j];
   }
-  if (!any) return;   // both CTAs of the pair read the same flags and leave together
+  if (!any) return;   // both CTAs of a pair read the same flags and leave together
   if (P.sr != SR) {   // the plan was built for another super-row size: refuse
     if (threadIdx.x == 0) atomicExch(B.err, 2);
     return;
@@ -245,21 +260,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
   const int e0 = P.sub_e0[s];
   const int n = (P.sub_e0[s + 1] - e0) * P.np;
   const long long d0 = (long long)e0 * P.np;
-  const int nbt = (n + T - 1) / T, npadh = nbt * 16;
+  const int nbt = (n + T - 1) / T, npadh = nbt * YL;
   const int nsr = (nbt + SR - 1) / SR;
   const int sr0 = P.sub_sr[s];
   const long long ff0 = P.fwd_ptr[s], bb0 = P.bwd_ptr[s];
-  C* y = reinterpret_cast<C*>(smem);                  // [KCT][nbt][16]: own lines of every block
+  C* y = reinterpret_cast<C*>(smem);                  // [KCT][nbt][YL]: the held lines of every block
   // per-warp partial sums [NCW][SR][KCT][T], one buffer for both reductions of a super-row: a reduction
   // reads it only before its internal barrier, which every warp passes before writing the next partials
   C* part = y + KCT * npadh;
   C* dpart = part;
   C* tvs = part + NCW * SR * KCT * T;                  // [NCW][SR][KCT][LW]
-  C* xbuf = tvs + NCW * SR * KCT * LW;                 // [2][SR][KCT][16]: the peer's sums of own entries
-  C* cpart = xbuf + 2 * NX;                            // [SR][KCT][16]: this CTA's sums of own entries
-  int* runs_s = reinterpret_cast<int*>(cpart + NX);    // [2][nsr][SR][2]: the subdomain's coupling runs
-  S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][CH][HT]
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * CH * HT);
+  C* xbuf = tvs + NCW * SR * KCT * LW;                 // [2][SR][KCT][16]: the peer's sums of own entries (PAIR)
+  C* cpart = xbuf + (PAIR ? 2 * NX : 0);               // [SR][KCT][YL]: the sums of the held entries
+  int* runs_s = reinterpret_cast<int*>(cpart + (PAIR ? NX : NE));   // [2][nsr][SR][2]: the coupling runs
+  S* ring = reinterpret_cast<S*>(smem + ring_off);     // [nstage][SLOT]: per slot CH tiles of each held half
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + (size_t)nstage * SLOT);
   unsigned long long* empty = full + nstage;
   if (tid == 0) {
     abort_flag = 0;
@@ -273,18 +288,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  cluster_sync();   // the peer's barriers exist before any store reaches them
+  if constexpr (PAIR) cluster_sync();   // the peer's barriers exist before any store reaches them
 
   if (w == NCW) {
-    // ---- producer: half `rank` of the subdomain's forward stream, then of its backward stream.  Each
-    // super-row's coupling section and inverse-block section is copied in runs of up to CH tiles (one
-    // bulk copy per run), every section starting in a fresh slot.
+    // ---- producer: half `rank` (PAIR) or both halves of the subdomain's forward stream, then of its backward
+    // stream.  Each super-row's coupling section and inverse-block section is copied in runs of up to CH
+    // tiles (one bulk copy per run and half), every section starting in a fresh slot.
     if (lane == 0) {
       int sl = 0;
       unsigned round = 0;   // how many times the ring has wrapped
       long long issued = 0;
       bool ok = true;
       for (int pass = 0; pass < 2 && ok; ++pass) {
+        const long long tot = pass == 0 ? P.fwd_total : P.bwd_total;
         const S* base = pass == 0 ? reinterpret_cast<const S*>(P.Lc) + (rank * P.fwd_total + ff0) * HT
                                   : reinterpret_cast<const S*>(P.Lr) + (rank * P.bwd_total + bb0) * HT;
         const int* rt = (pass == 0 ? P.fwd_run : P.bwd_run) + (size_t)sr0 * SR * 2;
@@ -300,8 +316,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
               const int len = min(CH, len_sec - t);
               if (round > 0 && !mbar_wait(empty + sl, (round - 1) & 1, &abort_flag, B.err)) { ok = false; break; }
               const unsigned bytes = (unsigned)(len * HT * sizeof(S));
-              mbar_expect_tx(full + sl, bytes);
-              bulk_g2s(ring + (size_t)sl * CH * HT, base + (pos + t) * HT, bytes, full + sl);
+              mbar_expect_tx(full + sl, PAIR ? bytes : 2 * bytes);
+              bulk_g2s(ring + (size_t)sl * SLOT, base + (pos + t) * HT, bytes, full + sl);
+              if constexpr (!PAIR)   // the same tiles' second half, after the first half's CH tiles
+                bulk_g2s(ring + (size_t)sl * SLOT + (size_t)CH * HT, base + (tot + pos + t) * HT, bytes, full + sl);
               ++issued;
               if (++sl == nstage) { sl = 0; ++round; }
             }
@@ -325,12 +343,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     }
     for (int idx = tid; idx < KCT * npadh; idx += NCT) {
       const int j = idx / npadh, m = idx - j * npadh;
-      const int i = (m >> 4) * T + 16 * (int)rank + (m & 15);
+      const int i = (m / YL) * T + 16 * (int)rank + (m % YL);
       C v = (C)0;
       if (i < n && act[j]) v = (C)(P.scale[d0 + i] * P.r[(long long)(k0 + j) * P.ndof + d0 + i]);
       y[idx] = v;
     }
-    consumer_sync();
+    consumer_sync<NCT>();
     // Stream cursor: ring slot cs (phase parity cph), this warp's line pair of the current tile in it
     // (cur), tiles left in the slot's run of tiles (left_in), tiles of the current stream still to come
     // after this slot (rest).  A slot is waited for when the cursor enters it and handed back to the
@@ -338,11 +356,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     int cs = 0, left_in = 0, rest = 0;
     unsigned cph = 0;
     const VS* cur = nullptr;
-    const size_t wofs = (size_t)w * T + lane;   // this warp's pair within a half tile, in pairs
+    // this warp's pair within a slot, in pairs: its half's region (one CTA), then its line pair in the half
+    const size_t wofs = (PAIR ? 0 : (size_t)(w >> 3) * CH * (HT / 2)) + (size_t)(w & 7) * T + lane;
     auto enter_slot = [&]() {
       left_in = min(CH, rest);
       rest -= left_in;
-      cur = reinterpret_cast<const VS*>(ring + (size_t)cs * CH * HT) + wofs;
+      cur = reinterpret_cast<const VS*>(ring + (size_t)cs * SLOT) + wofs;
       if (left_in > 0 && !mbar_try(full + cs, cph)) mbar_wait(full + cs, cph, &abort_flag, B.err);
     };
     auto leave_slot = [&]() {
@@ -411,6 +430,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     unsigned xcount = 0;
     C* tw = tvs + w * SR * KCT * LW;   // this warp's own entries of t (the block product's input)
     auto reduce = [&](const C* buf, auto&& use) {
+      if constexpr (!PAIR) {
+        // as a pair would: each half's eight warps in warp order, then (half 0 sum) + (half 1 sum)
+        for (int e = tid; e < NE; e += NCT) {
+          const int c = e % T, j = (e / T) % KCT, ii = e / (T * KCT);
+          const C* b = buf + (ii * KCT + j) * T + c;
+          C v0 = b[0], v1 = b[8 * SR * KCT * T];
+#pragma unroll
+          for (int ww = 1; ww < 8; ++ww) {
+            v0 += b[ww * SR * KCT * T];
+            v1 += b[(8 + ww) * SR * KCT * T];
+          }
+          cpart[(ii * KCT + j) * T + c] = v0 + v1;
+        }
+        consumer_sync<NCT>();
+        for (int e = lane; e < SR * LW * KCT; e += 32) {
+          const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
+          use(ii, j, u, cpart[(ii * KCT + j) * T + lw + u]);
+        }
+        __syncwarp();
+        return;
+      }
       const unsigned xb = xcount & 1u, xph = (xcount >> 1) & 1u;
       ++xcount;
       if (tid == 0 && !xdead) mbar_expect_tx(&xbar[xb], (unsigned)(NX * sizeof(C)));
@@ -426,7 +466,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
         if ((c >> 4) == (int)rank) cpart[slot16] = v;
         else st_async(pbuf + (unsigned)(slot16 * sizeof(C)), v, pbar);
       }
-      consumer_sync();
+      consumer_sync<NCT>();
       xbar_wait(&xbar[xb], xph, &abort_flag, &xdead, B.err);
       for (int e = lane; e < SR * LW * KCT; e += 32) {
         const int u = e % LW, ii = (e / LW) % SR, j = e / (LW * SR);
@@ -483,7 +523,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
         C res[KCT];
         if (o < ntr) {
           const int op0 = runs[2 * o], cnt = runs[2 * o + 1];
-          run(cnt, y + op0 * 16 + lw, 16, npadh, res);
+          run(cnt, y + op0 * YL + lw, YL, npadh, res);
         } else {
 #pragma unroll
           for (int j = 0; j < KCT; ++j) res[j] = (C)0;
@@ -491,9 +531,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
 #pragma unroll
         for (int j = 0; j < KCT; ++j) part[((w * SR + o) * KCT + j) * T + lane] = res[j];
       }
-      consumer_sync();
+      consumer_sync<NCT>();
       reduce(part, [&](int ii, int j, int u, C tot) {
-        tw[(ii * KCT + j) * LW + u] = ii < ntr ? y[j * npadh + (I0 + ii) * 16 + lw + u] - tot : (C)0;
+        tw[(ii * KCT + j) * LW + u] = ii < ntr ? y[j * npadh + (I0 + ii) * YL + lw + u] - tot : (C)0;
       });
       start_section(ntr * (ntr + 1) / 2);
       if (ntr == SR) {
@@ -518,30 +558,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
           for (int j = 0; j < KCT; ++j) dpart[((w * SR + o) * KCT + j) * T + lane] = res[j];
         }
       }
-      consumer_sync();
+      consumer_sync<NCT>();
       reduce(dpart, [&](int ii, int j, int u, C tot) {
-        if (ii < ntr) y[j * npadh + (I0 + ii) * 16 + lw + u] = tot;
+        if (ii < ntr) y[j * npadh + (I0 + ii) * YL + lw + u] = tot;
       });
     };
     for (int q = 0; q < nsr; ++q) sweep_step(q, runs_s + q * SR * 2, true);
     for (int q = nsr - 1; q >= 0; --q) sweep_step(q, runs_s + (nsr + q) * SR * 2, false);
   }
   __syncthreads();
-  // z_i = D^{-1/2} y on own entries, partial (r, z) of this CTA; rank 1 hands its sums to rank 0, which
-  // writes (rank 0 sum) + (rank 1 sum)
+  // z_i = D^{-1/2} y on own entries, partial (r, z) of each half (a pair: of each CTA; rank 1 hands its sums to
+  // rank 0), and the item's partial = (half 0 sum) + (half 1 sum); one CTA groups the rows exactly as a pair
+  const int h = PAIR ? (int)rank : (tid >> 8);    // the half whose rows this thread takes
+  const int th = PAIR ? tid : (tid & 255);        // its thread index within that half
   double prz[KCT];
 #pragma unroll
   for (int j = 0; j < KCT; ++j) prz[j] = 0.0;
   if (w < NCW) {
-    for (int m = tid; m < nbt * 16; m += NCT) {
-      const int i = (m >> 4) * T + 16 * (int)rank + (m & 15);
+    for (int m = th; m < nbt * 16; m += NCW_PAIR * 32) {
+      const int i = (m >> 4) * T + 16 * h + (m & 15);
       if (i >= n) continue;
       const double sc = P.scale[d0 + i];
 #pragma unroll
       for (int j = 0; j < KCT; ++j) {
         if (!act[j]) continue;
         const long long o = (long long)(k0 + j) * P.ndof + d0 + i;
-        const double zv = sc * (double)y[j * npadh + m];
+        const double zv = sc * (double)y[j * npadh + (PAIR ? m : i)];
         P.z[o] = zv;
         prz[j] = fma(P.r[o], zv, prz[j]);
       }
@@ -553,19 +595,41 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTH, 1)
     if (lane == 0) red[w][j] = v;
   }
   __syncthreads();
-  double csum = 0.0;
-  if (tid < kc) {
-    for (int ww = 0; ww <= NCW; ++ww) csum += red[ww][tid];
-    if (rank == 1) st_cluster(mapa(&peer_rz[tid], 0), csum);
+  if constexpr (PAIR) {
+    double csum = 0.0;
+    if (tid < kc) {
+      for (int ww = 0; ww <= NCW; ++ww) csum += red[ww][tid];
+      if (rank == 1) st_cluster(mapa(&peer_rz[tid], 0), csum);
+    }
+    cluster_sync();   // also: no access to this CTA's shared memory from the peer after this point
+    if (rank == 0 && tid < kc) P.part_rz[(long long)s * P.k + k0 + tid] = P.done[k0 + tid] == 0 ? csum + peer_rz[tid] : 0.0;
+  } else if (tid < kc) {
+    double c0 = 0.0, c1 = 0.0;
+    for (int ww = 0; ww < NCW_PAIR; ++ww) {
+      c0 += red[ww][tid];
+      c1 += red[NCW_PAIR + ww][tid];
+    }
+    c0 += red[NCW][tid];   // the producer warp's zero, where a pair's CTAs add theirs
+    c1 += red[NCW][tid];
+    P.part_rz[(long long)s * P.k + k0 + tid] = P.done[k0 + tid] == 0 ? c0 + c1 : 0.0;
   }
-  cluster_sync();   // also: no access to this CTA's shared memory from the peer after this point
-  if (rank == 0 && tid < kc) P.part_rz[(long long)s * P.k + k0 + tid] = P.done[k0 + tid] == 0 ? csum + peer_rz[tid] : 0.0;
+}
+
+template <typename S, typename C, int KCT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NCW_PAIR * 32 + 32, 1)
+    k_local(BatchDev B, int slot, int ring_off, int nstage) {
+  local_body<S, C, KCT, true>(B, slot, ring_off, nstage);
+}
+
+template <typename S, typename C, int KCT>
+__global__ void __launch_bounds__(2 * NCW_PAIR * 32 + 32, 1) k_local1(BatchDev B, int slot, int ring_off, int nstage) {
+  local_body<S, C, KCT, false>(B, slot, ring_off, nstage);
 }
 
 // shared memory: y, partial sums, exchange buffers and run tables, then a ring of nstage slots of 32 KB of
 // half tiles
 template <typename S, typename C>
-int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* total) {
+int smem_layout(int ndof_max, int kct, bool pair, int* ring_off, int* nstage, int* total) {
   int dev = 0;
   cudaGetDevice(&dev);
   int optin = 0;
@@ -573,11 +637,13 @@ int smem_layout(int ndof_max, int kct, int* ring_off, int* nstage, int* total) {
   constexpr int SR = 8;
   const int npad = ((ndof_max + T - 1) / T) * T;
   const int nsr_max = (npad / T + SR - 1) / SR;
-  const int head = (int)sizeof(C) * (kct * npad / 2 + NCW * SR * kct * T + NCW * SR * LW * kct + 3 * SR * kct * 16) +
+  const int ncw = pair ? NCW_PAIR : 2 * NCW_PAIR;
+  const int head = (int)sizeof(C) * (kct * npad / (pair ? 2 : 1) + ncw * SR * kct * T + ncw * SR * LW * kct +
+                                     (pair ? 3 * SR * kct * 16 : SR * kct * T)) +
                    (int)sizeof(int) * 4 * nsr_max * SR;
   const int off = (head + 127) & ~127;
   const int budget = optin - 2048 - off;   // static shared memory and slack
-  const int slot = slot_tiles<S>() * (int)(HT * sizeof(S)) + 16;   // 32 KB of tiles + its barriers
+  const int slot = (pair ? 1 : 2) * slot_tiles<S>() * (int)(HT * sizeof(S)) + 16;   // 32 KB of tiles per half + barriers
   int ns = budget / slot;
   if (ns > 32) ns = 32;
   if (ns < 2) return -1;   // the subdomains are too large for this kernel's shared memory
@@ -603,20 +669,33 @@ int ensure_smem(K fn) {
   return 0;
 }
 
+// one CTA pair per item, or one CTA per item (the same bits; chosen by the caller, and a pair wherever a CTA
+// alone would not hold two ring slots next to its subdomain's vectors)
 template <typename S, typename C, int KCT>
-int launch_one(const BatchDev& B, int slot, int items, int ndof_max, cudaStream_t st) {
+int launch_one(const BatchDev& B, int slot, int items, int ndof_max, bool pair, cudaStream_t st) {
   int ring_off, nstage, smem;
-  if (smem_layout<S, C>(ndof_max, KCT, &ring_off, &nstage, &smem)) return (int)cudaErrorInvalidValue;
-  auto fn = k_local<S, C, KCT>;
-  if (int e = ensure_smem(fn)) return e;
-  fn<<<2 * items, NTH, smem, st>>>(B, slot, ring_off, nstage);   // one CTA pair per item
+  if (!pair && smem_layout<S, C>(ndof_max, KCT, false, &ring_off, &nstage, &smem)) pair = true;
+  if (pair && smem_layout<S, C>(ndof_max, KCT, true, &ring_off, &nstage, &smem)) return (int)cudaErrorInvalidValue;
+  if (pair) {
+    auto fn = k_local<S, C, KCT>;
+    if (int e = ensure_smem(fn)) return e;
+    fn<<<2 * items, NCW_PAIR * 32 + 32, smem, st>>>(B, slot, ring_off, nstage);
+  } else {
+    auto fn = k_local1<S, C, KCT>;
+    if (int e = ensure_smem(fn)) return e;
+    fn<<<items, 2 * NCW_PAIR * 32 + 32, smem, st>>>(B, slot, ring_off, nstage);
+  }
   return (int)cudaGetLastError();
 }
 
 template <typename S, typename C>
-int launch_local_t(const BatchDev& B, int slot, int kcl, int items, int ndof_max, cudaStream_t st) {
-  return kcl == 0 ? launch_one<S, C, 1>(B, slot, items, ndof_max, st) : launch_one<S, C, KC>(B, slot, items, ndof_max, st);
+int launch_local_t(const BatchDev& B, int slot, int kcl, int items, int ndof_max, bool pair, cudaStream_t st) {
+  if constexpr (sizeof(C) == 8) pair = true;   // FP64 sweeps always take both SMs' FP64 pipes
+  return kcl == 0 ? launch_one<S, C, 1>(B, slot, items, ndof_max, pair, st)
+                  : launch_one<S, C, KC>(B, slot, items, ndof_max, pair, st);
 }
+
+std::atomic<int> g_cta_form{0};   // 0: by the rule below, 1: one CTA per item, 2: a CTA pair per item
 
 // Self-test of the bounded wait every ring and exchange wait of k_local goes through: one CTA waits on an
 // mbarrier that nothing arrives on, with a limit of `limit` cycles; the wait gives up, sets the error word
@@ -648,15 +727,34 @@ int launch_wait_selftest(int* err, long long limit, void* stream) {
 }
 
 // slot = K_NKINDS + 2 * prec + (kc > 1); `param` is the largest subdomain dof count of the launch
+// The FP32 and BF16 sweeps run as CTA pairs while all of a launch's pairs fit on the GPU at once (the lowest
+// latency for one problem), and as one CTA per item beyond that (no exchange, half the SMs per item: more
+// items in flight for batches); both forms give the same bits.
 int launch_local(const BatchDev& B, int slot, int total, int param, void* stream) {
   const int prec = (slot - K_NKINDS) / 2, kcl = (slot - K_NKINDS) % 2;
   cudaStream_t s = (cudaStream_t)stream;
+  bool pair = true;
+  const int form = g_cta_form.load();
+  if (form == 1) {
+    pair = false;
+  } else if (form == 0) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return (int)cudaGetLastError();
+    pair = 2 * total <= nsm;
+  }
   switch (prec) {
-    case DGASM_FP64: return launch_local_t<double, double>(B, slot, kcl, total, param, s);
+    case DGASM_FP64: return launch_local_t<double, double>(B, slot, kcl, total, param, true, s);
     case DGASM_FP32:
-    case DGASM_TF32: return launch_local_t<float, float>(B, slot, kcl, total, param, s);
-    default: return launch_local_t<__nv_bfloat16, float>(B, slot, kcl, total, param, s);
+    case DGASM_TF32: return launch_local_t<float, float>(B, slot, kcl, total, param, pair, s);
+    default: return launch_local_t<__nv_bfloat16, float>(B, slot, kcl, total, param, pair, s);
   }
 }
 
 }  // namespace dgasm
+
+extern "C" int dgasm_set_local_cta_form(int form) {
+  if (form < 0 || form > 2) return dgasm::set_error(DGASM_EINVAL, "dgasm_set_local_cta_form: form %d is not 0, 1 or 2", form);
+  dgasm::g_cta_form.store(form);
+  return DGASM_OK;
+}

@@ -120,6 +120,7 @@ def lib():
             "dgasm_server_destroy": [vp],
             "dgasm_system_spmv_dot_noalloc": [vp, vp, vp, vp, vp],
             "dgasm_probe_fp64": [ip, dp, dp],
+            "dgasm_set_local_cta_form": [C.c_int],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -550,3 +551,9 @@ def probe_fp64():
     t = C.c_double()
     check(lib().dgasm_probe_fp64(C.byref(n), C.byref(r), C.byref(t)))
     return n.value, r.value, t.value
+
+
+def set_local_cta_form(form):
+    """FP32/BF16 local-solve launches: "auto" (pairs while they all fit at once, else one CTA per item), "one"
+    or "pair" (dgasm_set_local_cta_form; process-wide; results are the same bits in every form)."""
+    check(lib().dgasm_set_local_cta_form({"auto": 0, "one": 1, "pair": 2}[form]))
