@@ -81,10 +81,17 @@ int DevBuf::alloc(size_t n) {
   return DGASM_OK;
 }
 
+// A cudaMemcpy from pageable host memory returns once the data sit in the driver's staging buffer; the DMA to
+// the destination is ordered only on the legacy default stream, and the library's kernels run on non-blocking
+// streams.  The upload therefore waits for that stream before it returns, so that a kernel launched afterwards
+// on any stream reads the new data, not what the allocation held before.
 template <typename T>
 int upload(DevBuf& dst, const std::vector<T>& src) {
   DG_TRY(dst.alloc(src.size() * sizeof(T)));
-  if (!src.empty()) DG_CUDA(cudaMemcpy(dst.ptr, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (!src.empty()) {
+    DG_CUDA(cudaMemcpy(dst.ptr, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    DG_CUDA(cudaStreamSynchronize(cudaStreamLegacy));
+  }
   return DGASM_OK;
 }
 template int upload<int>(DevBuf&, const std::vector<int>&);
