@@ -268,8 +268,9 @@ def _systems(specs, meshes, dg, torch, rhs_seed_offset=1):
 
 def batch_measure(steps, warmup):
     """48 independent problems (element counts log-uniform in 1024..16384, p in 1..4, N/256 subdomains,
-    N/64 agglomerates at p_c=1): setup of all 48 preconditioners and one batched solve of all of them (FP64
-    outer PCG; per iteration one launch per kernel kind for the whole batch, replayed from CUDA graphs), with
+    N/64 agglomerates at p_c=1): setup of all 48 preconditioners at once (dgasm_setup_batch) and one batched
+    solve of all of them (FP64 outer PCG; per iteration one launch per kernel kind for the whole batch, replayed
+    from CUDA graphs), with
     FP32 / BF16 / FP64 local factors, against the plain FP64 library mode, one
     problem at a time (setup + solve each)."""
     from synth.workloads import build_meshes, problem_specs
@@ -282,7 +283,10 @@ def batch_measure(steps, warmup):
     nrhs = len(probs)
 
     def batched(precision):
-        precs = [dg.Prec(S, s["nsub"], s["ncoarse"], 1, precision=precision, stream=stream) for s, S, _ in probs]
+        # all 48 set up at once (dgasm_setup_batch: host plans on the worker threads, device work on per-problem
+        # streams), then one batched solve
+        precs = dg.setup_batch([dict(system=S, nsub=s["nsub"], ncoarse=s["ncoarse"], p_c=1, precision=precision)
+                                for s, S, _ in probs])
         xs = [torch.zeros_like(b) for _, _, b in probs]
         rc, sts = dg.solve_batch(precs, [b for _, _, b in probs], xs, rtol=1e-8, stream=stream)
         assert rc == 0, rc

@@ -217,6 +217,16 @@ typedef struct {
  * or coarse cell that overlaps nothing), DGASM_ENOTSPD (the message names the subdomain, or "coarse", and
  * the pivot row), DGASM_ENOMEM, DGASM_ECUDA. */
 int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_prec_t* out);
+/* n preconditioners at once (a batch of independent problems; the paper sets up one): out[i] is what
+ * dgasm_setup(systems[i], opts[i], &out[i]) would build, with the same plan and bitwise the same factors.  The
+ * host plans run on the library's worker threads, several problems at a time, and each problem's device work
+ * on its own streams (or on opts[i]->stream where one is given: problems that share a stream run their device
+ * work in turn), so the setups of small problems, which leave most of the GPU idle, overlap.  The setups'
+ * temporaries are released only after the last one has finished: the call's peak device memory is the sum of
+ * every problem's setup peak.  All or nothing: on an error every preconditioner built so far is destroyed, out
+ * is all NULL, and the code and message are those of the failing problem (the message names its index).
+ * Errors as dgasm_setup, and DGASM_EINVAL for n < 1 or NULL arrays or entries. */
+int dgasm_setup_batch(int n, const dgasm_system_t* systems, const dgasm_setup_opts* const* opts, dgasm_prec_t* out);
 /* z = B r for nrhs vectors (device, caller's dof order, column-major ndof x nrhs). */
 int dgasm_prec_apply(dgasm_prec_t pc, int nrhs, const double* r, double* z, void* stream);
 /* Consistency self-check of the host plan dgasm_setup would build for nsub RCB subdomains (no device work): the

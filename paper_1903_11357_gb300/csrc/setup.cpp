@@ -2,16 +2,20 @@
 // its tile Cholesky factorisation, the L2 prolongation R_0^T (Eq. R0T), A_0 = R_0 A R_0^T (Eq. A0) and
 // the FP64 factor and inverse of A_0.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
 #include "common.h"
 #include "engine.h"
+#include "hostpool.h"
 #include "plan.h"
 #include "profile.h"
 #include "solver.h"
@@ -171,7 +175,7 @@ size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit) {
 // The coarse space (R_0^T, A_0 = R_0 A R_0^T, its factor and inverse) does not depend on the local factors:
 // it is issued on the side stream and runs beside the local factorisation.  Nothing is freed and no stream is
 // synchronised until all device work of the setup has been issued (a cudaFree waits for the whole device).
-int prec_build(dgasm_prec_s* pc) {
+int prec_build(dgasm_prec_s* pc, SetupTemps* defer) {
   dgasm_system_s* s = pc->sys;
   Plan& P = pc->P;
   EventPairs* ev = profiling() ? &pc->setup_ev : nullptr;
@@ -316,6 +320,12 @@ int prec_build(dgasm_prec_s* pc) {
   if (ev) ev->accumulate();
   pc->setup_launches = nl;
   pc->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - pc->t_start).count();
+  if (defer) {   // every stream of this setup has finished: the buffers are idle, their release is the caller's
+    for (auto& b : keep.bufs) defer->add(std::move(b));
+    keep.bufs.clear();
+    defer->add(std::move(Lf));
+    defer->add(std::move(pc->src_blk));
+  }
   pc->src_blk.reset();
   return DGASM_OK;
 }
@@ -330,6 +340,57 @@ extern "C" int dgasm_setup(dgasm_system_t s, const dgasm_setup_opts* o, dgasm_pr
   DG_TRY(prec_plan(s, o, pc));
   DG_TRY(prec_build(pc.get()));
   *out = pc.release();
+  return DGASM_OK;
+}
+
+extern "C" int dgasm_setup_batch(int n, const dgasm_system_t* systems, const dgasm_setup_opts* const* opts,
+                                 dgasm_prec_t* out) {
+  clear_error();
+  if (n < 1 || !systems || !opts || !out) return set_error(DGASM_EINVAL, "dgasm_setup_batch: bad arguments");
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!systems[i] || !opts[i]) return set_error(DGASM_EINVAL, "dgasm_setup_batch: NULL entry %d", i);
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  std::vector<std::unique_ptr<dgasm_prec_s>> pcs(n);
+  std::vector<SetupTemps> temps(n);   // released after the last setup has finished
+  std::vector<int> rc(n, DGASM_OK);
+  std::vector<std::string> msg(n);
+  std::atomic<int> next{0};
+  std::atomic<bool> failed{false};
+  // each worker takes the next problem: its host plan (loops run on the worker itself, nested in this job)
+  // and its device work on the problem's own streams, so plans and device work of different problems overlap
+  const int width = std::min(n, pool_width());
+  parallel_for(width, [&](int) {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      failed = true;
+      return;
+    }
+    for (int i = next.fetch_add(1); i < n && !failed.load(); i = next.fetch_add(1)) {
+      int r = prec_plan(systems[i], opts[i], pcs[i]);
+      if (r == DGASM_OK) r = prec_build(pcs[i].get(), &temps[i]);
+      if (r != DGASM_OK) {
+        char buf[512];
+        dgasm_last_error(buf, sizeof(buf));
+        rc[i] = r;
+        msg[i] = buf;
+        pcs[i].reset();
+        failed = true;
+      }
+    }
+  });
+  temps.clear();
+  for (int i = 0; i < n; ++i)
+    if (rc[i] != DGASM_OK) {
+      pcs.clear();
+      return set_error(rc[i], "dgasm_setup_batch: problem %d: %s", i, msg[i].c_str());
+    }
+  if (failed.load()) {
+    pcs.clear();
+    return set_error(DGASM_ECUDA, "dgasm_setup_batch: a worker thread could not select device %d", dev);
+  }
+  for (int i = 0; i < n; ++i) out[i] = pcs[i].release();
   return DGASM_OK;
 }
 

@@ -96,7 +96,9 @@ int solve_all(Engine& E, int n, dgasm_prec_s* const* pcs, const int* nrhs, const
               const dgasm_solve_opts* o, cudaStream_t stream, dgasm_stats* st);
 int prec_plan(dgasm_system_s* s, const dgasm_setup_opts* o, std::unique_ptr<dgasm_prec_s>& pc);
 size_t prec_estimate_bytes(const dgasm_prec_s& pc, int nrhs, int maxit);
-int prec_build(dgasm_prec_s* pc);
+// With `defer`, the setup's temporaries are handed to it after the final synchronisation instead of being
+// freed (a free waits for the whole device, which would stall setups running beside this one).
+int prec_build(dgasm_prec_s* pc, SetupTemps* defer = nullptr);
 // times one preconditioner application of b with each right-hand-side chunking and keeps the faster
 int tune_rhs_chunk(dgasm_prec_s* pc, int nrhs, const double* b, cudaStream_t stream);
 // local-solve variants: 1 = forward/backward sweeps with the envelope factors, 2 = explicit inverses

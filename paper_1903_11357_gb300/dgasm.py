@@ -89,6 +89,7 @@ def lib():
             "dgasm_system_spmv": [vp, vp, vp, vp],
             "dgasm_system_destroy": [vp],
             "dgasm_setup": [vp, C.POINTER(SetupOpts), C.POINTER(vp)],
+            "dgasm_setup_batch": [C.c_int, C.POINTER(vp), C.POINTER(C.POINTER(SetupOpts)), C.POINTER(vp)],
             "dgasm_prec_apply": [vp, C.c_int, vp, vp, vp],
             "dgasm_prec_partition": [vp, ip, ip],
             "dgasm_prec_footprint": [vp, i64p],
@@ -291,7 +292,15 @@ class Prec:
     def __init__(self, system: System, nsub: int, ncoarse: int, p_c: int = 1, precision="fp64", sub_of_elem=None,
                  agg_of_elem=None, stream=None, coarse_mesh=None):
         """coarse_mesh: a Mesh of the same domain carrying a non-nested coarse space (ncoarse is ignored)."""
+        o = self._options(system, nsub, ncoarse, p_c, precision, sub_of_elem, agg_of_elem, stream, coarse_mesh)
+        h = C.c_void_p()
+        check(lib().dgasm_setup(system.h, C.byref(o), C.byref(h)))
+        self.h = h
+
+    def _options(self, system, nsub, ncoarse, p_c, precision, sub_of_elem, agg_of_elem, stream, coarse_mesh):
+        """dgasm_setup_opts for this preconditioner; the arrays it points into are kept on the object."""
         self.system = system
+        self.ndof = system.ndof
         self._coarse = coarse_mesh
         o = SetupOpts()
         if coarse_mesh is not None:
@@ -306,10 +315,7 @@ class Prec:
             self._agg = np.ascontiguousarray(agg_of_elem, np.int32)
             o.agg_of_elem = _ip(self._agg)
         o.stream = _stream_ptr(stream)
-        h = C.c_void_p()
-        check(lib().dgasm_setup(system.h, C.byref(o), C.byref(h)))
-        self.h = h
-        self.ndof = system.ndof
+        return o
 
     def set_rhs_chunk(self, nrhs, kc):
         """Right-hand sides per local-solve item for nrhs-vector solves: 1, 4, or 0 to let the first solve
@@ -376,6 +382,31 @@ class Prec:
         if getattr(self, "h", None) and _lib is not None:
             _lib.dgasm_prec_destroy(self.h)
             self.h = None
+
+
+def setup_batch(problems):
+    """Preconditioners of several problems built at once (dgasm_setup_batch): problems is a list of dicts of
+    Prec's arguments (system, nsub, ncoarse and optionally p_c, precision, sub_of_elem, agg_of_elem, stream,
+    coarse_mesh).  Returns one Prec per problem, each the same as Prec(**problem) would build."""
+    n = len(problems)
+    if n < 1:
+        raise ValueError("no problems")
+    precs, opts = [], []
+    for pr in problems:
+        P = Prec.__new__(Prec)
+        P.h = None
+        a = dict(p_c=1, precision="fp64", sub_of_elem=None, agg_of_elem=None, stream=None, coarse_mesh=None)
+        a.update(pr)
+        opts.append(P._options(a["system"], a["nsub"], a["ncoarse"], a["p_c"], a["precision"], a["sub_of_elem"],
+                               a["agg_of_elem"], a["stream"], a["coarse_mesh"]))
+        precs.append(P)
+    systems = (C.c_void_p * n)(*[P.system.h.value for P in precs])
+    op = (C.POINTER(SetupOpts) * n)(*[C.pointer(o) for o in opts])
+    hs = (C.c_void_p * n)()
+    check(lib().dgasm_setup_batch(n, systems, op, hs))
+    for P, h in zip(precs, hs):
+        P.h = C.c_void_p(h)
+    return precs
 
 
 def solve_batch(precs, bs, xs, rtol=1e-8, maxit=10000, fixed_iters=0, stream=None, x0_given=False):

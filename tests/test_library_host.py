@@ -24,6 +24,7 @@ def test_library_loads_and_exports_header_symbols():
 # every entry point with NULL handles and buffers: an argument check answers before any CUDA call
 NULL_CALLS = {
     "dgasm_setup": (None, None, None),
+    "dgasm_setup_batch": (0, None, None, None),
     "dgasm_prec_apply": (None, 1, None, None, None),
     "dgasm_prec_set_rhs_chunk": (None, 1, 1),
     "dgasm_prec_get_rhs_chunk": (None, 1, None),
