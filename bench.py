@@ -388,6 +388,7 @@ def serve_measure(n_req, fracs):
         reqs = [make_request() for _ in arrivals]
         t0 = time.perf_counter()
         pending, lat, rhs_done = {}, [], 0
+        failed = {}   # return code -> requests that ended with it (reported, not dropped silently)
         i = 0
         t_last = t0
         while i < len(reqs) or pending:
@@ -404,7 +405,9 @@ def serve_measure(n_req, fracs):
                 if rc == 1:
                     continue
                 a, k, _ = pending.pop(t)
-                assert rc == 0, rc
+                if rc != 0:
+                    failed[str(rc)] = failed.get(str(rc), 0) + 1
+                    continue
                 t_done = time.perf_counter() - t0
                 lat.append(t_done - a)
                 rhs_done += k
@@ -413,9 +416,14 @@ def serve_measure(n_req, fracs):
         stats = srv.stats()
         srv.close()
         lat.sort()
-        return {"requests": len(lat), "rhs": rhs_done, "rhs_per_s": rhs_done / max(t_last - arrivals[0], 1e-9),
-                "p50_ms": 1000 * lat[len(lat) // 2], "p99_ms": 1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                "mean_ms": 1000 * sum(lat) / len(lat), "rounds": stats["rounds"], "stalls": stats["stalls"]}
+        out = {"requests": len(lat), "rhs": rhs_done, "rhs_per_s": rhs_done / max(t_last - arrivals[0], 1e-9),
+               "rounds": stats["rounds"], "stalls": stats["stalls"]}
+        if lat:
+            out.update(p50_ms=1000 * lat[len(lat) // 2], p99_ms=1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       mean_ms=1000 * sum(lat) / len(lat))
+        if failed:
+            out["failed_requests_by_code"] = failed
+        return out
 
     res = {}
     for precision, fr in fracs.items():
@@ -848,33 +856,44 @@ def main():
         mixed_tf32 = run_mixed("tf32", "fp32 local factors with tensor-core (split TF32) trailing updates, fp64 outer")
         mixed_bf16 = run_mixed("bf16", "bf16 local factor streams (fp32 factorisation and accumulation), fp64 outer")
 
-    # the precision (p = 4), batching and serving configurations, compact (rank 0 only)
-    extras = {}
-    if rank == 0 and not args.quick:
+    # the precision (p = 4), batching and serving configurations, compact (rank 0 only); a section that fails
+    # is recorded in the line with its error instead of ending the run before the headline is printed
+    def section(fn):
         t0 = time.perf_counter()
-        extras["precision_sweep"] = {
-            "workload": "16384-cell mesh (seed 2) at p=4 (245760 dofs), 64 subdomains, 256 agglomerates p_c=1, "
-                        "checkerboard contrast 1..1e6, local factors per row, fp64 outer PCG; error against the "
-                        "oracle's converged FP64 solve at 1000 sampled dofs",
-            "rows": sweep_measure(timed_reps=2)}
-        extras["precision_sweep"]["seconds"] = time.perf_counter() - t0
-        t0 = time.perf_counter()
+        try:
+            out = fn()
+        except Exception as e:
+            out = {"error": f"{type(e).__name__}: {e}"}
+        out["seconds"] = time.perf_counter() - t0
+        return out
+
+    def sweep_section():
+        return {"workload": "16384-cell mesh (seed 2) at p=4 (245760 dofs), 64 subdomains, 256 agglomerates p_c=1, "
+                            "checkerboard contrast 1..1e6, local factors per row, fp64 outer PCG; error against the "
+                            "oracle's converged FP64 solve at 1000 sampled dofs",
+                "rows": sweep_measure(timed_reps=2)}
+
+    def batch_section():
         bm = batch_measure(1, 1)
         bm["workload"] = ("48 problems: Voronoi meshes (rng 4) with 1024..16384 cells log-uniform, p in {1..4}, N/256 "
                           "subdomains, N/64 agglomerates p_c=1, rho per subdomain log-uniform in [1,1e3], N(0,1) rhs; "
                           "step = setup of all 48 + one batched solve")
-        bm["seconds"] = time.perf_counter() - t0
-        extras["batch"] = bm
-        t0 = time.perf_counter()
+        return bm
+
+    def serving_section():
         sv = serve_measure(args.requests, {"fp32": (0.5, 0.75, 0.9), "fp64": (0.9,)})
-        extras["serving"] = {
-            "workload": f"pool of 16 problems (rng 5) shaped like the batch mix, 1..8 N(0,1) rhs per request, "
-                        f"{args.requests} requests per rate: all at once (saturation), then Poisson arrivals at "
-                        f"fractions of the saturation rate; budget 96 GiB, 24 slots",
-            "fp32": sv["fp32"], "fp64": sv["fp64"],
-            "saturation_speedup_mixed_vs_fp64": sv["fp32"]["saturation_closed_batch"]["rhs_per_s"] /
-                                                sv["fp64"]["saturation_closed_batch"]["rhs_per_s"],
-            "seconds": time.perf_counter() - t0}
+        return {"workload": f"pool of 16 problems (rng 5) shaped like the batch mix, 1..8 N(0,1) rhs per request, "
+                            f"{args.requests} requests per rate: all at once (saturation), then Poisson arrivals at "
+                            f"fractions of the saturation rate; budget 96 GiB, 24 slots",
+                "fp32": sv["fp32"], "fp64": sv["fp64"],
+                "saturation_speedup_mixed_vs_fp64": sv["fp32"]["saturation_closed_batch"]["rhs_per_s"] /
+                                                    sv["fp64"]["saturation_closed_batch"]["rhs_per_s"]}
+
+    extras = {}
+    if rank == 0 and not args.quick:
+        extras["precision_sweep"] = section(sweep_section)
+        extras["batch"] = section(batch_section)
+        extras["serving"] = section(serving_section)
 
     if rank != 0:
         if world > 1:
