@@ -20,7 +20,7 @@
 namespace dgasm {
 
 // ---- workspace of one problem for k right-hand sides ------------------------------------------
-int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
+int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_, cudaStream_t stream) {
   // partial (r, z) sums: one per subdomain, element chunk (element blocks) or explicit-inverse item
   const int need_rz = std::max(pc.P.nsub, std::max(pc.n_dli_items, (pc.P.ne + NTHREADS / pc.P.np - 1) / (NTHREADS / pc.P.np)));
   if (k_ <= k && maxit_ <= maxit && need_rz <= n_rz_cap && buf.ptr) return DGASM_OK;
@@ -49,7 +49,7 @@ int Workspace::ensure(const dgasm_prec_s& pc, int k_, int maxit_) {
   o_pc = take(sizeof(double) * (size_t)std::max(n_coarse_items, 1) * k);
   o_cnt = take(sizeof(unsigned) * C_NCOUNTERS);
   DG_TRY(buf.alloc(off));
-  DG_CUDA(cudaMemset(buf.ptr, 0, off));
+  DG_CUDA(cudaMemsetAsync(buf.ptr, 0, off, stream));
   return DGASM_OK;
 }
 
@@ -155,7 +155,7 @@ int Engine::build(int n, dgasm_prec_s* const* pcs_, const int* nrhs_, const doub
     const int maxit = (o && o->maxit > 0) ? o->maxit : 10000;
     const int fixed = o ? std::max(o->fixed_iters, 0) : 0;
     const int hist = fixed > 0 ? fixed : maxit;
-    DG_TRY(pc->ws.ensure(*pc, nrhs[i], hist));
+    DG_TRY(pc->ws.ensure(*pc, nrhs[i], hist, st));
     pc->ws.fill(*pc, hp[i], nrhs[i], b[i], x[i], hist, fixed, rtol);
     const ProbDev& D = hp[i];
     for (int kind = 0; kind < K_NSLOTS; ++kind) P_(kind, i + 1) = P_(kind, i);

@@ -38,7 +38,10 @@ struct Workspace {
   // none); kept with the problem, so it survives the engine being rebuilt for other batches
   std::vector<int> lanczos_len;
   size_t o_vec = 0, o_coarse = 0, o_scal = 0, o_int = 0, o_hist = 0, o_ppq = 0, o_prr = 0, o_prz = 0, o_pc = 0, o_cnt = 0;
-  int ensure(const dgasm_prec_s& pc, int k, int maxit);
+  // (re)allocates for k right-hand sides and maxit recorded iterations; a new buffer is zeroed on `stream`, the
+  // stream the caller's kernels then use (a plain cudaMemset would run on the legacy stream, unordered with
+  // the library's non-blocking streams, and could land after the first kernels had written the state)
+  int ensure(const dgasm_prec_s& pc, int k, int maxit, cudaStream_t stream);
   void fill(const dgasm_prec_s& pc, ProbDev& D, int k, const double* b_user, double* x_user, int maxit, int fixed,
             double rtol) const;
 };
