@@ -259,3 +259,30 @@ def test_partitions_and_plans_from_concurrent_threads_match_serial():
     for (i, c), (sub, agg) in got.items():
         assert np.array_equal(sub, ref[c][0]) and np.array_equal(agg, ref[c][1]), (i, c)
     assert all(v == 0 and k > 0 for v, k in checks.values()), checks
+
+
+def test_no_unordered_legacy_stream_writes_in_library_sources():
+    """The library's kernels run on non-blocking streams, which the legacy default stream does not order with.
+    A plain cudaMemset, or a cudaMemcpy from the host, is queued on that legacy stream and can land after kernels
+    issued later on another stream.  Two such gaps were found (the upload of plan arrays, the clear of a new
+    Krylov workspace); this scan keeps new ones out: every plain cudaMemset or host-to-device cudaMemcpy in the
+    sources must sit in a function listed here, each of which orders it (a legacy-stream wait, or kernels that run
+    on the legacy stream themselves)."""
+    import os
+    import re
+    allowed = {"upload", "dgasm_selftest_bounded_wait", "selftest_tc"}
+    src = os.path.join(os.path.dirname(dg.__file__), "csrc")
+    bad = []
+    for name in sorted(os.listdir(src)):
+        if not name.endswith((".cu", ".cpp", ".h")):
+            continue
+        func = None
+        for lineno, line in enumerate(open(os.path.join(src, name)), 1):
+            m = re.match(r"^(?:extern \"C\" )?(?:static )?[\w:<>*& ]+?\b(\w+)\(", line)
+            if m and not line.startswith((" ", "\t", "//", "#")):
+                func = m.group(1)
+            plain_set = re.search(r"\bcudaMemset\(", line)
+            plain_h2d = re.search(r"\bcudaMemcpy\(", line) and "cudaMemcpyDeviceToHost" not in line
+            if (plain_set or plain_h2d) and func not in allowed:
+                bad.append(f"{name}:{lineno} in {func}: {line.strip()}")
+    assert not bad, "\n".join(bad)
